@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a property the
+paper states (Hermiticity and non-negativity of g, Sec. II; SVDU equivalence,
+Sec. II; exact D=2 evolution at h_x=0, Sec. III), a brute-force contraction
+of the eight-site network written independently of the oracle's contraction
+order, a closed form (Eckart-Young, separable metrics, single-site
+evolution), or a gauge invariance that follows from the definitions.
+"""
+import numpy as np
+import pytest
+
+from oracle import ntu_oracle as O
+from paper_2107_06635_gb300 import inputs as I
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _reduced(A, B, G, r, d_anc=1):
+    GA, GB = O.gate_split(G, r)
+    QA, RA = O.qr_positive(O.gated_matrix(A, GA, d_anc, "left"))
+    QB, RB = O.qr_positive(O.gated_matrix(B, GB, d_anc, "right"))
+    return QA, RA, QB, RB
+
+
+# ------------------------------------------------------------- gate split
+def test_gate_split_zz_closed_form():
+    """exp(-i t ZZ) reshaped has operator-Schmidt values 2 cos t, 2 sin t and
+    the split reproduces the gate exactly (Fig. 2(a))."""
+    t = 0.37
+    G = I.zz_gate(t)
+    GA, GB = O.gate_split(G, 2)
+    back = np.einsum("ask,btk->abst", GA, GB)
+    assert _rel(back, G) < 1e-14
+    X = G.transpose(0, 2, 1, 3).reshape(4, 4)
+    s = np.linalg.svd(X, compute_uv=False)
+    assert np.allclose(s[:2], [2 * np.cos(t), 2 * np.sin(t)], atol=1e-14)
+    assert s[2] < 1e-14
+
+
+def test_gate_split_truncates_rank():
+    """A rank-4 gate split at r=2 keeps the two leading Schmidt terms."""
+    G = I.heisenberg_gate(0.2)
+    GA, GB = O.gate_split(G, 4)
+    assert _rel(np.einsum("ask,btk->abst", GA, GB), G) < 1e-14
+    GA2, GB2 = O.gate_split(G, 1)
+    X = G.transpose(0, 2, 1, 3).reshape(4, 4)
+    U, s, Vh = np.linalg.svd(X)
+    best1 = s[0] * np.outer(U[:, 0], Vh[0])
+    got = np.einsum("ask,btk->asbt", GA2, GB2).reshape(4, 4)
+    assert _rel(got, best1) < 1e-13
+
+
+# ------------------------------------------------------- P1: Hermitian PSD
+@pytest.mark.parametrize("D,d_anc,r", [(2, 1, 2), (3, 1, 2), (4, 1, 2), (3, 2, 2), (3, 1, 4)])
+def test_p1_raw_metric_hermitian_psd(D, d_anc, r):
+    """The exact metric is Hermitian and non-negative to machine precision
+    (Sec. II)."""
+    A, B = I.random_pair(10 + D, 2 * d_anc, D)
+    G = I.zz_gate(0.1) if r == 2 else I.heisenberg_gate(0.1)
+    QA, RA, QB, RB = _reduced(A, B, G, r, d_anc)
+    g = O.metric_raw(A, B, QA, QB, 2 * d_anc, D)
+    assert np.linalg.norm(g - g.conj().T) / np.linalg.norm(g) < 1e-14
+    lam = np.linalg.eigvalsh(0.5 * (g + g.conj().T))
+    assert lam[0] >= -1e-13 * lam[-1]
+
+
+# --------------------------------------------- P2: brute-force eight sites
+def _brute(Ta, Tb, QA, QB, d_p, D):
+    K = QA.shape[1]
+    qa = QA.reshape(d_p, D, D, D, K)      # [pA, A.l, A.u, A.dn, kA]
+    qb = QB.reshape(d_p, D, D, D, K)      # [pB, B.r, B.u, B.dn, kB]
+    g = np.zeros((K * K, K * K), dtype=np.complex128)
+    for pl in range(d_p):
+        for pt in range(d_p):
+            for pm in range(d_p):
+                # L = Tb[pl][l, u, r, dn]: r = A.l (a)
+                # TL = Tb[pt][l, u, r, dn]: r = h (top crossing), dn = A.u (b)
+                # BL = Tb[pm][l, u, r, dn]: u = A.dn (c), r = i (bottom crossing)
+                # R = Ta[p][l, u, r, dn]: l = B.r (d)
+                # TR = Ta[p][l, u, r, dn]: l = h, dn = B.u (e)
+                # BR = Ta[p][l, u, r, dn]: l = i, u = B.dn (f)
+                phi = np.einsum(
+                    "AabcK,BdefZ,jkal,mnhb,ocip,Rdqst,Shvwe,Nifxy->ABRSNjklmnopqstvwxyKZ",
+                    qa, qb, Tb[pl], Tb[pt], Tb[pm], Ta, Ta, Ta, optimize=True)
+                phi = phi.reshape(-1, K * K)
+                g += phi.conj().T @ phi
+    return g
+
+
+@pytest.mark.parametrize("D,r", [(1, 2), (2, 1), (2, 2)])
+def test_p2_brute_force_eight_site(D, r):
+    """The oracle's contraction order (edge tensors, half environments,
+    join) equals the literal eight-site network Phi^dag Phi."""
+    d_p = 2
+    A, B = I.random_pair(20 + D + r, d_p, D)
+    rng = np.random.default_rng(3)
+    G = I.random_gate(rng)
+    QA, RA, QB, RB = _reduced(A, B, G, r)
+    g = O.metric_raw(A, B, QA, QB, d_p, D)
+    gb = _brute(A, B, QA, QB, d_p, D)
+    assert _rel(g, gb) < 1e-13
+
+
+def test_p2_catches_planted_mistakes(monkeypatch):
+    """Plant plausible mistakes in the oracle and check the brute force sees
+    them: a ket/bra swap on one crossing leg, and a dropped conjugate."""
+    D, r, d_p = 2, 2, 2
+    A, B = I.random_pair(31, d_p, D)
+    G = I.random_gate(np.random.default_rng(4))
+    QA, RA, QB, RB = _reduced(A, B, G, r)
+    gb = _brute(A, B, QA, QB, d_p, D)
+    orig = O.edge_tensors
+
+    def swapped(Ta, Tb):
+        E = orig(Ta, Tb)
+        E["TL"] = E["TL"].transpose(2, 1, 0, 3)     # ht <-> ht'
+        return E
+
+    monkeypatch.setattr(O, "edge_tensors", swapped)
+    assert _rel(O.metric_raw(A, B, QA, QB, d_p, D), gb) > 1e-3
+    monkeypatch.setattr(O, "edge_tensors", orig)
+
+    orig_half = O.half_environment
+
+    def no_conj(Q, Es, Et, Eb, d_p_, D_):
+        return orig_half(Q, Es.T, Et, Eb, d_p_, D_)    # side edge transposed
+
+    monkeypatch.setattr(O, "half_environment", no_conj)
+    assert _rel(O.metric_raw(A, B, QA, QB, d_p, D), gb) > 1e-3
+
+
+# ------------------------------------------------- P3: gauge invariance
+def _random_unitary(rng, n):
+    m = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    q, r = np.linalg.qr(m)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def test_p3_unitary_gauge_invariance():
+    """Unitaries U on A's legs u, l, dn with conj(U) on B's matching legs
+    leave R_A R_B^T and g unchanged (the external legs are closed by
+    ket/bra pairing, which is unitarily invariant)."""
+    D, d_p = 3, 2
+    A, B = I.random_pair(41, d_p, D)
+    G = I.zz_gate(0.2)
+    rng = np.random.default_rng(5)
+    U1, U2, U3 = (_random_unitary(rng, D) for _ in range(3))
+    # bond type 1 (A.u - B.dn), 2 (A.l - B.r), 3 (A.dn - B.u)
+    A2 = np.einsum("xu,plurn->plxrn", U1, A)
+    B2 = np.einsum("xn,plurn->plurx", U1.conj(), B)
+    A2 = np.einsum("xl,plurn->pxurn", U2, A2)
+    B2 = np.einsum("xr,plurn->pluxn", U2.conj(), B2)
+    A2 = np.einsum("xn,plurn->plurx", U3, A2)
+    B2 = np.einsum("xu,plurn->plxrn", U3.conj(), B2)
+    QA, RA, QB, RB = _reduced(A, B, G, 2)
+    QA2, RA2, QB2, RB2 = _reduced(A2, B2, G, 2)
+    assert _rel(RA2 @ RB2.T, RA @ RB.T) < 1e-13
+    g = O.metric_raw(A, B, QA, QB, d_p, D)
+    g2 = O.metric_raw(A2, B2, QA2, QB2, d_p, D)
+    assert _rel(g2, g) < 1e-13
+
+
+# ------------------------------------------------------ P4: identity gate
+@pytest.mark.parametrize("r", [1, 2])
+def test_p4_identity_gate_zero_error(r):
+    """With the identity gate R_A R_B^T has rank <= D, so the truncation is
+    exact: delta = 0 (Fig. 2(c))."""
+    D = 3
+    A, B = I.random_pair(51, 2, D)
+    cfg = O.Config(D=D, r=r)
+    _, _, info = O.bond_update(A, B, I.identity_gate(), cfg)
+    assert info.delta <= 1e-14
+
+
+# ------------------------------------------------- P5: g = 1, Eckart-Young
+def test_p5_identity_metric_keeps_svdu():
+    """With g = 1 the error is the Frobenius norm; SVDU is its minimiser
+    (Sec. II) and ALS must stay there: eps = sum of discarded s_i^2."""
+    rng = np.random.default_rng(6)
+    K, D = 8, 4
+    RA = rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K))
+    RB = rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K))
+    g = np.eye(K * K, dtype=np.complex128)
+    s = np.linalg.svd(RA @ RB.T, compute_uv=False)
+    _, _, eps, delta, eps0, _ = O.als_truncate(g, RA, RB, D, 6, O.Config(D=D).taus)
+    assert abs(eps - np.sum(s[D:] ** 2)) <= 1e-12 * np.sum(s ** 2)
+    assert abs(eps0 - np.sum(s ** 2)) <= 1e-12 * eps0
+
+
+# --------------------------------------------- P6: separable metric optimum
+def _sqrtm_h(m):
+    lam, w = np.linalg.eigh(m)
+    return (w * np.sqrt(lam)) @ w.conj().T
+
+
+def test_p6_separable_metric_reaches_closed_form():
+    """For g = g_L (x) g_R (the product form of the simple-update metric,
+    Sec. II) the weighted problem becomes plain Eckart-Young for
+    Y = g_L^{1/2} X (g_R^T)^{1/2}: eps_min = sum of the discarded s_i(Y0)^2.
+    ALS from the SVDU start must reach it."""
+    rng = np.random.default_rng(7)
+    K, D = 6, 3
+
+    def pd(n):
+        w = _random_unitary(rng, n)
+        return (w * rng.uniform(0.5, 2.0, n)) @ w.conj().T
+
+    gL, gR = pd(K), pd(K)
+    g = np.kron(gL, gR)
+    SL, SR = _sqrtm_h(gL), _sqrtm_h(gR.T)
+    sy = np.array([9.0, 6.0, 4.0, 0.4, 0.2, 0.1])
+    Y0 = _random_unitary(rng, K) @ np.diag(sy) @ _random_unitary(rng, K)
+    X0 = np.linalg.solve(SL, Y0) @ np.linalg.inv(SR)
+    eps_min = np.sum(sy[D:] ** 2)
+    _, _, eps, _, eps0, _ = O.als_truncate(g, X0, np.eye(K), D, 50, O.Config(D=D).taus)
+    assert abs(eps0 - np.sum(sy ** 2)) < 1e-10 * eps0
+    assert abs(eps - eps_min) <= 1e-10 * eps_min
+    # rank <= D: the optimum is exact, eps = 0
+    Y1 = Y0.copy()
+    U, s, Vh = np.linalg.svd(Y1)
+    s[D:] = 0
+    X1 = np.linalg.solve(SL, (U * s) @ Vh) @ np.linalg.inv(SR)
+    _, _, eps1, _, eps01, _ = O.als_truncate(g, X1, np.eye(K), D, 3, O.Config(D=D).taus)
+    assert eps1 <= 1e-13 * eps01
+
+
+# ------------------------------------------ P7: D=1 exact single-site run
+def test_p7_product_state_single_site_evolution():
+    """H = -h X from |+z> at D=1 with identity two-site gates: the Trotter
+    step is exact and <sigma_z>(t) = cos(2 h t)."""
+    h, dt, n = 0.7, 0.05, 20
+    cfg = O.Config(D=1, r=1, sweeps=2)
+    A = I.plus_z_state(1)
+    B = I.plus_z_state(1)
+    gate1 = I.x_rotation(h * dt / 2)
+    gates2 = [I.identity_gate()] * 4
+    for step in range(1, n + 1):
+        A, B, deltas = O.ntu_step(A, B, gates2, gate1, cfg)
+        t = step * dt
+        for site in (0, 1):
+            z = O.measure(A, B, site, I.pauli("Z"), 1)
+            assert abs(z - np.cos(2 * h * t)) < 1e-12
+        assert max(deltas) < 1e-14
+
+
+# ---------------------------------------------- P8: h_x = 0 is exact at D=2
+def test_p8_classical_quench_exact_at_D2():
+    """At h_x = 0 the exact evolution has bond rank 2 (Sec. III): every bond
+    update at D=2 is exact, delta <= 1e-12."""
+    cfg = O.Config(D=2, r=2, sweeps=4)
+    A = I.plus_x_state(2)
+    B = I.plus_x_state(2)
+    gates2, _ = I.tfim_real_time_gates(0.0, 0.05)
+    for _ in range(4):
+        A, B, deltas = O.ntu_step(A, B, gates2, None, cfg)
+        assert max(deltas) <= 1e-12
+
+
+# --------------------------------------- P9: schematic SVDU = efficient SVDU
+def _schematic_svdu(A, B, G, D):
+    """Fig. 1(b,c): apply G to the pair, SVD the (d D^3) x (d D^3) matrix,
+    keep D values."""
+    d_p = A.shape[0]
+    # theta[pA', A.l, A.u, A.dn, pB', B.u, B.r, B.dn], summed over A.r = B.l (x)
+    theta = np.einsum("abst,sluxn,txvwy->alunbvwy", G, A, B)
+    M = theta.reshape(d_p * D ** 3, d_p * D ** 3)
+    U, s, Vh = np.linalg.svd(M)
+    return (U[:, :D] * s[:D]) @ Vh[:D]
+
+
+def test_p9_schematic_equals_efficient_svdu():
+    """The efficient SVDU of Fig. 2 equals the schematic SVDU of Fig. 1 (Sec.
+    II calls them equivalent): same truncated two-site product, up to
+    normalisation."""
+    for D in (1, 2):
+        A, B = I.random_pair(61 + D, 2, D)
+        G = I.random_gate(np.random.default_rng(8))
+        cfg = O.Config(D=D, r=4, sweeps=0)
+        A2, B2, _ = O.bond_update(A, B, G, cfg)
+        pair = np.einsum("plurn,qrvwx->plunqvwx", A2, B2).reshape(2 * D ** 3, 2 * D ** 3)
+        ref = _schematic_svdu(A, B, G, D)
+        pair = pair / np.linalg.norm(pair)
+        ref = ref / np.linalg.norm(ref)
+        assert _rel(pair, ref) < 1e-12
+
+
+# ------------------------------------------- P11: error bookkeeping (Eq. 3)
+def test_p11_spectral_eps_matches_quadratic_form():
+    """eps(tau) evaluated in g_A's eigenbasis equals Eq. 3 at the same
+    candidate, and the final eps (full quadratic form in g) equals the last
+    half-step's eps; eps does not increase over sweeps."""
+    D = 3
+    A, B = I.random_pair(71, 2, D)
+    cfg = O.Config(D=D)
+    _, _, info = O.bond_update(A, B, I.random_gate(np.random.default_rng(9)), cfg, keep=True)
+    g, RA, RB = info.g, info.RA, info.RB
+    X0 = RA @ RB.T
+    x0 = X0.reshape(-1)
+    gx0 = g @ x0
+    eps0 = np.real(np.vdot(x0, gx0))
+    MA, MB = O.svdu_init(X0, D)
+    gA, JA = O.reduced_problem_A(g, gx0, MB)
+    for tau in (1e-4, 1e-8):
+        v, t, e = O.pinv_select(gA, JA, eps0, [tau])
+        direct = np.real(np.vdot(v, gA @ v)) - 2 * np.real(np.vdot(v, JA)) + eps0
+        assert abs(e - direct) <= 1e-12 * eps0
+        x = (v.reshape(-1, D) @ MB.T).reshape(-1) - x0
+        assert abs(np.real(np.vdot(x, g @ x)) - e) <= 1e-12 * eps0
+    prev = np.inf
+    for sweeps in range(0, 5):
+        _, _, eps, _, _, _ = O.als_truncate(g, RA, RB, D, sweeps, cfg.taus)
+        assert eps <= prev * (1 + 1e-10)
+        prev = eps
+
+
+# --------------------------------------------------- bookkeeping helpers
+def test_rotation_round_trip():
+    A, _ = I.random_pair(81, 2, 3)
+    assert np.array_equal(O.unrotate(O.rotate(A)), A)
+    R4 = O.rotate(O.rotate(O.rotate(O.rotate(A))))
+    assert np.array_equal(R4, A)
+
+
+def test_measure_product_state():
+    psi = np.array([0.6, 0.8j])
+    A = I.product_state(psi, 1)
+    x = O.measure(A, A, 0, I.pauli("X"), 1)
+    assert abs(x - np.vdot(psi, I.pauli("X") @ psi)) < 1e-15
+    P = I.purification_state(1)
+    assert abs(O.measure(P, P, 0, I.pauli("Z"), 2)) < 1e-15
+
+
+def test_recompose_reproduces_gated_pair():
+    """Without truncation (r=1, identity), A'B' equals the original pair up to
+    normalisation: the bookkeeping of Fig. 2(e) inverts Fig. 2(a,b)."""
+    D = 2
+    A, B = I.random_pair(91, 2, D)
+    cfg = O.Config(D=D, r=1, sweeps=1)
+    A2, B2, _ = O.bond_update(A, B, I.identity_gate(), cfg)
+    p1 = np.einsum("plurn,qrvwx->plunqvwx", A, B)
+    p2 = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
+    assert _rel(p2 / np.linalg.norm(p2), p1 / np.linalg.norm(p1)) < 1e-12
+
+
+def test_p3_catches_swapped_legs_in_gated_matrix(monkeypatch):
+    """Plant the mistake of reading T's l and u legs in swapped order when
+    the gate is applied: gauge invariance must break."""
+    D, d_p = 3, 2
+    A, B = I.random_pair(42, d_p, D)
+    G = I.zz_gate(0.2)
+    U = _random_unitary(np.random.default_rng(6), D)
+    A2 = np.einsum("xn,plurn->plurx", U, A)
+    B2 = np.einsum("xu,plurn->plxrn", U.conj(), B)
+
+    def wrong(T, GX, d_anc, side):
+        Dd = T.shape[1]
+        T6 = T.reshape(GX.shape[0], d_anc, Dd, Dd, Dd, Dd)
+        spec = "tsk,sculwn->tclunwk" if side == "left" else "tsk,sculwn->tcwunlk"
+        return np.einsum(spec, GX, T6).reshape(T.shape[0] * Dd ** 3, -1)
+
+    monkeypatch.setattr(O, "gated_matrix", wrong)
+    _, RA, _, RB = _reduced(A, B, G, 2)
+    _, RA2, _, RB2 = _reduced(A2, B2, G, 2)
+    assert _rel(RA2 @ RB2.T, RA @ RB.T) > 1e-3
+
+
+def test_golden_one_step_d3_regression():
+    """The oracle still reproduces its stored one-step record (D=3, seed 1)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "one_step_d3.json")
+    ref = json.load(open(path))
+    A, B = I.random_pair(1, 2, 3)
+    cfg = O.Config(D=3, r=2, sweeps=10)
+    for b in range(4):
+        A, B, info = O.update_bond(A, B, b, I.zz_gate(0.01), cfg)
+        assert abs(info.delta - ref["bonds"][b]["delta"]) < 1e-12
+    Aref = np.array(ref["A_after"][0]) + 1j * np.array(ref["A_after"][1])
+    assert np.linalg.norm(A.reshape(-1) - Aref) < 1e-10
