@@ -59,8 +59,9 @@ class Config:
 
     @property
     def taus(self):
-        """Candidate relative pseudo-inverse tolerances, largest first."""
-        return [10.0 ** (-k) for k in sorted(self.tau_exponents)]
+        """Candidate relative pseudo-inverse tolerances 1e-k, largest first
+        (parsed from their decimal form, i.e. correctly rounded)."""
+        return [float("1e-%d" % k) for k in sorted(self.tau_exponents)]
 
 
 # ---------------------------------------------------------------- helpers
