@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Throughput of batched NTU bond updates on GB300.
+
+One step = one pass of the whole bond update (gate split and QR, exact
+eight-site environment metric, Hermitise/repair, SVDU start + ALS sweeps,
+recompose) over a batch of independent synthetic bond updates shaped like the
+paper's workloads: D=8, d=2, gate exp(-i 0.01 ZZ) split at r=2, iid complex
+N(0,1) site tensors (seed 5, normalised), 10 ALS sweeps.  The headline path
+is the mixed one (FP32 environment contraction, FP64 solvers); the plain FP64
+path is measured on the same GPU for comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_06635_gb300 import inputs as I  # noqa: E402
+
+METRIC = "NTU bond updates/s"
+FP64_PEAK = 1.25e12          # nominal GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
+FP32_SIMT_PEAK = 152 * 128 * 2 * 2.07e9   # nominal FP32 FMA pipes
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------- algorithmic work
+def env_flops(D, r, d_p=2):
+    """Real flops of the environment contraction of one bond update:
+    8 x complex MACs of edge tensors, half networks and join (Fig. 4)."""
+    mac = d_p * (2 * D ** 5 + 4 * D ** 6) + 2 * (d_p * D ** 5 * r + d_p * D ** 7 * r * r
+                                                 + 2 * D ** 8 * r * r) + D ** 8 * r ** 4
+    return 8.0 * mac
+
+
+def als_flops(D, r, sweeps):
+    """Real FP64 flops of the ALS stage of one bond update: per sweep two
+    reduced-metric builds (8 (K^4 D + K^3 D^2) each) and two Hermitian
+    tridiagonalisations of n_A = K D ((16/3) n_A^3 each), plus g x0 and the
+    final error (8 n_g^2 each)."""
+    K = D * r
+    nA, ng = K * D, K * K
+    per_sweep = 2 * 8.0 * (K ** 4 * D + K ** 3 * D * D) + 2 * (16.0 / 3.0) * nA ** 3
+    return sweeps * per_sweep + 2 * 8.0 * ng * ng
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, f in enumerate(fl)
+                          if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ oracle leg
+def _oracle_rate(D, r, sweeps, seconds, seed, max_items=64):
+    """Bond updates/s of the CPU oracle on the first items of the workload,
+    run in a fresh child process with all host cores available to BLAS."""
+    cores = len(os.sched_getaffinity(0))
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import ntu_oracle as O
+from paper_2107_06635_gb300 import inputs as I
+cfg = O.Config(D={D}, r={r}, sweeps={sweeps})
+Ta, Tb, G = I.batch_items({seed}, {max_items}, 2, {D}, I.zz_gate(0.01))
+O.bond_update(Ta[0], Tb[0], G[0], cfg)          # warm-up (BLAS threads, caches)
+t0 = time.perf_counter(); n = 0
+while n < {max_items} and (n < 2 or time.perf_counter() - t0 < {seconds}):
+    O.bond_update(Ta[n], Tb[n], G[n], cfg); n += 1
+dt = time.perf_counter() - t0
+print(json.dumps({{"n": n, "seconds": dt}}))
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    return res["n"] / res["seconds"], res["n"], res["seconds"], cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    D, r, sweeps = args.D, args.r, args.sweeps
+    times, items = [], 0
+    cores = len(os.sched_getaffinity(0))
+    # one step = a bounded sample of the workload on the host cores
+    for i in range(args.warmup + args.steps):
+        rate, n, sec, cores = _oracle_rate(D, r, sweeps, args.ref_seconds, 5 + i, max_items=8)
+        if i >= args.warmup:
+            times.append(sec)
+            items += n
+    value = items / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "bond updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": workload_config(args, "fp64 oracle (CPU)"),
+        "cpu_baseline": {"value": value, "unit": "bond updates/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{items} D={D} bond updates over {args.steps} steps"},
+        "e2e": {"value": value, "unit": "bond updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def workload_config(args, precision):
+    return {"workload": f"batched NTU bond updates, D={args.D} d=2 r={args.r}, "
+                        f"exp(-i 0.01 ZZ), {args.sweeps} ALS sweeps",
+            "D": args.D, "d": 2, "r": args.r, "batch_per_gpu": args.batch,
+            "sweeps": args.sweeps, "precision": precision, "seed": 5,
+            "l2": "flushed (256 MB write) before every timed step"}
+
+
+# --------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+    from paper_2107_06635_gb300 import ntu
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    D, r, B, S = args.D, args.r, args.batch, args.sweeps
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    Ta_h, Tb_h, G_h = I.batch_items(5 + 1000 * rank, B, 2, D, I.zz_gate(0.01))
+    Ta = torch.from_numpy(Ta_h).cuda()
+    Tb = torch.from_numpy(Tb_h).cuda()
+    G = torch.from_numpy(G_h).cuda()
+    Ta_o, Tb_o = torch.empty_like(Ta), torch.empty_like(Tb)
+    info = torch.empty((B, 4), dtype=torch.float64, device="cuda")
+
+    def measure(precision, steps, warmup, kmax):
+        ctx = ntu.Context(D, 2, 1, r, S, precision, 4, kmax, B, stream=stream.cuda_stream)
+        ctx.set_profiling(True)
+        t_step, stages, launches = [], [], 0
+        for i in range(warmup + steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.batch_update_dev(B, Ta, Tb, G, Ta_o, Tb_o, info)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            if i >= warmup:
+                t_step.append(e0.elapsed_time(e1))
+                stages.append(ctx.stage_times())
+                launches += ctx.last_launch_count()
+        ctx.sync()
+        return ctx, t_step, np.mean(stages, axis=0), launches
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx, t_mixed, st_mixed, launches = measure(ntu.NTU_MIXED_FP32, args.steps, args.warmup, 8)
+    clk = clocks.stop()
+    ms_mixed = max_over_ranks(statistics.mean(t_mixed))
+    value = world * B / (ms_mixed / 1e3)
+    delta_mixed = info[:, 1].cpu().numpy()
+
+    # end to end through the host-pointer call: pinned inputs in, results out
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    hTa, hTb, hG = pin(Ta_h), pin(Tb_h), pin(G_h)
+    hA = torch.empty_like(hTa).pin_memory()
+    hB = torch.empty_like(hTb).pin_memory()
+    hI = torch.empty((B, 4), dtype=torch.float64).pin_memory()
+    t_e2e = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ctx._ck(ctx.lib.ntu_batch_update_host(ctx.h, B, hTa.data_ptr(), hTb.data_ptr(),
+                                              hG.data_ptr(), hA.data_ptr(), hB.data_ptr(),
+                                              hI.data_ptr()))
+        dt = time.perf_counter() - t0
+        barrier()
+        if i >= args.warmup:
+            t_e2e.append(dt)
+    e2e_s = max_over_ranks(statistics.mean(t_e2e))
+    h2d = (Ta_h.nbytes + Tb_h.nbytes + G_h.nbytes)
+    d2h = (Ta_h.nbytes + Tb_h.nbytes + B * 4 * 8)
+    ctx.close()
+    del ctx
+
+    # plain FP64 path on the same GPU, same batch
+    fp64 = None
+    if not args.no_fp64:
+        ctx64, t64, st64, _ = measure(ntu.NTU_FP64, args.fp64_steps, 1, 15)
+        ms64 = max_over_ranks(statistics.mean(t64))
+        fp64 = {"value": world * B / (ms64 / 1e3), "unit": "bond updates/s",
+                "ms_per_step": ms64,
+                "env_tflops": B * env_flops(D, r) / (st64[1] / 1e3) / 1e12,
+                "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
+                                     [round(x, 3) for x in st64]))}
+        ctx64.close()
+
+    if rank != 0:
+        return
+
+    als_ms = float(st_mixed[3])
+    achieved = B * als_flops(D, r, S) / (als_ms / 1e3)
+    env_achieved = B * env_flops(D, r) / (float(st_mixed[1]) / 1e3)
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, n, sec, cores = _oracle_rate(D, r, S, args.cpu_seconds, 5)
+        cpu = {"value": rate, "unit": "bond updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} of the D={D} workload's bond updates in {sec:.1f} s "
+                         f"(numpy/BLAS, {cores} threads)"}
+    peaks = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "bond updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 env + c128 solvers", "data": "synthetic",
+        "config": workload_config(args, "mixed: FP32 environment, FP64 solvers"),
+        "roofline": {"kernel": "k_als (ALS truncation, Fig. 5)", "bound": "alu",
+                     "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK, "traffic": None,
+                     "peak_source": "nominal FP64 derived from unit counts and clocks"},
+        "env_roofline": {"bound": "alu (FP32 SIMT)", "achieved": env_achieved / 1e12,
+                         "peak": FP32_SIMT_PEAK / 1e12, "unit": "TFLOP/s",
+                         "frac": env_achieved / FP32_SIMT_PEAK,
+                         "tensor_peak_bf16_measured": peaks.get("bf16_tflops")},
+        "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
+                             [round(float(x), 3) for x in st_mixed])),
+        "delta_median": float(np.median(delta_mixed)),
+        "fp64_path": fp64,
+        "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+        "e2e": {"value": world * B / e2e_s, "unit": "bond updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--D", type=int, default=8)
+    ap.add_argument("--r", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=304)
+    ap.add_argument("--sweeps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

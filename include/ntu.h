@@ -1,0 +1,185 @@
+/*
+ * ntu.h -- C ABI of the GB300 neighbourhood tensor update (NTU) library.
+ *
+ * The library implements one NTU bond update of an infinite PEPS on the
+ * two-site checkerboard cell (Dziarmaga, arXiv:2107.06635, Sec. II and
+ * Figs. 2-5): split the Trotter gate (Fig. 2(a)), apply it and QR-reduce the
+ * two site tensors to R_A, R_B without physical/ancilla index (Fig. 2(b)),
+ * contract the exact eight-site neighbourhood into the Hermitian,
+ * non-negative bond metric g (Fig. 3(b), Fig. 4), and truncate the bond back
+ * to D by alternating least squares with a tolerance-selected pseudo-inverse,
+ * starting from the local SVD truncation (Fig. 2(c,d), Fig. 5, Eqs. 2-5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - complex numbers are complex128: interleaved (re, im) doubles, i.e. the
+ *    layout of C99 `double _Complex`;
+ *  - site tensor T[p][l][u][r][dn], row-major, dn fastest, with
+ *    p = s_phys * d_anc + s_anc (d_p = d_phys * d_anc);
+ *  - two-site gate G[sA'][sB'][sA][sB] (d_phys^4 complex);
+ *  - bond b of the cell is A's leg b in the order (r, u, l, dn):
+ *    0: A.r-B.l, 1: A.u-B.dn, 2: A.l-B.r, 3: A.dn-B.u;
+ *  - K = D * r is the bond dimension after the gate; n_g = K*K;
+ *  - reduced matrices R are K x K row-major; isometries Q are (d_p D^3) x K
+ *    row-major with rows (p, e, u, dn), e = the horizontal leg pointing away
+ *    from the bond (l for the left-role site, r for the right-role site);
+ *  - metric g is n_g x n_g row-major, rows = bra pair (kA', kB'), columns =
+ *    ket pair (kA, kB), kA slow (Fig. 4(d,e): eps = x^H g x, Eq. 2);
+ *  - truncated matrices M_A, M_B are K x D row-major.
+ *
+ * Ownership and errors
+ * --------------------
+ *  - The caller owns every array it passes and keeps it alive until the call
+ *    returns (host pointers) or until the context's stream has passed the
+ *    work (device pointers, "_dev" calls); the library copies what it keeps.
+ *  - The context owns all device memory it allocates (ntu_init) and frees it
+ *    in ntu_destroy.
+ *  - Every call returns an ntu_status; none aborts the process or traps the
+ *    GPU.  Numeric failures found on the device (non-finite values,
+ *    non-convergence of an eigen-solver) are raised through a status word
+ *    read back at the next synchronising call (ntu_sync, or any call taking
+ *    host pointers).  ntu_last_error() gives a one-line description.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef NTU_H
+#define NTU_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ntu_ctx ntu_ctx;
+
+typedef enum {
+  NTU_OK = 0,
+  NTU_EINVAL = 1,        /* bad argument (shape, index, NULL pointer)        */
+  NTU_ENOMEM = 2,        /* device allocation failed                         */
+  NTU_ECUDA = 3,         /* CUDA runtime error                               */
+  NTU_ENUMERIC = 4,      /* non-finite value or solver non-convergence        */
+  NTU_ETIMEOUT = 5,      /* a bounded device-side wait ran out                */
+  NTU_EUNSUPPORTED = 6,  /* valid request this build does not support        */
+  NTU_ESTATE = 7         /* calls made out of order (apply -> env -> als)     */
+} ntu_status;
+
+typedef enum {
+  NTU_FP64 = 0,          /* every step in FP64                                */
+  NTU_MIXED_FP32 = 1,    /* environment contraction (Fig. 4) in FP32,         */
+                         /* solvers in FP64                                   */
+  NTU_MIXED_BF16X3 = 2   /* environment contraction with split-BF16 tensor-  */
+                         /* core products, FP32 accumulation; solvers FP64   */
+} ntu_precision;
+
+typedef struct {
+  int D;            /* bond dimension, 1 <= D <= 8                           */
+  int d_phys;       /* physical dimension, 2 <= d_phys <= 4                  */
+  int d_anc;        /* ancilla dimension (1: none, 2: purification)         */
+  int r;            /* gate rank kept by the split, 1 <= r <= d_phys^2      */
+  int als_sweeps;   /* fixed number of ALS sweeps (Fig. 5, Eq. 5)           */
+  int precision;    /* ntu_precision                                         */
+  int tau_kmin;     /* candidate pseudo-inverse tolerances are 10^-k,       */
+  int tau_kmax;     /*   k = tau_kmin..tau_kmax (Eq. 4)                      */
+  int max_batch;    /* largest n accepted by the ntu_batch_* calls          */
+} ntu_config;
+
+/* Create a context for one (D, d, r) configuration.  `stream` is a
+ * cudaStream_t (NULL: the context creates its own non-blocking stream).
+ * Requires d_p * D^2 >= r so that the gated site matrix has at least K rows.
+ * Allocates all device memory the calls below need for up to max_batch items. */
+int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out);
+int ntu_destroy(ntu_ctx* ctx);
+const char* ntu_last_error(const ntu_ctx* ctx);
+/* Wait for the context's stream; returns the first device-raised status. */
+int ntu_sync(ntu_ctx* ctx);
+
+/* ---- two-site unit cell held by the context (host pointers) ------------ */
+
+/* Load / read the iPEPS tensors A and B (each d_p*D^4 complex). */
+int ntu_set_state(ntu_ctx* ctx, const double* A, const double* B);
+int ntu_get_state(ntu_ctx* ctx, double* A, double* B);
+
+/* Fig. 2(a,b): split `gate` (d_phys^4 complex) at rank r, apply its halves to
+ * the two sites of `bond`, and QR-reduce them.  Keeps Q and R on the device
+ * for the next two calls.  RA_out / RB_out (K x K complex each) may be NULL. */
+int ntu_apply_gate(ntu_ctx* ctx, int bond, const double* gate,
+                   double* RA_out, double* RB_out);
+
+/* Fig. 4: the exact eight-site metric of the bond prepared by
+ * ntu_apply_gate, Hermitised, non-negativity repaired and normalised to unit
+ * trace.  g_out (n_g x n_g complex) may be NULL; diag_out (3 doubles, may be
+ * NULL) receives [||g - g^H|| / ||g|| before repair, lambda_min / lambda_max
+ * (NaN when a Cholesky factorisation certified g positive definite and no
+ * repair was needed), log(trace) removed by the normalisation]. */
+int ntu_env_metric(ntu_ctx* ctx, int bond, double* g_out, double* diag_out);
+
+/* Fig. 5, Eqs. 2-5: SVDU start, als_sweeps ALS sweeps with the tolerance
+ * chosen to minimise eps, balancing, then A' = Q_A M_A, B' = Q_B M_B written
+ * back into the context's state (unit Frobenius norm each).  Outputs (may be
+ * NULL): eps, delta = eps / eps0, and the last selected tolerance. */
+int ntu_als_truncate(ntu_ctx* ctx, int bond, double* eps_out, double* delta_out,
+                     double* tau_out);
+
+/* One second-order Trotter step: single-site gate `gate1_half` (d_phys x
+ * d_phys complex, NULL for none) on both sites, then the four bond updates
+ * in the order 0,1,2,3 with gates2[b] (4 x d_phys^4 complex), then
+ * gate1_half again.  delta_out (4 doubles) may be NULL. */
+int ntu_step(ntu_ctx* ctx, const double* gates2, const double* gate1_half,
+             double* delta_out);
+
+/* Cluster estimator <O> on site 0 (A) or 1 (B): the site with `op` (d_phys x
+ * d_phys complex) on its physical factor, closed by the leaf edge tensors of
+ * its four neighbours, over the same network with the identity.  value_out:
+ * one complex. */
+int ntu_measure(ntu_ctx* ctx, int site, const double* op, double* value_out);
+
+/* ---- batches of independent bond updates (device pointers) ------------- */
+/* Item i is the bond Ta[i].r - Tb[i].l (bond-0 orientation) of its own
+ * two-site cell with gate gates[i].  All arrays are contiguous stacks of n
+ * items; work is queued on the context's stream and the call returns at once. */
+
+/* The whole update: Ta_out / Tb_out receive A', B'; info (n x 4 doubles)
+ * receives [eps, delta, eps0, tau] per item. */
+int ntu_batch_update_dev(ntu_ctx* ctx, int n, const double* Ta, const double* Tb,
+                         const double* gates, double* Ta_out, double* Tb_out,
+                         double* info);
+
+/* Same with host pointers: host-to-device copies, the update and the
+ * device-to-host copies, synchronised before return. */
+int ntu_batch_update_host(ntu_ctx* ctx, int n, const double* Ta, const double* Tb,
+                          const double* gates, double* Ta_out, double* Tb_out,
+                          double* info);
+
+/* Stage calls (device pointers), for testing and for callers that chain
+ * their own pipeline.
+ *   gate_qr : Fig. 2(a,b)   -> QA, QB ((d_p D^3) x K), RA, RB (K x K)
+ *   env     : Fig. 4        -> raw g (n_g x n_g), no Hermitisation/repair
+ *   repair  : Sec. II       -> g Hermitised, repaired, unit trace; diag n x 3
+ *   als     : Fig. 5        -> MA, MB (K x D), info n x 4
+ *   recompose: Fig. 2(e)    -> Ta_out, Tb_out                              */
+int ntu_batch_gate_qr_dev(ntu_ctx* ctx, int n, const double* Ta, const double* Tb,
+                          const double* gates, double* QA, double* RA, double* QB,
+                          double* RB);
+int ntu_batch_env_dev(ntu_ctx* ctx, int n, const double* Ta, const double* Tb,
+                      const double* QA, const double* QB, double* g);
+int ntu_batch_repair_dev(ntu_ctx* ctx, int n, double* g, double* diag);
+int ntu_batch_als_dev(ntu_ctx* ctx, int n, const double* g, const double* RA,
+                      const double* RB, double* MA, double* MB, double* info);
+int ntu_batch_recompose_dev(ntu_ctx* ctx, int n, const double* QA, const double* QB,
+                            const double* MA, const double* MB, double* Ta_out,
+                            double* Tb_out);
+
+/* Number of kernel launches the last ntu_batch_update_* call queued. */
+int ntu_last_launch_count(const ntu_ctx* ctx);
+
+/* Stage timing of ntu_batch_update_dev / _host.  With profiling on (flag 1),
+ * the context records CUDA events on its stream between the stages of each
+ * update; ntu_stage_times then synchronises and writes the durations in ms of
+ * the last update's five stages into ms_out[5]: gate+QR (Fig. 2(a,b)),
+ * environment (Fig. 4), repair (Sec. II), ALS (Fig. 5), recompose
+ * (Fig. 2(e)).  The ALS stage is exactly one kernel launch. */
+int ntu_set_profiling(ntu_ctx* ctx, int on);
+int ntu_stage_times(ntu_ctx* ctx, double* ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NTU_H */

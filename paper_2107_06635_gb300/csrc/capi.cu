@@ -1,0 +1,505 @@
+// C ABI of the NTU library (include/ntu.h): context and work-space
+// management, argument validation, and the host-side sequencing of the
+// kernels of one bond update.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "ntu_dev.cuh"
+#include "ntu_impl.h"
+
+using namespace ntu;
+
+static char g_noctx_err[320] = "";
+
+int ntu::fail(ntu_ctx* c, int status, const char* fmt, ...) {
+  char* buf = c ? c->err : g_noctx_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 320, fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+static int cuda_check(ntu_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return NTU_OK;
+  int st = (e == cudaErrorMemoryAllocation) ? NTU_ENOMEM : NTU_ECUDA;
+  return fail(c, st, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                   \
+  do {                                                   \
+    int _s = cuda_check(c, (expr), what);                \
+    if (_s != NTU_OK) return _s;                         \
+  } while (0)
+
+// --------------------------------------------------------- work space
+namespace {
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  bool dry = true;
+  template <typename T> T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+void carve(ntu_ctx* c, Carver& cv) {
+  Plan& P = c->plan;
+  Work& W = c->w;
+  const size_t n = W.cap;
+  const size_t es = c->env_es;
+  const size_t d2r = (size_t)P.d * P.d * P.r, mK = (size_t)P.m * P.K;
+  W.GA = cv.take<double2>(n * d2r);
+  W.GB = cv.take<double2>(n * d2r);
+  W.Mg = cv.take<double2>(n * 2 * mK);
+  W.Qcm = cv.take<double2>(n * 2 * mK);
+  W.QA = cv.take<double2>(n * mK);
+  W.QB = cv.take<double2>(n * mK);
+  W.RA = cv.take<double2>(n * P.szR);
+  W.RB = cv.take<double2>(n * P.szR);
+  bool mixed = c->cfg.precision != NTU_FP64;
+  W.Tac = mixed ? (void*)cv.take<char>(n * P.szT * es) : nullptr;
+  W.Tbc = mixed ? (void*)cv.take<char>(n * P.szT * es) : nullptr;
+  W.QAc = mixed ? (void*)cv.take<char>(n * P.szQ * es) : nullptr;
+  W.QBc = mixed ? (void*)cv.take<char>(n * P.szQ * es) : nullptr;
+  W.EL = cv.take<char>(n * P.szE1 * es);
+  W.ER = cv.take<char>(n * P.szE1 * es);
+  W.ETL = cv.take<char>(n * P.szE2 * es);
+  W.EBL = cv.take<char>(n * P.szE2 * es);
+  W.ETR = cv.take<char>(n * P.szE2 * es);
+  W.EBR = cv.take<char>(n * P.szE2 * es);
+  W.Y = cv.take<char>(n * P.szQ * es);
+  W.T1 = cv.take<char>(n * P.szS2 * es);
+  W.T2 = cv.take<char>(n * P.szS2 * es);
+  W.HL = cv.take<char>(n * P.szS2 * es);
+  W.HR = cv.take<char>(n * P.szS2 * es);
+  W.graw = cv.take<double2>(n * P.szG);
+  W.g = cv.take<double2>(n * P.szG);
+  W.gscr = cv.take<double2>(n * P.szG);
+  W.gw = cv.take<double2>(n * P.szG);
+  W.gz = cv.take<double>(n * P.szG);
+  W.geig = cv.take<double>(n * 2 * P.ng);
+  W.gtau = cv.take<double2>(n * P.ng);
+  W.gp = cv.take<double2>(n * P.ng);
+  W.diag = cv.take<double>(n * 3);
+  W.x0 = cv.take<double2>(n * P.ng);
+  W.gx0 = cv.take<double2>(n * P.ng);
+  W.Tm = cv.take<double2>(n * (size_t)P.ng * P.nA);
+  W.gA = cv.take<double2>(n * (size_t)P.nA * P.nA);
+  W.jv = cv.take<double2>(n * P.nA);
+  W.pv = cv.take<double2>(n * P.nA);
+  W.tauv = cv.take<double2>(n * P.nA);
+  W.dv = cv.take<double>(n * P.nA);
+  W.ev = cv.take<double>(n * P.nA);
+  W.rotcap = 6 * P.nA * P.nA + 64;
+  W.rc = cv.take<double>(n * W.rotcap);
+  W.rs = cv.take<double>(n * W.rotcap);
+  W.rk = cv.take<int>(n * W.rotcap);
+  W.MA = cv.take<double2>(n * (size_t)P.K * P.D);
+  W.MB = cv.take<double2>(n * (size_t)P.K * P.D);
+  W.info = cv.take<double>(n * 4 + 16);
+  W.Ta_out = cv.take<double2>(n * P.szT);
+  W.Tb_out = cv.take<double2>(n * P.szT);
+  W.Ta_in = cv.take<double2>(n * P.szT);
+  W.Tb_in = cv.take<double2>(n * P.szT);
+  const size_t d4 = (size_t)P.d * P.d * P.d * P.d;
+  W.G_in = cv.take<double2>(n * d4);
+  W.A = cv.take<double2>(P.szT);
+  W.B = cv.take<double2>(P.szT);
+  W.cTa = cv.take<double2>(P.szT);
+  W.cTb = cv.take<double2>(P.szT);
+  W.cA2 = cv.take<double2>(P.szT);
+  W.cB2 = cv.take<double2>(P.szT);
+  W.cG = cv.take<double2>(4 * d4);
+  W.op = cv.take<double2>(2 * (size_t)P.d * P.d);
+  W.mscr1 = cv.take<double2>(P.szT);
+  W.mscr2 = cv.take<double2>(P.szT);
+  W.medge = cv.take<double2>(4 * (size_t)P.D * P.D);
+  W.mval = cv.take<double2>(2);
+}
+}  // namespace
+
+static int check_status(ntu_ctx* c) {
+  int st = 0;
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  if (st != 0) {
+    int zero = 0;
+    cudaMemcpy(c->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    return fail(c, st, "device raised status %d (%s)", st,
+                st == NTU_ENUMERIC ? "non-finite value or solver non-convergence"
+                                   : "bounded wait ran out");
+  }
+  return NTU_OK;
+}
+
+// ------------------------------------------------------------- lifecycle
+extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, NTU_EINVAL, "ntu_init: NULL argument");
+  *out = nullptr;
+  const ntu_config& f = *cfg;
+  if (f.D < 1 || f.D > 8) return fail(nullptr, NTU_EINVAL, "D=%d outside 1..8", f.D);
+  if (f.d_phys < 2 || f.d_phys > 4) return fail(nullptr, NTU_EINVAL, "d_phys=%d outside 2..4", f.d_phys);
+  if (f.d_anc < 1 || f.d_anc > 4) return fail(nullptr, NTU_EINVAL, "d_anc=%d outside 1..4", f.d_anc);
+  if (f.r < 1 || f.r > f.d_phys * f.d_phys) return fail(nullptr, NTU_EINVAL, "r=%d outside 1..d^2", f.r);
+  if (f.D * f.r > 32) return fail(nullptr, NTU_EINVAL, "D*r=%d exceeds 32", f.D * f.r);
+  if (f.d_phys * f.d_anc * f.D * f.D < f.r)
+    return fail(nullptr, NTU_EINVAL, "d_p*D^2 < r: gated matrix has fewer rows than columns");
+  if (f.als_sweeps < 0 || f.als_sweeps > 1000) return fail(nullptr, NTU_EINVAL, "als_sweeps=%d", f.als_sweeps);
+  if (f.precision < 0 || f.precision > 2) return fail(nullptr, NTU_EINVAL, "precision=%d", f.precision);
+  if (f.precision == NTU_MIXED_BF16X3)
+    return fail(nullptr, NTU_EUNSUPPORTED, "NTU_MIXED_BF16X3 is not available in this build");
+  if (f.tau_kmin < 0 || f.tau_kmax > 20 || f.tau_kmin > f.tau_kmax)
+    return fail(nullptr, NTU_EINVAL, "tau_kmin=%d tau_kmax=%d", f.tau_kmin, f.tau_kmax);
+  if (f.max_batch < 1 || f.max_batch > 65535) return fail(nullptr, NTU_EINVAL, "max_batch=%d", f.max_batch);
+  ntu_ctx* c = new (std::nothrow) ntu_ctx();
+  if (!c) return fail(nullptr, NTU_ENOMEM, "host allocation");
+  memset(c, 0, sizeof(*c));
+  c->cfg = f;
+  c->env_es = f.precision == NTU_FP64 ? sizeof(double2) : sizeof(float2);
+  if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
+  else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { int st = cuda_check(nullptr, e, "stream"); delete c; return st; }
+    c->own_stream = true;
+  }
+  int st = plan_build(c);
+  if (st != NTU_OK) { ntu_destroy(c); return fail(nullptr, st, "plan tables"); }
+  c->w.cap = f.max_batch;
+  Carver dry;
+  carve(c, dry);
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, dry.off);
+  if (e != cudaSuccess) {
+    ntu_destroy(c);
+    return fail(nullptr, NTU_ENOMEM, "device work space of %zu bytes: %s", dry.off,
+                cudaGetErrorString(e));
+  }
+  Carver real;
+  real.base = (char*)base;
+  real.dry = false;
+  carve(c, real);
+  // carve() filled every pointer; W.GA is the first slice, i.e. the block base
+  e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e != cudaSuccess) { cudaFree(base); ntu_destroy(c); return fail(nullptr, NTU_ENOMEM, "status word"); }
+  cudaMemset(c->d_status, 0, sizeof(int));
+  cudaMemset(base, 0, dry.off);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    ntu_destroy(c);
+    return fail(nullptr, NTU_ECUDA, "device synchronize after allocation");
+  }
+  *out = c;
+  return NTU_OK;
+}
+
+extern "C" int ntu_destroy(ntu_ctx* c) {
+  if (!c) return NTU_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->w.GA) cudaFree(c->w.GA);
+  if (c->d_status) cudaFree(c->d_status);
+  for (int i = 0; i < 6; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  plan_free(c);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return NTU_OK;
+}
+
+extern "C" const char* ntu_last_error(const ntu_ctx* c) { return c ? c->err : g_noctx_err; }
+
+extern "C" int ntu_sync(ntu_ctx* c) {
+  if (!c) return fail(nullptr, NTU_EINVAL, "NULL context");
+  return check_status(c);
+}
+
+extern "C" int ntu_last_launch_count(const ntu_ctx* c) { return c ? c->launches : 0; }
+
+// ------------------------------------------------------------ unit cell
+extern "C" int ntu_set_state(ntu_ctx* c, const double* A, const double* B) {
+  if (!c || !A || !B) return fail(c, NTU_EINVAL, "ntu_set_state: NULL argument");
+  size_t bytes = c->plan.szT * sizeof(double2);
+  CK(cudaMemcpyAsync(c->w.A, A, bytes, cudaMemcpyHostToDevice, c->stream), "copy A");
+  CK(cudaMemcpyAsync(c->w.B, B, bytes, cudaMemcpyHostToDevice, c->stream), "copy B");
+  c->stage = 0;
+  return check_status(c);
+}
+
+extern "C" int ntu_get_state(ntu_ctx* c, double* A, double* B) {
+  if (!c || !A || !B) return fail(c, NTU_EINVAL, "ntu_get_state: NULL argument");
+  size_t bytes = c->plan.szT * sizeof(double2);
+  CK(cudaMemcpyAsync(A, c->w.A, bytes, cudaMemcpyDeviceToHost, c->stream), "copy A");
+  CK(cudaMemcpyAsync(B, c->w.B, bytes, cudaMemcpyDeviceToHost, c->stream), "copy B");
+  return check_status(c);
+}
+
+static int cell_gate_qr(ntu_ctx* c, int bond, const double2* gate_dev) {
+  Work& W = c->w;
+  CK(launch_orient(c, bond, W.A, W.B, W.cTa, W.cTb), "orient");
+  CK(launch_gate_qr(c, 1, W.cTa, W.cTb, gate_dev, bond >= 2 ? 1 : 0, W.QA, W.RA, W.QB, W.RB),
+     "gate + QR");
+  return NTU_OK;
+}
+
+static int cell_env(ntu_ctx* c) {
+  Work& W = c->w;
+  CK(launch_env(c, 1, W.cTa, W.cTb, W.QA, W.QB, W.graw), "environment");
+  CK(launch_repair(c, 1, W.graw, c->cfg.precision != NTU_FP64, W.g, W.diag), "repair");
+  return NTU_OK;
+}
+
+static int cell_als(ntu_ctx* c, int bond, double* info_dev) {
+  Work& W = c->w;
+  CK(launch_als(c, 1, W.g, W.RA, W.RB, W.MA, W.MB, info_dev), "ALS");
+  CK(launch_recompose(c, 1, W.QA, W.QB, W.MA, W.MB, W.cA2, W.cB2), "recompose");
+  CK(launch_deorient(c, bond, W.cA2, W.cB2, W.A, W.B), "write back");
+  return NTU_OK;
+}
+
+extern "C" int ntu_apply_gate(ntu_ctx* c, int bond, const double* gate, double* RA_out,
+                              double* RB_out) {
+  if (!c || !gate) return fail(c, NTU_EINVAL, "ntu_apply_gate: NULL argument");
+  if (bond < 0 || bond > 3) return fail(c, NTU_EINVAL, "bond=%d outside 0..3", bond);
+  const Plan& P = c->plan;
+  size_t d4 = (size_t)P.d * P.d * P.d * P.d;
+  CK(cudaMemcpyAsync(c->w.cG, gate, d4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+     "copy gate");
+  int st = cell_gate_qr(c, bond, c->w.cG);
+  if (st) return st;
+  size_t rb = P.szR * sizeof(double2);
+  if (RA_out) CK(cudaMemcpyAsync(RA_out, c->w.RA, rb, cudaMemcpyDeviceToHost, c->stream), "copy RA");
+  if (RB_out) CK(cudaMemcpyAsync(RB_out, c->w.RB, rb, cudaMemcpyDeviceToHost, c->stream), "copy RB");
+  st = check_status(c);
+  if (st) return st;
+  c->stage = 1;
+  c->stage_bond = bond;
+  return NTU_OK;
+}
+
+extern "C" int ntu_env_metric(ntu_ctx* c, int bond, double* g_out, double* diag_out) {
+  if (!c) return fail(c, NTU_EINVAL, "NULL context");
+  if (c->stage < 1 || c->stage_bond != bond)
+    return fail(c, NTU_ESTATE, "ntu_env_metric(bond=%d) needs ntu_apply_gate on that bond first", bond);
+  int st = cell_env(c);
+  if (st) return st;
+  if (g_out)
+    CK(cudaMemcpyAsync(g_out, c->w.g, c->plan.szG * sizeof(double2), cudaMemcpyDeviceToHost,
+                       c->stream), "copy g");
+  if (diag_out)
+    CK(cudaMemcpyAsync(diag_out, c->w.diag, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "copy diag");
+  st = check_status(c);
+  if (st) return st;
+  c->stage = 2;
+  return NTU_OK;
+}
+
+extern "C" int ntu_als_truncate(ntu_ctx* c, int bond, double* eps_out, double* delta_out,
+                                double* tau_out) {
+  if (!c) return fail(c, NTU_EINVAL, "NULL context");
+  if (c->stage != 2 || c->stage_bond != bond)
+    return fail(c, NTU_ESTATE, "ntu_als_truncate(bond=%d) needs ntu_env_metric on that bond first", bond);
+  double* info_dev = c->w.info + 4 * (size_t)c->w.cap;
+  int st = cell_als(c, bond, info_dev);
+  if (st) return st;
+  double info[4];
+  CK(cudaMemcpyAsync(info, info_dev, sizeof(info), cudaMemcpyDeviceToHost, c->stream), "copy info");
+  st = check_status(c);
+  c->stage = 0;
+  if (st) return st;
+  if (eps_out) *eps_out = info[0];
+  if (delta_out) *delta_out = info[1];
+  if (tau_out) *tau_out = info[3];
+  return NTU_OK;
+}
+
+extern "C" int ntu_step(ntu_ctx* c, const double* gates2, const double* gate1_half,
+                        double* delta_out) {
+  if (!c || !gates2) return fail(c, NTU_EINVAL, "ntu_step: NULL argument");
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  size_t d4 = (size_t)P.d * P.d * P.d * P.d, d2 = (size_t)P.d * P.d;
+  CK(cudaMemcpyAsync(W.cG, gates2, 4 * d4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+     "copy gates");
+  if (gate1_half) {
+    CK(cudaMemcpyAsync(W.op, gate1_half, d2 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+       "copy gate1");
+    CK(launch_site_gate(c, W.A, W.B, W.op), "site gate");
+  }
+  double* info_dev = W.info + 4 * (size_t)W.cap;
+  for (int b = 0; b < 4; ++b) {
+    int st = cell_gate_qr(c, b, W.cG + b * d4);
+    if (!st) st = cell_env(c);
+    if (!st) st = cell_als(c, b, info_dev + 4 * b);
+    if (st) return st;
+  }
+  if (gate1_half) CK(launch_site_gate(c, W.A, W.B, W.op), "site gate");
+  double info[16];
+  CK(cudaMemcpyAsync(info, info_dev, sizeof(info), cudaMemcpyDeviceToHost, c->stream), "copy info");
+  int st = check_status(c);
+  c->stage = 0;
+  if (st) return st;
+  if (delta_out)
+    for (int b = 0; b < 4; ++b) delta_out[b] = info[4 * b + 1];
+  return NTU_OK;
+}
+
+extern "C" int ntu_measure(ntu_ctx* c, int site, const double* op, double* value_out) {
+  if (!c || !op || !value_out) return fail(c, NTU_EINVAL, "ntu_measure: NULL argument");
+  if (site < 0 || site > 1) return fail(c, NTU_EINVAL, "site=%d outside 0..1", site);
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  size_t d2 = (size_t)P.d * P.d;
+  double2* opd = W.op + d2;
+  CK(cudaMemcpyAsync(opd, op, d2 * sizeof(double2), cudaMemcpyHostToDevice, c->stream), "copy op");
+  CK(launch_measure(c, site ? W.B : W.A, site ? W.A : W.B, opd, W.mval), "measure");
+  CK(cudaMemcpyAsync(value_out, W.mval, sizeof(double2), cudaMemcpyDeviceToHost, c->stream),
+     "copy value");
+  return check_status(c);
+}
+
+// ---------------------------------------------------------------- batches
+static int check_batch(ntu_ctx* c, int n) {
+  if (!c) return fail(c, NTU_EINVAL, "NULL context");
+  if (n < 0 || n > c->w.cap)
+    return fail(c, NTU_EINVAL, "n=%d outside 0..max_batch=%d", n, c->w.cap);
+  return NTU_OK;
+}
+
+extern "C" int ntu_batch_update_dev(ntu_ctx* c, int n, const double* Ta, const double* Tb,
+                                    const double* gates, double* Ta_out, double* Tb_out,
+                                    double* info) {
+  int st = check_batch(c, n);
+  if (st) return st;
+  if (n == 0) return NTU_OK;
+  if (!Ta || !Tb || !gates || !Ta_out || !Tb_out || !info)
+    return fail(c, NTU_EINVAL, "ntu_batch_update_dev: NULL argument");
+  Work& W = c->w;
+  c->launches = 0;
+  const bool prof = c->profiling != 0;
+  const double2 *ta = (const double2*)Ta, *tb = (const double2*)Tb;
+  if (prof) CK(cudaEventRecord(c->ev[0], c->stream), "event");
+  CK(launch_gate_qr(c, n, ta, tb, (const double2*)gates, 0, W.QA, W.RA, W.QB, W.RB), "gate + QR");
+  if (prof) CK(cudaEventRecord(c->ev[1], c->stream), "event");
+  CK(launch_env(c, n, ta, tb, W.QA, W.QB, W.graw), "environment");
+  if (prof) CK(cudaEventRecord(c->ev[2], c->stream), "event");
+  CK(launch_repair(c, n, W.graw, c->cfg.precision != NTU_FP64, W.g, W.diag), "repair");
+  if (prof) CK(cudaEventRecord(c->ev[3], c->stream), "event");
+  CK(launch_als(c, n, W.g, W.RA, W.RB, W.MA, W.MB, info), "ALS");
+  if (prof) CK(cudaEventRecord(c->ev[4], c->stream), "event");
+  CK(launch_recompose(c, n, W.QA, W.QB, W.MA, W.MB, (double2*)Ta_out, (double2*)Tb_out),
+     "recompose");
+  if (prof) CK(cudaEventRecord(c->ev[5], c->stream), "event");
+  return NTU_OK;
+}
+
+extern "C" int ntu_set_profiling(ntu_ctx* c, int on) {
+  if (!c) return fail(c, NTU_EINVAL, "NULL context");
+  if (on && !c->ev[0])
+    for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&c->ev[i]), "event create");
+  c->profiling = on ? 1 : 0;
+  return NTU_OK;
+}
+
+extern "C" int ntu_stage_times(ntu_ctx* c, double* ms_out) {
+  if (!c || !ms_out) return fail(c, NTU_EINVAL, "ntu_stage_times: NULL argument");
+  if (!c->profiling) return fail(c, NTU_ESTATE, "profiling is off");
+  CK(cudaEventSynchronize(c->ev[5]), "event synchronize");
+  for (int i = 0; i < 5; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]), "event elapsed");
+    ms_out[i] = ms;
+  }
+  return NTU_OK;
+}
+
+extern "C" int ntu_batch_update_host(ntu_ctx* c, int n, const double* Ta, const double* Tb,
+                                     const double* gates, double* Ta_out, double* Tb_out,
+                                     double* info) {
+  int st = check_batch(c, n);
+  if (st) return st;
+  if (n == 0) return NTU_OK;
+  if (!Ta || !Tb || !gates || !Ta_out || !Tb_out || !info)
+    return fail(c, NTU_EINVAL, "ntu_batch_update_host: NULL argument");
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  size_t tb = (size_t)n * P.szT * sizeof(double2);
+  size_t gb = (size_t)n * P.d * P.d * P.d * P.d * sizeof(double2);
+  CK(cudaMemcpyAsync(W.Ta_in, Ta, tb, cudaMemcpyHostToDevice, c->stream), "copy Ta");
+  CK(cudaMemcpyAsync(W.Tb_in, Tb, tb, cudaMemcpyHostToDevice, c->stream), "copy Tb");
+  CK(cudaMemcpyAsync(W.G_in, gates, gb, cudaMemcpyHostToDevice, c->stream), "copy gates");
+  st = ntu_batch_update_dev(c, n, (const double*)W.Ta_in, (const double*)W.Tb_in,
+                            (const double*)W.G_in, (double*)W.Ta_out, (double*)W.Tb_out, W.info);
+  if (st) return st;
+  CK(cudaMemcpyAsync(Ta_out, W.Ta_out, tb, cudaMemcpyDeviceToHost, c->stream), "copy Ta_out");
+  CK(cudaMemcpyAsync(Tb_out, W.Tb_out, tb, cudaMemcpyDeviceToHost, c->stream), "copy Tb_out");
+  CK(cudaMemcpyAsync(info, W.info, (size_t)n * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream), "copy info");
+  return check_status(c);
+}
+
+extern "C" int ntu_batch_gate_qr_dev(ntu_ctx* c, int n, const double* Ta, const double* Tb,
+                                     const double* gates, double* QA, double* RA, double* QB,
+                                     double* RB) {
+  int st = check_batch(c, n);
+  if (st || n == 0) return st;
+  if (!Ta || !Tb || !gates || !QA || !RA || !QB || !RB)
+    return fail(c, NTU_EINVAL, "ntu_batch_gate_qr_dev: NULL argument");
+  CK(launch_gate_qr(c, n, (const double2*)Ta, (const double2*)Tb, (const double2*)gates, 0,
+                    (double2*)QA, (double2*)RA, (double2*)QB, (double2*)RB), "gate + QR");
+  return NTU_OK;
+}
+
+extern "C" int ntu_batch_env_dev(ntu_ctx* c, int n, const double* Ta, const double* Tb,
+                                 const double* QA, const double* QB, double* g) {
+  int st = check_batch(c, n);
+  if (st || n == 0) return st;
+  if (!Ta || !Tb || !QA || !QB || !g) return fail(c, NTU_EINVAL, "ntu_batch_env_dev: NULL argument");
+  if (c->cfg.precision == NTU_FP64) {
+    CK(launch_env(c, n, (const double2*)Ta, (const double2*)Tb, (const double2*)QA,
+                  (const double2*)QB, g), "environment");
+  } else {
+    CK(launch_env(c, n, (const double2*)Ta, (const double2*)Tb, (const double2*)QA,
+                  (const double2*)QB, c->w.graw), "environment");
+    CK(launch_copy_raw(c, n, c->w.graw, (double2*)g), "widen g");
+  }
+  return NTU_OK;
+}
+
+extern "C" int ntu_batch_repair_dev(ntu_ctx* c, int n, double* g, double* diag) {
+  int st = check_batch(c, n);
+  if (st || n == 0) return st;
+  if (!g || !diag) return fail(c, NTU_EINVAL, "ntu_batch_repair_dev: NULL argument");
+  CK(cudaMemcpyAsync(c->w.graw, g, (size_t)n * c->plan.szG * sizeof(double2),
+                     cudaMemcpyDeviceToDevice, c->stream), "stage g");
+  CK(launch_repair(c, n, c->w.graw, 0, (double2*)g, diag), "repair");
+  return NTU_OK;
+}
+
+extern "C" int ntu_batch_als_dev(ntu_ctx* c, int n, const double* g, const double* RA,
+                                 const double* RB, double* MA, double* MB, double* info) {
+  int st = check_batch(c, n);
+  if (st || n == 0) return st;
+  if (!g || !RA || !RB || !MA || !MB || !info) return fail(c, NTU_EINVAL, "ntu_batch_als_dev: NULL argument");
+  CK(launch_als(c, n, (const double2*)g, (const double2*)RA, (const double2*)RB, (double2*)MA,
+                (double2*)MB, info), "ALS");
+  return NTU_OK;
+}
+
+extern "C" int ntu_batch_recompose_dev(ntu_ctx* c, int n, const double* QA, const double* QB,
+                                       const double* MA, const double* MB, double* Ta_out,
+                                       double* Tb_out) {
+  int st = check_batch(c, n);
+  if (st || n == 0) return st;
+  if (!QA || !QB || !MA || !MB || !Ta_out || !Tb_out)
+    return fail(c, NTU_EINVAL, "ntu_batch_recompose_dev: NULL argument");
+  CK(launch_recompose(c, n, (const double2*)QA, (const double2*)QB, (const double2*)MA,
+                      (const double2*)MB, (double2*)Ta_out, (double2*)Tb_out), "recompose");
+  return NTU_OK;
+}

@@ -1,0 +1,352 @@
+// Environment contraction of the eight-site neighbourhood (Fig. 4): edge
+// double tensors (Fig. 4(a,b)), the two half networks with the double
+// isometries (Fig. 4(c,d)) and their join into the metric g (Fig. 4(d,e)).
+// Every step is one batched complex GEMM whose operands and result are
+// addressed through separable index tables, so no permutation is ever
+// materialised.  FP64 (double2) and FP32 (float2) instantiations.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "ntu_dev.cuh"
+#include "ntu_impl.h"
+
+namespace ntu {
+
+template <typename C2> struct CplxT;
+template <> struct CplxT<double2> {
+  typedef double R;
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ static double2 mk(double a, double b) { return make_double2(a, b); }
+};
+template <> struct CplxT<float2> {
+  typedef float R;
+  __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+  __device__ static float2 mk(float a, float b) { return make_float2(a, b); }
+};
+
+struct GemmArgs {
+  int M, N, Kd;
+  const int* rowA; const int* kA; const int* kB; const int* colB; const int* rowC; const int* colC;
+  int conjA, conjB;
+  long long sA, sB, sC;
+};
+
+// Tile BM x BN per CTA, BK-deep k chunks, each thread TM x TN outputs.
+template <typename C2, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_cgemm(GemmArgs g, const C2* __restrict__ A, const C2* __restrict__ B, C2* __restrict__ C) {
+  typedef typename CplxT<C2>::R R;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ C2 As[BK][BM];
+  __shared__ C2 Bs[BK][BN];
+  __shared__ int rA[BM], cB[BN], kAs[BK], kBs[BK];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const long long b = blockIdx.z;
+  const C2* Ab = A + b * g.sA;
+  const C2* Bb = B + b * g.sB;
+  C2* Cb = C + b * g.sC;
+  for (int i = tid; i < BM; i += NT) rA[i] = (m0 + i < g.M) ? g.rowA[m0 + i] : -1;
+  for (int i = tid; i < BN; i += NT) cB[i] = (n0 + i < g.N) ? g.colB[n0 + i] : -1;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  C2 acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = CplxT<C2>::zero();
+  for (int k0 = 0; k0 < g.Kd; k0 += BK) {
+    __syncthreads();
+    for (int i = tid; i < BK; i += NT) {
+      bool ok = k0 + i < g.Kd;
+      kAs[i] = ok ? g.kA[k0 + i] : -1;
+      kBs[i] = ok ? g.kB[k0 + i] : -1;
+    }
+    __syncthreads();
+    for (int i = tid; i < BK * BM; i += NT) {
+      int kk = i / BM, mm = i % BM;
+      C2 v = CplxT<C2>::zero();
+      if (rA[mm] >= 0 && kAs[kk] >= 0) {
+        v = Ab[(long long)rA[mm] + kAs[kk]];
+        if (g.conjA) v.y = -v.y;
+      }
+      As[kk][mm] = v;
+    }
+    for (int i = tid; i < BK * BN; i += NT) {
+      int kk = i / BN, nn = i % BN;
+      C2 v = CplxT<C2>::zero();
+      if (cB[nn] >= 0 && kBs[kk] >= 0) {
+        v = Bb[(long long)kBs[kk] + cB[nn]];
+        if (g.conjB) v.y = -v.y;
+      }
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      C2 a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + j * (BN / TN)];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          R re = acc[i][j].x, im = acc[i][j].y;
+          re = fma(a[i].x, bb[j].x, re); re = fma(-a[i].y, bb[j].y, re);
+          im = fma(a[i].x, bb[j].y, im); im = fma(a[i].y, bb[j].x, im);
+          acc[i][j].x = re; acc[i][j].y = im;
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int m = m0 + ty + i * (BM / TM);
+    if (m >= g.M) continue;
+    long long rc = g.rowC[m];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int n = n0 + tx + j * (BN / TN);
+      if (n < g.N) Cb[rc + g.colC[n]] = acc[i][j];
+    }
+  }
+}
+
+template <typename C2>
+static void run_gemm(ntu_ctx* c, const GemmOp& op, int n, const void* A, const void* B, void* C) {
+  GemmArgs a;
+  const int* t = c->plan.d_tab;
+  a.M = op.M; a.N = op.N; a.Kd = op.Kd;
+  a.rowA = t + op.rowA; a.kA = t + op.kA; a.kB = t + op.kB; a.colB = t + op.colB;
+  a.rowC = t + op.rowC; a.colC = t + op.colC;
+  a.conjA = op.conjA; a.conjB = op.conjB;
+  a.sA = op.sA; a.sB = op.sB; a.sC = op.sC;
+  constexpr int BM = 64, BN = 64, TM = 4, TN = 4;
+  constexpr int BK = sizeof(C2) == 16 ? 8 : 16;
+  dim3 grid((op.N + BN - 1) / BN, (op.M + BM - 1) / BM, n);
+  k_cgemm<C2, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, c->stream>>>(
+      a, (const C2*)A, (const C2*)B, (C2*)C);
+  c->launches += 1;
+}
+
+// --------------------------------------------------------------- plan
+// Table builder: composite index -> element offset, first listed factor
+// slowest.  Each factor is (extent, stride).
+struct TabBuilder {
+  std::vector<int> tab;
+  int add(std::initializer_list<std::pair<int, long long>> f) {
+    int off = (int)tab.size();
+    std::vector<std::pair<int, long long>> v(f);
+    long long total = 1;
+    for (auto& p : v) total *= p.first;
+    for (long long i = 0; i < total; ++i) {
+      long long rem = i, o = 0;
+      for (int k = (int)v.size() - 1; k >= 0; --k) {
+        long long idx = rem % v[k].first;
+        rem /= v[k].first;
+        o += idx * v[k].second;
+      }
+      tab.push_back((int)o);
+    }
+    return off;
+  }
+};
+
+int plan_build(ntu_ctx* c) {
+  Plan& P = c->plan;
+  const ntu_config& cf = c->cfg;
+  P.D = cf.D; P.d = cf.d_phys; P.d_anc = cf.d_anc; P.dp = P.d * P.d_anc; P.r = cf.r;
+  const int D = P.D, dp = P.dp;
+  P.K = D * P.r;
+  const int K = P.K;
+  P.m = dp * D * D * D;
+  P.ng = K * K;
+  P.nA = K * D;
+  const long long D2 = D * D, D3 = D2 * D, D4 = D3 * D, K2 = (long long)K * K;
+  P.szT = dp * D4; P.szQ = (long long)P.m * K; P.szR = K2; P.szE1 = D2; P.szE2 = D4;
+  P.szS2 = D4 * K2; P.szG = K2 * K2;
+  TabBuilder T;
+  auto op = [&](int M, int N, int Kd, int rowA, int kA, int kB, int colB, int rowC, int colC,
+                int cA, int cB, long long sA, long long sB, long long sC) {
+    GemmOp o;
+    o.M = M; o.N = N; o.Kd = Kd; o.rowA = rowA; o.kA = kA; o.kB = kB; o.colB = colB;
+    o.rowC = rowC; o.colC = colC; o.conjA = cA; o.conjB = cB; o.sA = sA; o.sB = sB; o.sC = sC;
+    return o;
+  };
+  // ---- edge double tensors, Gram form E = T^T conj(T) over the closed legs
+  // E_L[x][x'] = sum_{p,l,u,n} Tb[p,l,u,x,n] conj(Tb[p,l,u,x',n])   (keeps r)
+  {
+    int rA = T.add({{D, D}});
+    int kk = T.add({{dp, D4}, {D, D3}, {D, D2}, {D, 1}});
+    int rC = T.add({{D, D}}), cC = T.add({{D, 1}});
+    P.eL = op(D, D, dp * D3, rA, kk, kk, rA, rC, cC, 0, 1, P.szT, P.szT, D2);
+  }
+  // E_R[x][x'] = sum_{p,u,r,n} Ta[p,x,u,r,n] conj(...)   (keeps l)
+  {
+    int rA = T.add({{D, D3}});
+    int kk = T.add({{dp, D4}, {D, D2}, {D, D}, {D, 1}});
+    int rC = T.add({{D, D}}), cC = T.add({{D, 1}});
+    P.eR = op(D, D, dp * D3, rA, kk, kk, rA, rC, cC, 0, 1, P.szT, P.szT, D2);
+  }
+  int rC4 = T.add({{D, D3}, {D, D2}});   // (x, y) -> (x*D + y) * D^2
+  int cC4 = T.add({{D, D}, {D, 1}});     // (x', y') -> x'*D + y'
+  // E_TL[x,y,x',y'] = sum_{p,l,u} Tb[p,l,u,x,y] conj(...)  (x = r, y = dn)
+  {
+    int rA = T.add({{D, D}, {D, 1}});
+    int kk = T.add({{dp, D4}, {D, D3}, {D, D2}});
+    P.eTL = op((int)D2, (int)D2, dp * (int)D2, rA, kk, kk, rA, rC4, cC4, 0, 1, P.szT, P.szT, D4);
+  }
+  // E_BL[x,y,x',y'] = sum_{p,l,n} Tb[p,l,y,x,n] conj(...)  (x = r, y = u)
+  {
+    int rA = T.add({{D, D}, {D, D2}});
+    int kk = T.add({{dp, D4}, {D, D3}, {D, 1}});
+    P.eBL = op((int)D2, (int)D2, dp * (int)D2, rA, kk, kk, rA, rC4, cC4, 0, 1, P.szT, P.szT, D4);
+  }
+  // E_TR[x,y,x',y'] = sum_{p,u,r} Ta[p,x,u,r,y] conj(...)  (x = l, y = dn)
+  {
+    int rA = T.add({{D, D3}, {D, 1}});
+    int kk = T.add({{dp, D4}, {D, D2}, {D, D}});
+    P.eTR = op((int)D2, (int)D2, dp * (int)D2, rA, kk, kk, rA, rC4, cC4, 0, 1, P.szT, P.szT, D4);
+  }
+  // E_BR[x,y,x',y'] = sum_{p,r,n} Ta[p,x,y,r,n] conj(...)  (x = l, y = u)
+  {
+    int rA = T.add({{D, D3}, {D, D2}});
+    int kk = T.add({{dp, D4}, {D, D}, {D, 1}});
+    P.eBR = op((int)D2, (int)D2, dp * (int)D2, rA, kk, kk, rA, rC4, cC4, 0, 1, P.szT, P.szT, D4);
+  }
+  // ---- half environment (Q rows (p, e, u, n), columns k)
+  const long long DK = D * K, D2K = D2 * K, D3K = D3 * K, DK2 = D * K2, D2K2 = D2 * K2,
+                  D3K2 = D3 * K2;
+  // Y[p,e',u,n,k] = sum_e Q[p,e,u,n,k] E_side[e,e']
+  {
+    int rA = T.add({{dp, D3K}, {D, DK}, {D, K}, {K, 1}});
+    int kA = T.add({{D, D2K}});
+    int kB = T.add({{D, D}});
+    int cB = T.add({{D, 1}});
+    int cC = T.add({{D, D2K}});
+    P.y = op(dp * (int)D2 * K, D, D, rA, kA, kB, cB, rA, cC, 0, 0, P.szQ, D2, P.szQ);
+  }
+  // T1[u,u',n,k,n',k'] = sum_{p,e'} Y[p,e',u,n,k] conj(Q[p,e',u',n',k'])
+  {
+    int rA = T.add({{D, DK}, {D, K}, {K, 1}});
+    int kk = T.add({{dp, D3K}, {D, D2K}});
+    int rC = T.add({{D, D3K2}, {D, DK2}, {K, DK}});
+    int cC = T.add({{D, D2K2}, {D, K}, {K, 1}});
+    P.t1 = op((int)D2K, (int)D2K, dp * D, rA, kk, kk, rA, rC, cC, 0, 1, P.szQ, P.szQ, P.szS2);
+  }
+  // T2[n,n',ht,ht',k,k'] = sum_{u,u'} E_top[ht,u,ht',u'] T1[u,u',n,k,n',k']
+  {
+    int rA = T.add({{D, D3}, {D, D}});
+    int kA = T.add({{D, D2}, {D, 1}});
+    int kB = T.add({{D, D3K2}, {D, D2K2}});
+    int cB = T.add({{D, DK2}, {K, DK}, {D, K}, {K, 1}});
+    int rC = T.add({{D, DK2}, {D, K2}});
+    int cC = T.add({{D, D3K2}, {K, K}, {D, D2K2}, {K, 1}});
+    P.t2 = op((int)D2, (int)D2K2, (int)D2, rA, kA, kB, cB, rC, cC, 0, 0, D4, P.szS2, P.szS2);
+  }
+  // H[hb,hb',ht,ht',k,k'] = sum_{n,n'} E_bot[hb,n,hb',n'] T2[n,n',ht,ht',k,k']
+  {
+    int rA = T.add({{D, D3}, {D, D}});
+    int kA = T.add({{D, D2}, {D, 1}});
+    int kB = T.add({{D, D3K2}, {D, D2K2}});
+    int cB = T.add({{D, DK2}, {D, K2}, {K, K}, {K, 1}});
+    int rC = T.add({{D, D3K2}, {D, D2K2}});
+    P.h = op((int)D2, (int)D2K2, (int)D2, rA, kA, kB, cB, rC, cB, 0, 0, D4, P.szS2, P.szS2);
+  }
+  // g[(k',j'),(k,j)] = sum_h HL[h,k,k'] HR[h,j,j']
+  {
+    int rA = T.add({{K, K}, {K, 1}});
+    int kk = T.add({{(int)D4, K2}});
+    int rC = T.add({{K, K}, {K, (long long)K * K2}});
+    int cC = T.add({{K, 1}, {K, K2}});
+    P.join = op((int)K2, (int)K2, (int)D4, rA, kk, kk, rA, rC, cC, 0, 0, P.szS2, P.szS2, P.szG);
+  }
+  P.n_tab = (int)T.tab.size();
+  if (cudaMalloc(&P.d_tab, sizeof(int) * P.n_tab) != cudaSuccess) return NTU_ENOMEM;
+  if (cudaMemcpy(P.d_tab, T.tab.data(), sizeof(int) * P.n_tab, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return NTU_ECUDA;
+  return NTU_OK;
+}
+
+void plan_free(ntu_ctx* c) {
+  if (c->plan.d_tab) cudaFree(c->plan.d_tab);
+  c->plan.d_tab = nullptr;
+}
+
+// --------------------------------------------------------- conversions
+__global__ void k_to_f32(long long n, const double2* __restrict__ in, float2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+static void to_f32(ntu_ctx* c, long long n, const double2* in, void* out) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_to_f32<<<(int)blocks, 256, 0, c->stream>>>(n, in, (float2*)out);
+  c->launches += 1;
+}
+
+__global__ void k_to_f64(long long n, const float2* __restrict__ in, double2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+cudaError_t launch_copy_raw(ntu_ctx* c, int n, const void* graw, double2* g) {
+  long long cnt = (long long)n * c->plan.szG;
+  long long blocks = (cnt + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_to_f64<<<(int)blocks, 256, 0, c->stream>>>(cnt, (const float2*)graw, g);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename C2>
+static void env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, const void* QA,
+                      const void* QB, void* graw) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  run_gemm<C2>(c, P.eL, n, Tb, Tb, W.EL);
+  run_gemm<C2>(c, P.eTL, n, Tb, Tb, W.ETL);
+  run_gemm<C2>(c, P.eBL, n, Tb, Tb, W.EBL);
+  run_gemm<C2>(c, P.eR, n, Ta, Ta, W.ER);
+  run_gemm<C2>(c, P.eTR, n, Ta, Ta, W.ETR);
+  run_gemm<C2>(c, P.eBR, n, Ta, Ta, W.EBR);
+  // left half: Q_A with E_L, E_TL, E_BL
+  run_gemm<C2>(c, P.y, n, QA, W.EL, W.Y);
+  run_gemm<C2>(c, P.t1, n, W.Y, QA, W.T1);
+  run_gemm<C2>(c, P.t2, n, W.ETL, W.T1, W.T2);
+  run_gemm<C2>(c, P.h, n, W.EBL, W.T2, W.HL);
+  // right half: Q_B with E_R, E_TR, E_BR
+  run_gemm<C2>(c, P.y, n, QB, W.ER, W.Y);
+  run_gemm<C2>(c, P.t1, n, W.Y, QB, W.T1);
+  run_gemm<C2>(c, P.t2, n, W.ETR, W.T1, W.T2);
+  run_gemm<C2>(c, P.h, n, W.EBR, W.T2, W.HR);
+  run_gemm<C2>(c, P.join, n, W.HL, W.HR, graw);
+}
+
+cudaError_t launch_env(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
+                       const double2* QA, const double2* QB, void* graw) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  if (c->cfg.precision == NTU_FP64) {
+    env_chain<double2>(c, n, Ta, Tb, QA, QB, graw);
+  } else {
+    to_f32(c, (long long)n * P.szT, Ta, W.Tac);
+    to_f32(c, (long long)n * P.szT, Tb, W.Tbc);
+    to_f32(c, (long long)n * P.szQ, QA, W.QAc);
+    to_f32(c, (long long)n * P.szQ, QB, W.QBc);
+    env_chain<float2>(c, n, W.Tac, W.Tbc, W.QAc, W.QBc, graw);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ntu

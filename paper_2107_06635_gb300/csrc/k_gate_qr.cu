@@ -1,0 +1,400 @@
+// Gate split, gate application and QR reduction (Fig. 2(a,b)), recomposition
+// of the updated site tensors (Fig. 2(e)), lattice orientation of the four
+// bonds, single-site Trotter gates and the cluster estimator.
+#include <cuda_runtime.h>
+
+#include "ntu_dev.cuh"
+#include "ntu_impl.h"
+
+namespace ntu {
+
+// ----------------------------------------------------------- gate split
+// X[(sA', sA), (sB', sB)] = G[sA', sB', sA, sB] = U S V^H (Fig. 2(a)); for the
+// first r singular triples G_A[:, k] = sqrt(s_k) u_k and
+// G_B[:, k] = (u_k^H X) / sqrt(s_k); components with s_k <= 1e-15 s_1 are
+// exact zeros.  With swap_sites the gate is read with its two sites
+// exchanged, G'[x', y', x, y] = G[y', x', y, x], for bonds whose left-role site
+// is B.  One CTA per item.
+__global__ void __launch_bounds__(NTU_CTA) k_gate_split(int d, int r, int swap_sites,
+                                                        const double2* __restrict__ G,
+                                                        double2* __restrict__ GA,
+                                                        double2* __restrict__ GB) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SvdSmem& S = *reinterpret_cast<SvdSmem*>(smem);
+  double2* X = reinterpret_cast<double2*>(smem + sizeof(SvdSmem));   // 16 x 16
+  const int item = blockIdx.x, tid = threadIdx.x;
+  const int dd = d * d;
+  const double2* g = G + (size_t)item * dd * dd;
+  for (int idx = tid; idx < dd * dd; idx += NTU_CTA) {
+    int row = idx / dd, col = idx % dd;
+    int a1 = row / d, a0 = row % d, b1 = col / d, b0 = col % d;
+    double2 v = swap_sites ? g[((b1 * d + a1) * d + b0) * d + a0]
+                           : g[((a1 * d + b1) * d + a0) * d + b0];
+    X[row * 16 + col] = v;
+    S.A[col * 32 + row] = v;
+  }
+  __syncthreads();
+  cta_svd_small(S, dd);
+  double2* ga = GA + (size_t)item * dd * r;
+  double2* gb = GB + (size_t)item * dd * r;
+  const double s0 = S.s[0];
+  for (int idx = tid; idx < dd * r; idx += NTU_CTA) {
+    int a = idx / r, k = idx % r;
+    bool keep = k < dd && S.s[k] > 1e-15 * s0 && s0 > 0.0;
+    double2 va = cz(), vb = cz();
+    if (keep) {
+      double sk = S.s[k], rs = sqrt(sk);
+      va = cscale(S.A[k * 32 + a], rs);
+      double2 acc = cz();
+      for (int i = 0; i < dd; ++i) acc = cfmac(S.A[k * 32 + i], X[i * 16 + a], acc);
+      vb = cscale(acc, 1.0 / rs);
+    }
+    ga[idx] = va;
+    gb[idx] = vb;
+  }
+}
+
+// ---------------------------------------------------- gated site matrices
+// Left role (side 0): M[(p', l, u, dn), (r_leg, k)] = sum_s GA[s', s, k] T[(s, c), l, u, r_leg, dn]
+// Right role (side 1): M[(p', r, u, dn), (l_leg, k)] with GB.  Column-major.
+__global__ void __launch_bounds__(NTU_CTA) k_gated(int d, int danc, int D, int r,
+                                                   const double2* __restrict__ Ta,
+                                                   const double2* __restrict__ Tb,
+                                                   const double2* __restrict__ GA,
+                                                   const double2* __restrict__ GB,
+                                                   double2* __restrict__ Mg) {
+  const int item = blockIdx.x, side = blockIdx.y;
+  const int dp = d * danc, D2 = D * D, D3 = D2 * D, D4 = D3 * D;
+  const int m = dp * D3, K = D * r;
+  const double2* T = (side ? Tb : Ta) + (size_t)item * dp * D4;
+  const double2* GX = (side ? GB : GA) + (size_t)item * d * d * r;
+  double2* out = Mg + ((size_t)item * 2 + side) * m * K;
+  for (int idx = blockIdx.z * NTU_CTA + threadIdx.x; idx < m * K; idx += NTU_CTA * gridDim.z) {
+    int col = idx / m, row = idx % m;
+    int leg = col / r, k = col % r;
+    int n_ = row % D, t = row / D;
+    int u = t % D; t /= D;
+    int e = t % D; t /= D;
+    int c = t % danc, tp = t / danc;
+    int l = side ? leg : e, w = side ? e : leg;
+    double2 acc = cz();
+    for (int s = 0; s < d; ++s)
+      acc = cfma(GX[(tp * d + s) * r + k],
+                 T[(size_t)(s * danc + c) * D4 + l * D3 + u * D2 + w * D + n_], acc);
+    out[(size_t)col * m + row] = acc;
+  }
+}
+
+// ------------------------------------------------------- Householder QR
+// Thin QR of the column-major m x K gated matrix with R's diagonal made real
+// non-negative (Fig. 2(b)).  Q is written row-major (m x K), R row-major
+// (K x K).  One CTA per (item, side).
+__global__ void __launch_bounds__(NTU_CTA) k_qr(int m, int K, double2* __restrict__ Mg,
+                                                double2* __restrict__ Qcm,
+                                                double2* __restrict__ QA, double2* __restrict__ RA,
+                                                double2* __restrict__ QB, double2* __restrict__ RB) {
+  __shared__ double2 taus[32];
+  __shared__ double betas[32];
+  __shared__ double sred[2 * NTU_WARPS];
+  const int item = blockIdx.x, side = blockIdx.y, tid = threadIdx.x;
+  const int wid = tid >> 5, lid = tid & 31;
+  double2* M = Mg + ((size_t)item * 2 + side) * m * K;
+  double2* Qc = Qcm + ((size_t)item * 2 + side) * m * K;
+  for (int j = 0; j < K; ++j) {
+    double2* col = M + (size_t)j * m;
+    double xn = 0.0;
+    for (int i = j + 1 + tid; i < m; i += NTU_CTA) xn += cabs2(col[i]);
+    xn = block_sum(xn, sred);
+    double2 alpha = col[j];
+    Reflector R = make_reflector(alpha, xn);
+    __syncthreads();
+    for (int i = j + 1 + tid; i < m; i += NTU_CTA) col[i] = cmul(col[i], R.scale);
+    if (tid == 0) { taus[j] = R.tau; betas[j] = R.beta; col[j] = make_double2(1.0, 0.0); }
+    __syncthreads();
+    if (R.tau.x != 0.0 || R.tau.y != 0.0) {
+      double2 ct = cconj(R.tau);
+      for (int c = j + 1 + wid; c < K; c += NTU_WARPS) {
+        double2* cc = M + (size_t)c * m;
+        double2 dot = cz();
+        for (int i = j + lid; i < m; i += 32) dot = cfmac(col[i], cc[i], dot);
+        dot = warp_sum2(dot);
+        double2 f = cmul(ct, dot);
+        for (int i = j + lid; i < m; i += 32) cc[i] = csub(cc[i], cmul(f, col[i]));
+      }
+      __syncthreads();
+    }
+  }
+  // Q = H_0 ... H_{K-1} [I; 0]
+  for (size_t idx = tid; idx < (size_t)m * K; idx += NTU_CTA)
+    Qc[idx] = make_double2((idx % m) == (idx / m) ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int j = K - 1; j >= 0; --j) {
+    double2 t = taus[j];
+    if (t.x == 0.0 && t.y == 0.0) continue;
+    const double2* v = M + (size_t)j * m;
+    for (int c = j + wid; c < K; c += NTU_WARPS) {
+      double2* qc = Qc + (size_t)c * m;
+      double2 dot = cz();
+      for (int i = j + lid; i < m; i += 32) dot = cfmac(v[i], qc[i], dot);
+      dot = warp_sum2(dot);
+      double2 f = cmul(t, dot);
+      for (int i = j + lid; i < m; i += 32) qc[i] = csub(qc[i], cmul(f, v[i]));
+    }
+    __syncthreads();
+  }
+  double2* Qo = (side ? QB : QA) + (size_t)item * m * K;
+  double2* Ro = (side ? RB : RA) + (size_t)item * K * K;
+  for (size_t idx = tid; idx < (size_t)m * K; idx += NTU_CTA) {
+    int i = idx / K, c = idx % K;
+    double sg = betas[c] < 0.0 ? -1.0 : 1.0;
+    Qo[idx] = cscale(Qc[(size_t)c * m + i], sg);
+  }
+  for (int idx = tid; idx < K * K; idx += NTU_CTA) {
+    int j = idx / K, c = idx % K;
+    double sg = betas[j] < 0.0 ? -1.0 : 1.0;
+    double2 v = c > j ? M[(size_t)c * m + j] : (c == j ? make_double2(betas[j], 0.0) : cz());
+    Ro[idx] = cscale(v, sg);
+  }
+}
+
+// ------------------------------------------------------------ recompose
+// T' = Q M (Fig. 2(e)) put back into [p, l, u, r, dn] and normalised.
+__global__ void __launch_bounds__(NTU_CTA) k_recompose(int dp, int D, int K,
+                                                       const double2* __restrict__ QA,
+                                                       const double2* __restrict__ QB,
+                                                       const double2* __restrict__ MA,
+                                                       const double2* __restrict__ MB,
+                                                       double2* __restrict__ TaO,
+                                                       double2* __restrict__ TbO) {
+  __shared__ double2 Ms[32 * 8];
+  __shared__ double sred[2 * NTU_WARPS];
+  const int item = blockIdx.x, side = blockIdx.y, tid = threadIdx.x;
+  const int D2 = D * D, D3 = D2 * D, D4 = D3 * D, m = dp * D3;
+  const double2* Q = (side ? QB : QA) + (size_t)item * m * K;
+  const double2* Mx = (side ? MB : MA) + (size_t)item * K * D;
+  double2* out = (side ? TbO : TaO) + (size_t)item * dp * D4;
+  for (int i = tid; i < K * D; i += NTU_CTA) Ms[i] = Mx[i];
+  __syncthreads();
+  double nrm2 = 0.0;
+  for (int idx = tid; idx < m * D; idx += NTU_CTA) {
+    int row = idx / D, a = idx % D;
+    double2 acc = cz();
+    for (int k = 0; k < K; ++k) acc = cfma(Q[(size_t)row * K + k], Ms[k * D + a], acc);
+    int n_ = row % D, t = row / D;
+    int u = t % D; t /= D;
+    int e = t % D; int p = t / D;
+    int l = side ? a : e, rr = side ? e : a;
+    out[(size_t)p * D4 + l * D3 + u * D2 + rr * D + n_] = acc;
+    nrm2 += cabs2(acc);
+  }
+  double nrm = sqrt(block_sum(nrm2, sred));
+  double sc = nrm > 0.0 ? 1.0 / nrm : 1.0;
+  __syncthreads();
+  for (int idx = tid; idx < dp * D4; idx += NTU_CTA) out[idx] = cscale(out[idx], sc);
+}
+
+// ------------------------------------------------------------ orientation
+// Bond b -> bond-0 orientation: bonds 1 and 3 rotate the lattice clockwise
+// (new (l, u, r, dn) = old (dn, l, u, r)); bonds 2 and 3 put B in the left role.
+__global__ void k_orient(int dp, int D, int bond, const double2* __restrict__ A,
+                         const double2* __restrict__ B, double2* __restrict__ Ta,
+                         double2* __restrict__ Tb) {
+  const int D2 = D * D, D3 = D2 * D, D4 = D3 * D;
+  const bool rot = (bond == 1 || bond == 3), swp = (bond >= 2);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < dp * D4; idx += gridDim.x * blockDim.x) {
+    int i4 = idx % D, t = idx / D;
+    int i3 = t % D; t /= D;
+    int i2 = t % D; t /= D;
+    int i1 = t % D; int p = t / D;
+    int src = rot ? (p * D4 + i2 * D3 + i3 * D2 + i4 * D + i1) : idx;
+    Ta[idx] = swp ? B[src] : A[src];
+    Tb[idx] = swp ? A[src] : B[src];
+  }
+}
+
+__global__ void k_deorient(int dp, int D, int bond, const double2* __restrict__ Ta,
+                           const double2* __restrict__ Tb, double2* __restrict__ A,
+                           double2* __restrict__ B) {
+  const int D2 = D * D, D3 = D2 * D, D4 = D3 * D;
+  const bool rot = (bond == 1 || bond == 3), swp = (bond >= 2);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < dp * D4; idx += gridDim.x * blockDim.x) {
+    int i4 = idx % D, t = idx / D;
+    int i3 = t % D; t /= D;
+    int i2 = t % D; t /= D;
+    int i1 = t % D; int p = t / D;
+    int src = rot ? (p * D4 + i4 * D3 + i1 * D2 + i2 * D + i3) : idx;
+    A[idx] = swp ? Tb[src] : Ta[src];
+    B[idx] = swp ? Ta[src] : Tb[src];
+  }
+}
+
+// ---------------------------------------------------- single-site gates
+// T <- (O (x) 1_anc) T on the physical factor, then unit norm.  Block 0: A,
+// block 1: B.
+__global__ void __launch_bounds__(NTU_CTA) k_site_gate(int d, int danc, int D,
+                                                       double2* __restrict__ A,
+                                                       double2* __restrict__ B,
+                                                       const double2* __restrict__ op) {
+  __shared__ double2 O[16];
+  __shared__ double sred[2 * NTU_WARPS];
+  double2* T = blockIdx.x ? B : A;
+  const int tid = threadIdx.x;
+  const int D4 = D * D * D * D, dp = d * danc;
+  if (tid < d * d) O[tid] = op[tid];
+  __syncthreads();
+  double nrm2 = 0.0;
+  for (int idx = tid; idx < danc * D4; idx += NTU_CTA) {
+    int c = idx / D4, rest = idx % D4;
+    double2 in[4], o[4];
+    for (int s = 0; s < d; ++s) in[s] = T[(size_t)(s * danc + c) * D4 + rest];
+    for (int t = 0; t < d; ++t) {
+      double2 acc = cz();
+      for (int s = 0; s < d; ++s) acc = cfma(O[t * d + s], in[s], acc);
+      o[t] = acc;
+      nrm2 += cabs2(acc);
+    }
+    for (int t = 0; t < d; ++t) T[(size_t)(t * danc + c) * D4 + rest] = o[t];
+  }
+  double nrm = sqrt(block_sum(nrm2, sred));
+  double sc = nrm > 0.0 ? 1.0 / nrm : 1.0;
+  __syncthreads();
+  for (int idx = tid; idx < dp * D4; idx += NTU_CTA) T[idx] = cscale(T[idx], sc);
+}
+
+// ------------------------------------------------------ cluster estimator
+// <O> on site T with its four neighbours N closed by their leaf edge
+// tensors, over the same network with the identity.  out[0] = num / den.
+__global__ void __launch_bounds__(NTU_CTA) k_measure(int d, int danc, int D,
+                                                     const double2* __restrict__ T,
+                                                     const double2* __restrict__ N,
+                                                     const double2* __restrict__ op,
+                                                     double2* __restrict__ S1,
+                                                     double2* __restrict__ S2,
+                                                     double2* __restrict__ E,
+                                                     double2* __restrict__ out) {
+  __shared__ double sred[2 * NTU_WARPS];
+  const int tid = threadIdx.x;
+  const int dp = d * danc, D2 = D * D, D3 = D2 * D, D4 = D3 * D;
+  // leaf edge tensors: El keeps r, Eu keeps dn, Er keeps l, Ed keeps u
+  for (int idx = tid; idx < 4 * D2; idx += NTU_CTA) {
+    int which = idx / D2, x = (idx % D2) / D, y = idx % D;
+    double2 acc = cz();
+    for (int p = 0; p < dp; ++p)
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b)
+          for (int c = 0; c < D; ++c) {
+            size_t ix, iy, base = (size_t)p * D4;
+            if (which == 0) { ix = base + a * D3 + b * D2 + x * D + c; iy = base + a * D3 + b * D2 + y * D + c; }
+            else if (which == 1) { ix = base + a * D3 + b * D2 + c * D + x; iy = base + a * D3 + b * D2 + c * D + y; }
+            else if (which == 2) { ix = base + x * D3 + a * D2 + b * D + c; iy = base + y * D3 + a * D2 + b * D + c; }
+            else { ix = base + a * D3 + x * D2 + b * D + c; iy = base + a * D3 + y * D2 + b * D + c; }
+            acc = cfma(N[ix], cconj(N[iy]), acc);
+          }
+    E[idx] = acc;
+  }
+  __syncthreads();
+  // contract the four legs of T one at a time: S <- sum_leg S * E_leg[leg, leg']
+  const double2* src = T;
+  double2* bufs[2] = {S1, S2};
+  for (int leg = 0; leg < 4; ++leg) {
+    double2* dst = bufs[leg & 1];
+    const double2* El = E + leg * D2;      // leg 0: l uses El (keeps r), 1: u/Eu, 2: r/Er, 3: dn/Ed
+    int stride = leg == 0 ? D3 : leg == 1 ? D2 : leg == 2 ? D : 1;
+    for (int idx = tid; idx < dp * D4; idx += NTU_CTA) {
+      int a = (idx / stride) % D;
+      int base = idx - a * stride;
+      double2 acc = cz();
+      for (int x = 0; x < D; ++x) acc = cfma(src[base + x * stride], El[x * D + a], acc);
+      dst[idx] = acc;
+    }
+    __syncthreads();
+    src = dst;
+  }
+  // num = sum conj(T[q..]) O_full[q, p] V[p..]; den = sum conj(T[p..]) V[p..]
+  double2 num = cz(), den = cz();
+  for (int idx = tid; idx < dp * D4; idx += NTU_CTA) {
+    int p = idx / D4, rest = idx % D4;
+    int s = p / danc, c = p % danc;
+    double2 v = src[idx];
+    den = cfmac(T[idx], v, den);
+    for (int t = 0; t < d; ++t) {
+      double2 ov = cmul(op[t * d + s], v);
+      num = cfmac(T[(size_t)(t * danc + c) * D4 + rest], ov, num);
+    }
+  }
+  num = block_sum2(num, sred);
+  den = block_sum2(den, sred);
+  if (tid == 0) out[0] = cdiv(num, den);
+}
+
+// ------------------------------------------------------------ launchers
+static inline int grid_for(long long work) {
+  long long b = (work + NTU_CTA - 1) / NTU_CTA;
+  return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
+
+cudaError_t launch_gate_qr(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
+                           const double2* G, int swap_sites, double2* QA, double2* RA,
+                           double2* QB, double2* RB) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  size_t sm = sizeof(SvdSmem) + 16 * 16 * sizeof(double2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gate_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  k_gate_split<<<n, NTU_CTA, sm, c->stream>>>(P.d, P.r, swap_sites, G, W.GA, W.GB);
+  int zsplit = (P.m * P.K + NTU_CTA * 8 - 1) / (NTU_CTA * 8);
+  if (zsplit < 1) zsplit = 1;
+  k_gated<<<dim3(n, 2, zsplit), NTU_CTA, 0, c->stream>>>(P.d, P.d_anc, P.D, P.r, Ta, Tb, W.GA,
+                                                         W.GB, W.Mg);
+  k_qr<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.m, P.K, W.Mg, W.Qcm, QA, RA, QB, RB);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recompose(ntu_ctx* c, int n, const double2* QA, const double2* QB,
+                             const double2* MA, const double2* MB, double2* Ta_out,
+                             double2* Tb_out) {
+  const Plan& P = c->plan;
+  k_recompose<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.dp, P.D, P.K, QA, QB, MA, MB, Ta_out,
+                                                     Tb_out);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orient(ntu_ctx* c, int bond, const double2* A, const double2* B,
+                          double2* Ta, double2* Tb) {
+  const Plan& P = c->plan;
+  k_orient<<<grid_for(P.szT), NTU_CTA, 0, c->stream>>>(P.dp, P.D, bond, A, B, Ta, Tb);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deorient(ntu_ctx* c, int bond, const double2* Ta, const double2* Tb,
+                            double2* A, double2* B) {
+  const Plan& P = c->plan;
+  k_deorient<<<grid_for(P.szT), NTU_CTA, 0, c->stream>>>(P.dp, P.D, bond, Ta, Tb, A, B);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_site_gate(ntu_ctx* c, double2* A, double2* B, const double2* op) {
+  const Plan& P = c->plan;
+  k_site_gate<<<2, NTU_CTA, 0, c->stream>>>(P.d, P.d_anc, P.D, A, B, op);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_measure(ntu_ctx* c, const double2* T, const double2* N, const double2* op,
+                           double2* out) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  k_measure<<<1, NTU_CTA, 0, c->stream>>>(P.d, P.d_anc, P.D, T, N, op, W.mscr1, W.mscr2,
+                                          W.medge, out);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace ntu

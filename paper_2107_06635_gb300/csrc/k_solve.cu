@@ -1,0 +1,414 @@
+// FP64 solvers of the bond update: Hermitisation and non-negativity repair
+// of the metric g (Sec. II), and the ALS truncation of Fig. 5 / Eqs. 2-5
+// (SVDU start, tilting, reduced metric and source, pseudo-inverse with the
+// tolerance that minimises eps, balancing).  One CTA per bond update.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ntu_dev.cuh"
+#include "ntu_impl.h"
+
+namespace ntu {
+
+__device__ __forceinline__ double2 ld2(const double2* p) { return *p; }
+__device__ __forceinline__ double2 ld2(const float2* p) {
+  float2 v = *p;
+  return make_double2((double)v.x, (double)v.y);
+}
+
+// ------------------------------------------------------------- repair
+// g <- (g + g^H)/2; if a Cholesky factorisation of g succeeds, g is
+// positive definite and clipping its negative eigenvalues would change
+// nothing; otherwise g = W diag(max(lambda, 0)) W^H from a full
+// eigendecomposition.  Finally g /= trace(g).
+// diag = [||g - g^H|| / ||g||, lambda_min / lambda_max (NaN on the Cholesky
+// path), log(trace)].
+template <typename C2in>
+__global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restrict__ graw,
+                                                    double2* __restrict__ g,
+                                                    double2* __restrict__ scr,
+                                                    double2* __restrict__ Wv,
+                                                    double* __restrict__ Z,
+                                                    double* __restrict__ de,
+                                                    double2* __restrict__ tau,
+                                                    double2* __restrict__ pv,
+                                                    double* __restrict__ diag, int* status) {
+  extern __shared__ double chain[];      // 2 * ng
+  __shared__ double sred[2 * NTU_WARPS];
+  __shared__ int sh[4];
+  __shared__ int ok;
+  const int tid = threadIdx.x;
+  const long long item = blockIdx.x;
+  const size_t nn = (size_t)ng * ng;
+  const C2in* gr = graw + item * nn;
+  double2* gi = g + item * nn;
+  double2* sc = scr + item * nn;
+  // 1. Hermitise
+  double n2 = 0.0, h2 = 0.0;
+  for (size_t idx = tid; idx < nn; idx += NTU_CTA) {
+    int r = idx / ng, c = idx % ng;
+    double2 a = ld2(gr + idx), b = ld2(gr + (size_t)c * ng + r);
+    double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    n2 += cabs2(a);
+    h2 += cabs2(make_double2(a.x - b.x, a.y + b.y));
+    gi[idx] = h;
+    sc[(size_t)c * ng + r] = h;          // column-major copy
+  }
+  n2 = block_sum(n2, sred);
+  h2 = block_sum(h2, sred);
+  const double herm = n2 > 0.0 ? sqrt(h2 / n2) : 0.0;
+  // 2. Cholesky of the lower triangle (column-major, right-looking)
+  if (tid == 0) ok = 1;
+  __syncthreads();
+  for (int j = 0; j < ng; ++j) {
+    double piv = sc[(size_t)j * ng + j].x;
+    if (!(piv > 0.0) || !isfinite(piv)) { if (tid == 0) ok = 0; break; }
+    double rp = 1.0 / sqrt(piv);
+    double2* cj = sc + (size_t)j * ng;
+    for (int i = j + 1 + tid; i < ng; i += NTU_CTA) cj[i] = cscale(cj[i], rp);
+    __syncthreads();
+    const int m = ng - j - 1;
+    for (int idx = tid; idx < m * m; idx += NTU_CTA) {
+      int kk = idx / m, ii = idx % m;
+      if (ii < kk) continue;
+      int k = j + 1 + kk, i = j + 1 + ii;
+      double2* ck = sc + (size_t)k * ng;
+      ck[i] = csub(ck[i], cmul(cj[i], cconj(cj[k])));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  double ratio = __longlong_as_double(0x7ff8000000000000ULL);   // NaN
+  if (!ok) {
+    // 3. full eigendecomposition and clipping of negative eigenvalues
+    double2* ta = tau + item * ng;
+    double2* pp = pv + item * ng;
+    double* dd = de + item * 2 * ng;
+    double* ee = dd + ng;
+    double* Zi = Z + item * nn;
+    double2* Wi = Wv + item * nn;
+    for (size_t idx = tid; idx < nn; idx += NTU_CTA) {
+      int r = idx / ng, c = idx % ng;
+      sc[(size_t)c * ng + r] = gi[idx];
+    }
+    __syncthreads();
+    cta_hetrd(sc, ng, dd, ee, ta, pp, sred);
+    int st = cta_tridiag_qr_z(dd, ee, ng, Zi, chain, sh);
+    if (st && tid == 0) raise_status(status, st);
+    // W = Q Z, one column per thread
+    for (int k = tid; k < ng; k += NTU_CTA) {
+      double2* col = Wi + (size_t)k * ng;
+      for (int i = 0; i < ng; ++i) col[i] = make_double2(Zi[(size_t)i * ng + k], 0.0);
+      for (int j = ng - 2; j >= 0; --j) {
+        double2 t = ta[j];
+        if (t.x == 0.0 && t.y == 0.0) continue;
+        const double2* v = sc + (size_t)j * ng + j + 1;
+        int m = ng - j - 1;
+        double2 s = cz();
+        for (int i = 0; i < m; ++i) s = cfmac(i == 0 ? make_double2(1.0, 0.0) : v[i], col[j + 1 + i], s);
+        double2 f = cmul(t, s);
+        for (int i = 0; i < m; ++i)
+          col[j + 1 + i] = csub(col[j + 1 + i], cmul(f, i == 0 ? make_double2(1.0, 0.0) : v[i]));
+      }
+    }
+    __syncthreads();
+    double lmin = dd[0], lmax = dd[0];
+    for (int i = 1; i < ng; ++i) { lmin = fmin(lmin, dd[i]); lmax = fmax(lmax, dd[i]); }
+    ratio = lmax > 0.0 ? lmin / lmax : 0.0;
+    for (size_t idx = tid; idx < nn; idx += NTU_CTA) {
+      int r = idx / ng, c = idx % ng;
+      double2 acc = cz();
+      for (int k = 0; k < ng; ++k) {
+        double lk = dd[k];
+        if (lk <= 0.0) continue;
+        acc = cfma(cscale(Wi[(size_t)k * ng + r], lk), cconj(Wi[(size_t)k * ng + c]), acc);
+      }
+      gi[idx] = acc;
+    }
+    __syncthreads();
+  }
+  // 4. unit trace
+  double tr = 0.0;
+  for (int i = tid; i < ng; i += NTU_CTA) tr += gi[(size_t)i * ng + i].x;
+  tr = block_sum(tr, sred);
+  if (!(tr > 0.0) || !isfinite(tr)) {
+    if (tid == 0) raise_status(status, ST_NUMERIC);
+    tr = 1.0;
+  }
+  const double inv = 1.0 / tr;
+  for (size_t idx = tid; idx < nn; idx += NTU_CTA) gi[idx] = cscale(gi[idx], inv);
+  if (tid == 0) {
+    diag[item * 3 + 0] = herm;
+    diag[item * 3 + 1] = ratio;
+    diag[item * 3 + 2] = log(tr);
+  }
+}
+
+// ---------------------------------------------------------------- ALS
+struct AlsShared {
+  SvdSmem S;
+  double2 MA[32 * 8];
+  double2 MB[32 * 8];
+  double2 y[256];
+  double red[2 * NTU_WARPS];
+  double eps0, tau_sel;
+  int err;
+};
+
+struct AlsArgs {
+  int D, K, ng, nA, sweeps, kmin, kmax;
+  const double2* g; const double2* RA; const double2* RB;
+  double2* MA; double2* MB; double* info;
+  double2 *x0, *gx0, *Tm, *gA, *jv, *pv, *tauv;
+  double *dv, *ev, *rc, *rs;
+  int* rk;
+  int rotcap;
+  int* status;
+};
+
+// X = MA MB^T -> SVD -> (MA, MB) by mode: 0 tilt before the A step
+// (U S, conj(V)), 1 tilt before the B step (U, conj(V) S), 2 balance
+// (U sqrt(S), conj(V) sqrt(S)).  With from_x0 the SVD input is X0 instead.
+__device__ void als_tilt(AlsShared& sm, const AlsArgs& a, int mode, const double2* X0) {
+  const int tid = threadIdx.x, K = a.K, D = a.D;
+  for (int idx = tid; idx < 32 * 32; idx += NTU_CTA) {
+    int i = idx & 31, j = idx >> 5;
+    double2 v = cz();
+    if (i < K && j < K) {
+      if (X0) v = X0[i * K + j];
+      else
+        for (int q = 0; q < D; ++q) v = cfma(sm.MA[i * D + q], sm.MB[j * D + q], v);
+    }
+    sm.S.A[j * 32 + i] = v;
+  }
+  __syncthreads();
+  cta_svd_small(sm.S, K);
+  for (int idx = tid; idx < K * D; idx += NTU_CTA) {
+    int i = idx / D, q = idx % D;
+    double2 u = cz(), vb = cz();
+    double sv = 0.0;
+    if (q < K) { u = sm.S.A[q * 32 + i]; vb = cconj(sm.S.V[q * 32 + i]); sv = sm.S.s[q]; }
+    if (mode == 0) { sm.MA[idx] = cscale(u, sv); sm.MB[idx] = vb; }
+    else if (mode == 1) { sm.MA[idx] = u; sm.MB[idx] = cscale(vb, sv); }
+    else { double rs = sqrt(sv); sm.MA[idx] = cscale(u, rs); sm.MB[idx] = cscale(vb, rs); }
+  }
+  __syncthreads();
+}
+
+// Reduced metric and source for the free side (Fig. 5(b,c)).  side 0: the
+// A step, free index i of (i, j), fixed F = MB; side 1: the B step, free j,
+// F = MA.  gX is written column-major (nA x nA), J into a.jv.
+__device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, int side,
+                            double2* Tm, double2* gX, double2* jv, const double2* gx0) {
+  const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
+  const double2* F = side == 0 ? sm.MB : sm.MA;
+  const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
+  // Tm[r][(f,q)] = sum_c g[r][f*sf + c*sc] F[c][q]
+  for (int idx = tid; idx < ng * nA; idx += NTU_CTA) {
+    int r = idx / nA, fq = idx % nA, f = fq / D, q = fq % D;
+    const double2* gr = g + (size_t)r * ng + f * sf;
+    double2 acc = cz();
+    for (int c = 0; c < K; ++c) acc = cfma(gr[c * sc], F[c * D + q], acc);
+    Tm[idx] = acc;
+  }
+  __syncthreads();
+  // gX[(f',q'),(f,q)] = sum_c' conj(F[c'][q']) Tm[f'*sf + c'*sc][(f,q)]
+  for (int idx = tid; idx < nA * nA; idx += NTU_CTA) {
+    int col = idx / nA, row = idx % nA, f1 = row / D, q1 = row % D;
+    double2 acc = cz();
+    for (int c = 0; c < K; ++c)
+      acc = cfmac(F[c * D + q1], Tm[(size_t)(f1 * sf + c * sc) * nA + col], acc);
+    gX[idx] = acc;
+  }
+  for (int row = tid; row < nA; row += NTU_CTA) {
+    int f1 = row / D, q1 = row % D;
+    double2 acc = cz();
+    for (int c = 0; c < K; ++c) acc = cfmac(F[c * D + q1], gx0[f1 * sf + c * sc], acc);
+    jv[row] = acc;
+  }
+  __syncthreads();
+}
+
+// M = pinv_tau(gX) J with the tolerance of the grid that minimises
+// eps(tau) = eps0 - sum_{lambda_i > tau lambda_max} |y_i|^2 / lambda_i,
+// y = W^H J (Eq. 4 inserted in Eq. 3); ties within 1e-14 eps0 go to the
+// larger tau.  The result is written to sm.MA (side 0) or sm.MB (side 1).
+__device__ void als_solve(AlsShared& sm, const AlsArgs& a, int side, double2* gX,
+                          const double2* jv, double2* pv, double2* tauv, double* dv, double* ev,
+                          RotLog& log) {
+  const int tid = threadIdx.x, nA = a.nA;
+  for (int i = tid; i < nA; i += NTU_CTA) sm.y[i] = jv[i];
+  __syncthreads();
+  cta_hetrd(gX, nA, dv, ev, tauv, pv, sm.red);
+  cta_apply_q(gX, nA, tauv, sm.y, true, sm.red);
+  if (tid == 0) {
+    int st = tridiag_qr(dv, ev, nA, log, sm.y);
+    if (st) sm.err = st;
+    double lmax = dv[0];
+    for (int i = 1; i < nA; ++i) lmax = fmax(lmax, dv[i]);
+    const double taus[21] = {1e0,   1e-1,  1e-2,  1e-3,  1e-4,  1e-5,  1e-6,
+                             1e-7,  1e-8,  1e-9,  1e-10, 1e-11, 1e-12, 1e-13,
+                             1e-14, 1e-15, 1e-16, 1e-17, 1e-18, 1e-19, 1e-20};
+    int kmin = a.kmin < 0 ? 0 : a.kmin, kmax = a.kmax > 20 ? 20 : a.kmax;
+    double tsel = taus[kmin];
+    if (lmax > 0.0 && !st) {
+      double emin = INFINITY;
+      for (int k = kmin; k <= kmax; ++k) {
+        double thr = taus[k] * lmax, s = 0.0;
+        for (int i = 0; i < nA; ++i)
+          if (dv[i] > thr) s += cabs2(sm.y[i]) / dv[i];
+        emin = fmin(emin, sm.eps0 - s);
+      }
+      for (int k = kmin; k <= kmax; ++k) {
+        double thr = taus[k] * lmax, s = 0.0;
+        for (int i = 0; i < nA; ++i)
+          if (dv[i] > thr) s += cabs2(sm.y[i]) / dv[i];
+        if (sm.eps0 - s <= emin + 1e-14 * sm.eps0) { tsel = taus[k]; break; }
+      }
+      double thr = tsel * lmax;
+      for (int i = 0; i < nA; ++i)
+        sm.y[i] = dv[i] > thr ? cscale(sm.y[i], 1.0 / dv[i]) : cz();
+      rotlog_apply_z(log, sm.y);
+    } else {
+      for (int i = 0; i < nA; ++i) sm.y[i] = cz();
+    }
+    sm.tau_sel = tsel;
+  }
+  __syncthreads();
+  cta_apply_q(gX, nA, tauv, sm.y, false, sm.red);
+  double2* M = side == 0 ? sm.MA : sm.MB;
+  for (int i = tid; i < nA; i += NTU_CTA) M[i] = sm.y[i];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AlsShared& sm = *reinterpret_cast<AlsShared*>(smem_raw);
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
+  const long long item = blockIdx.x;
+  const int K = a.K, D = a.D, ng = a.ng, nA = a.nA;
+  const double2* g = a.g + item * (long long)ng * ng;
+  const double2* RA = a.RA + item * K * K;
+  const double2* RB = a.RB + item * K * K;
+  double2* x0 = a.x0 + item * ng;
+  double2* gx0 = a.gx0 + item * ng;
+  double2* Tm = a.Tm + item * (long long)ng * nA;
+  double2* gX = a.gA + item * (long long)nA * nA;
+  double2* jv = a.jv + item * nA;
+  double2* pv = a.pv + item * nA;
+  double2* tauv = a.tauv + item * nA;
+  double* dv = a.dv + item * nA;
+  double* ev = a.ev + item * nA;
+  RotLog log;
+  log.c = a.rc + item * (long long)a.rotcap;
+  log.s = a.rs + item * (long long)a.rotcap;
+  log.k = a.rk + item * (long long)a.rotcap;
+  log.cap = a.rotcap;
+  log.count = 0;
+  if (tid == 0) sm.err = 0;
+  // X0 = R_A R_B^T, x0 = vec(X0) with kA slow
+  for (int idx = tid; idx < K * K; idx += NTU_CTA) {
+    int i = idx / K, j = idx % K;
+    double2 acc = cz();
+    for (int b = 0; b < K; ++b) acc = cfma(RA[i * K + b], RB[j * K + b], acc);
+    x0[idx] = acc;
+  }
+  __syncthreads();
+  // gx0 = g x0, eps0 = x0^H g x0
+  double e0 = 0.0;
+  for (int r = wid; r < ng; r += NTU_WARPS) {
+    const double2* gr = g + (size_t)r * ng;
+    double2 acc = cz();
+    for (int c = lid; c < ng; c += 32) acc = cfma(gr[c], x0[c], acc);
+    acc = warp_sum2(acc);
+    if (lid == 0) {
+      gx0[r] = acc;
+      e0 += cmulc(x0[r], acc).x;
+    }
+  }
+  e0 = block_sum(e0, sm.red);
+  if (tid == 0) sm.eps0 = e0;
+  __syncthreads();
+  // SVDU start (Fig. 2(c,d))
+  als_tilt(sm, a, 2, x0);
+  for (int s = 0; s < a.sweeps; ++s) {
+    als_tilt(sm, a, 0, nullptr);
+    als_reduced(sm, a, g, 0, Tm, gX, jv, gx0);
+    als_solve(sm, a, 0, gX, jv, pv, tauv, dv, ev, log);
+    als_tilt(sm, a, 1, nullptr);
+    als_reduced(sm, a, g, 1, Tm, gX, jv, gx0);
+    als_solve(sm, a, 1, gX, jv, pv, tauv, dv, ev, log);
+  }
+  als_tilt(sm, a, 2, nullptr);      // balance (Fig. 5(d))
+  // eps = x^H g x, x = vec(MA MB^T) - x0
+  double2* xv = Tm;
+  for (int idx = tid; idx < ng; idx += NTU_CTA) {
+    int i = idx / K, j = idx % K;
+    double2 acc = cz();
+    for (int q = 0; q < D; ++q) acc = cfma(sm.MA[i * D + q], sm.MB[j * D + q], acc);
+    xv[idx] = csub(acc, x0[idx]);
+  }
+  __syncthreads();
+  double eps = 0.0;
+  for (int r = wid; r < ng; r += NTU_WARPS) {
+    const double2* gr = g + (size_t)r * ng;
+    double2 acc = cz();
+    for (int c = lid; c < ng; c += 32) acc = cfma(gr[c], xv[c], acc);
+    acc = warp_sum2(acc);
+    if (lid == 0) eps += cmulc(xv[r], acc).x;
+  }
+  eps = block_sum(eps, sm.red);
+  double2* MAo = a.MA + item * K * D;
+  double2* MBo = a.MB + item * K * D;
+  for (int idx = tid; idx < K * D; idx += NTU_CTA) { MAo[idx] = sm.MA[idx]; MBo[idx] = sm.MB[idx]; }
+  if (tid == 0) {
+    double e0v = sm.eps0;
+    double delta = e0v > 0.0 ? eps / e0v : 0.0;
+    a.info[item * 4 + 0] = eps;
+    a.info[item * 4 + 1] = delta;
+    a.info[item * 4 + 2] = e0v;
+    a.info[item * 4 + 3] = sm.tau_sel;
+    if (sm.err || !isfinite(delta) || !isfinite(eps)) raise_status(a.status, ST_NUMERIC);
+  }
+}
+
+size_t als_smem_bytes() { return sizeof(AlsShared); }
+
+cudaError_t launch_repair(ntu_ctx* c, int n, const void* graw, int raw_is_f32, double2* g,
+                          double* diag) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  size_t sm = 2 * sizeof(double) * P.ng;
+  if (raw_is_f32) {
+    cudaFuncSetAttribute(k_repair<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_repair<float2><<<n, NTU_CTA, sm, c->stream>>>(P.ng, (const float2*)graw, g, W.gscr, W.gw,
+                                                    W.gz, W.geig, W.gtau, W.gp, diag, c->d_status);
+  } else {
+    cudaFuncSetAttribute(k_repair<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_repair<double2><<<n, NTU_CTA, sm, c->stream>>>(P.ng, (const double2*)graw, g, W.gscr,
+                                                     W.gw, W.gz, W.geig, W.gtau, W.gp, diag,
+                                                     c->d_status);
+  }
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
+                       const double2* RB, double2* MA, double2* MB, double* info) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  AlsArgs a;
+  a.D = P.D; a.K = P.K; a.ng = P.ng; a.nA = P.nA; a.sweeps = c->cfg.als_sweeps;
+  a.kmin = c->cfg.tau_kmin; a.kmax = c->cfg.tau_kmax;
+  a.g = g; a.RA = RA; a.RB = RB; a.MA = MA; a.MB = MB; a.info = info;
+  a.x0 = W.x0; a.gx0 = W.gx0; a.Tm = W.Tm; a.gA = W.gA; a.jv = W.jv; a.pv = W.pv;
+  a.tauv = W.tauv; a.dv = W.dv; a.ev = W.ev; a.rc = W.rc; a.rs = W.rs; a.rk = W.rk;
+  a.rotcap = W.rotcap; a.status = c->d_status;
+  size_t sm = sizeof(AlsShared);
+  cudaFuncSetAttribute(k_als, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_als<<<n, NTU_CTA, sm, c->stream>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace ntu

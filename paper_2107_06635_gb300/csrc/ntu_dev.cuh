@@ -1,0 +1,486 @@
+// Device-side numerics shared by the NTU kernels: complex helpers, CTA
+// reductions and the small dense linear-algebra routines of the bond update
+// (one-sided Jacobi SVD, Householder QR / Hermitian tridiagonalisation,
+// implicit symmetric tridiagonal QR).  All CTA routines assume
+// blockDim.x == NTU_CTA threads.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define NTU_CTA 256
+#define NTU_WARPS (NTU_CTA / 32)
+
+namespace ntu {
+
+// ------------------------------------------------------------------ complex
+__device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+// a * b + c
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+// conj(a) * b + c
+__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x); c.x = fma(a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y); c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double den = cabs2(b);
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+// --------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum over the CTA; every thread gets the result.  sbuf: >= NTU_WARPS*2 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sbuf) {
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sbuf[w] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < NTU_WARPS; ++i) t += sbuf[i];
+  return t;
+}
+__device__ __forceinline__ double2 block_sum2(double2 v, double* sbuf) {
+  v = warp_sum2(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sbuf[2 * w] = v.x; sbuf[2 * w + 1] = v.y; }
+  __syncthreads();
+  double2 t = cz();
+#pragma unroll
+  for (int i = 0; i < NTU_WARPS; ++i) { t.x += sbuf[2 * i]; t.y += sbuf[2 * i + 1]; }
+  return t;
+}
+__device__ __forceinline__ double block_max(double v, double* sbuf) {
+  v = warp_max(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sbuf[w] = v;
+  __syncthreads();
+  double t = sbuf[0];
+#pragma unroll
+  for (int i = 1; i < NTU_WARPS; ++i) t = fmax(t, sbuf[i]);
+  return t;
+}
+
+// Error codes a kernel may raise through the status word (same values as
+// ntu_status in include/ntu.h).
+enum { ST_NUMERIC = 4, ST_TIMEOUT = 5 };
+__device__ __forceinline__ void raise_status(int* status, int code) {
+  if (status) atomicMax(status, code);
+}
+
+// ------------------------------------------------- Householder reflectors
+// Reflector H = I - tau v v^H with v = [1; x/(alpha - beta)] such that
+// H^H [alpha; x] = [beta; 0] and beta real, beta = -sign(Re alpha) ||[alpha; x]||
+// (the convention of the standard complex Householder QR).  Given alpha and
+// ||x||^2, returns tau, beta and the factor that scales x into v.
+struct Reflector { double2 tau; double beta; double2 scale; };
+__device__ __forceinline__ Reflector make_reflector(double2 alpha, double xnorm2) {
+  Reflector r;
+  if (xnorm2 == 0.0 && alpha.y == 0.0) {
+    r.tau = cz(); r.beta = alpha.x; r.scale = make_double2(1.0, 0.0);
+    return r;
+  }
+  double nrm = sqrt(cabs2(alpha) + xnorm2);
+  double beta = alpha.x >= 0.0 ? -nrm : nrm;
+  r.beta = beta;
+  r.tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+  r.scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
+  return r;
+}
+
+// -------------------------------------------------- one-sided Jacobi SVD
+// SVD of an n x n complex matrix (n <= 32) held column-major in shared
+// memory with leading dimension 32.  On exit U (in A's storage) holds the
+// left singular vectors sorted by descending singular value, s the values,
+// V the right singular vectors, and each column pair carries the phase
+// convention "first entry of u within 1e-10 of the largest modulus is real
+// positive".  Columns with zero singular value are returned as zero vectors.
+// Work space: W (32 x 32 complex) and sw (>= 3*32 doubles + 32 ints).
+struct SvdSmem {
+  double2 A[32 * 32];
+  double2 V[32 * 32];
+  double2 W[32 * 32];
+  double s[32];
+  double red[2 * NTU_WARPS];
+  int perm[32];
+  int rotated;
+};
+
+__device__ inline void cta_svd_small(SvdSmem& S, int n) {
+  const int tid = threadIdx.x;
+  const int np = (n + 1) & ~1;          // even number of columns (virtual zero col)
+  // V = identity
+  for (int i = tid; i < 32 * 32; i += NTU_CTA) {
+    int r = i & 31, c = i >> 5;
+    S.V[i] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    if (c >= n || r >= n) S.A[i] = cz();
+  }
+  __syncthreads();
+  const int grp = tid >> 4;             // 16 groups of 16 lanes
+  const int lane = tid & 15;
+  const unsigned mask = 0xffffu << ((tid & 16));
+  const double tol = fmax(1e-15, 2.3e-16 * n);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) S.rotated = 0;
+    __syncthreads();
+    for (int t = 0; t < np - 1; ++t) {
+      if (grp < np / 2) {
+        int p, q;
+        if (grp == 0) { p = t; q = np - 1; }
+        else { p = (t + grp) % (np - 1); q = (t - grp + (np - 1)) % (np - 1); }
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        if (q < n) {
+          double al = 0.0, be = 0.0; double2 ga = cz();
+          for (int r = lane; r < n; r += 16) {
+            double2 ap = S.A[p * 32 + r], aq = S.A[q * 32 + r];
+            al += cabs2(ap); be += cabs2(aq); ga = cfmac(ap, aq, ga);
+          }
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(mask, al, o);
+            be += __shfl_xor_sync(mask, be, o);
+            ga.x += __shfl_xor_sync(mask, ga.x, o);
+            ga.y += __shfl_xor_sync(mask, ga.y, o);
+          }
+          double g = sqrt(cabs2(ga));
+          if (g > 0.0 && g > tol * sqrt(al * be)) {
+            // rotate (p, q) so that the pair becomes orthogonal
+            double zeta = (be - al) / (2.0 * g);
+            double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+            double2 ph = make_double2(ga.x / g, -ga.y / g);     // e^{-i phi}
+            for (int r = lane; r < n; r += 16) {
+              double2 ap = S.A[p * 32 + r], aq = cmul(S.A[q * 32 + r], ph);
+              S.A[p * 32 + r] = make_double2(c * ap.x - s * aq.x, c * ap.y - s * aq.y);
+              S.A[q * 32 + r] = make_double2(s * ap.x + c * aq.x, s * ap.y + c * aq.y);
+              double2 vp = S.V[p * 32 + r], vq = cmul(S.V[q * 32 + r], ph);
+              S.V[p * 32 + r] = make_double2(c * vp.x - s * vq.x, c * vp.y - s * vq.y);
+              S.V[q * 32 + r] = make_double2(s * vp.x + c * vq.x, s * vp.y + c * vq.y);
+            }
+            if (lane == 0) S.rotated = 1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!S.rotated) break;
+    __syncthreads();
+  }
+  // singular values = column norms
+  for (int c = grp; c < n; c += 16) {
+    double a = 0.0;
+    for (int r = lane; r < n; r += 16) a += cabs2(S.A[c * 32 + r]);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(mask, a, o);
+    if (lane == 0) S.s[c] = sqrt(a);
+  }
+  __syncthreads();
+  if (tid < n) {          // rank of column tid in descending order (stable)
+    double sv = S.s[tid];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double sj = S.s[j];
+      rank += (sj > sv) || (sj == sv && j < tid);
+    }
+    S.perm[rank] = tid;
+  }
+  __syncthreads();
+  // gather into W (U) and A's old storage reused for sorted V via W swap
+  for (int i = tid; i < 32 * 32; i += NTU_CTA) {
+    int r = i & 31, k = i >> 5;
+    double2 u = cz();
+    if (k < n && r < n) {
+      int src = S.perm[k];
+      double sv = S.s[src];
+      if (sv > 0.0) u = cscale(S.A[src * 32 + r], 1.0 / sv);
+    }
+    S.W[i] = u;
+  }
+  __syncthreads();
+  for (int i = tid; i < 32 * 32; i += NTU_CTA) {
+    int r = i & 31, k = i >> 5;
+    S.A[i] = (k < n && r < n) ? S.V[S.perm[k] * 32 + r] : cz();
+  }
+  __syncthreads();
+  double sv_sorted = 0.0;
+  if (tid < n) sv_sorted = S.s[S.perm[tid]];
+  __syncthreads();
+  if (tid < n) S.s[tid] = sv_sorted;
+  // W = U (sorted), A = V (sorted); move V to V, U to A
+  for (int i = tid; i < 32 * 32; i += NTU_CTA) { S.V[i] = S.A[i]; }
+  __syncthreads();
+  for (int i = tid; i < 32 * 32; i += NTU_CTA) { S.A[i] = S.W[i]; }
+  __syncthreads();
+  // phase convention, one group per column
+  for (int k = grp; k < n; k += 16) {
+    double m = 0.0;
+    for (int r = lane; r < n; r += 16) m = fmax(m, cabs2(S.A[k * 32 + r]));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(mask, m, o));
+    m = sqrt(m);
+    int piv = 1 << 30;
+    for (int r = lane; r < n; r += 16)
+      if (m > 0.0 && sqrt(cabs2(S.A[k * 32 + r])) >= (1.0 - 1e-10) * m) piv = min(piv, r);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(mask, piv, o));
+    if (m > 0.0) {
+      double2 up = S.A[k * 32 + piv];
+      double a = sqrt(cabs2(up));
+      double2 ph = make_double2(up.x / a, -up.y / a);
+      for (int r = lane; r < n; r += 16) {
+        S.A[k * 32 + r] = cmul(S.A[k * 32 + r], ph);
+        S.V[k * 32 + r] = cmul(S.V[k * 32 + r], ph);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// --------------------------------------- Hermitian tridiagonalisation
+// A (n x n complex Hermitian, column-major, leading dim n, global memory) is
+// reduced to a real symmetric tridiagonal T = Q^H A Q with
+// Q = H_0 H_1 ... H_{n-2}.  Reflector j acts on rows j+1..n-1; its vector is
+// v = [1; A[j+2:, j]] and its factor tau[j].  d[0..n) and e[0..n-1) receive T.
+// p: scratch of n complex.  sred: >= 2*NTU_WARPS doubles.
+__device__ inline void cta_hetrd(double2* __restrict__ A, int n, double* d, double* e,
+                                 double2* tau, double2* p, double* sred) {
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - j - 1;                 // length of the reflected part
+    double2* col = A + (size_t)j * n + j + 1;   // A[j+1:, j]
+    double xn = 0.0;
+    for (int i = 1 + tid; i < m; i += NTU_CTA) xn += cabs2(col[i]);
+    xn = block_sum(xn, sred);
+    double2 alpha = col[0];
+    Reflector R = make_reflector(alpha, xn);
+    __syncthreads();
+    for (int i = 1 + tid; i < m; i += NTU_CTA) col[i] = cmul(col[i], R.scale);
+    if (tid == 0) {
+      e[j] = R.beta; tau[j] = R.tau; d[j] = A[(size_t)j * n + j].x;
+      col[0] = make_double2(1.0, 0.0);      // v[0] = 1 stored temporarily
+    }
+    __syncthreads();
+    if (R.tau.x != 0.0 || R.tau.y != 0.0) {
+      double2* A22 = A + (size_t)(j + 1) * n + j + 1;
+      // p_i = tau * sum_k A22[i,k] v_k = tau * sum_k conj(A22[k,i]) v_k
+      for (int i = wid; i < m; i += NTU_WARPS) {
+        const double2* ci = A22 + (size_t)i * n;
+        double2 acc = cz();
+        for (int k = lid; k < m; k += 32) acc = cfmac(ci[k], col[k], acc);
+        acc = warp_sum2(acc);
+        if (lid == 0) p[i] = cmul(R.tau, acc);
+      }
+      __syncthreads();
+      // w = p - (1/2) conj(tau) (v^H p) v
+      double2 vp = cz();
+      for (int i = tid; i < m; i += NTU_CTA) vp = cfmac(col[i], p[i], vp);
+      vp = block_sum2(vp, sred);
+      double2 f = cscale(cmul(cconj(R.tau), vp), 0.5);
+      for (int i = tid; i < m; i += NTU_CTA) p[i] = csub(p[i], cmul(f, col[i]));
+      __syncthreads();
+      // A22 -= v w^H + w v^H
+      for (int idx = tid; idx < m * m; idx += NTU_CTA) {
+        int k = idx % m, i = idx / m;          // row k, column i
+        double2 a = A22[(size_t)i * n + k];
+        double2 vk = col[k], wk = p[k], vi = col[i], wi = p[i];
+        a = csub(a, cmul(vk, cconj(wi)));
+        a = csub(a, cmul(wk, cconj(vi)));
+        A22[(size_t)i * n + k] = a;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) d[n - 1] = A[(size_t)(n - 1) * n + n - 1].x;
+  __syncthreads();
+}
+
+// b <- Q^H b (conj == true) or b <- Q b, with Q from cta_hetrd.
+__device__ inline void cta_apply_q(const double2* __restrict__ A, int n, const double2* tau,
+                                   double2* b, bool adjoint, double* sred) {
+  const int tid = threadIdx.x;
+  for (int jj = 0; jj < n - 1; ++jj) {
+    int j = adjoint ? jj : (n - 2 - jj);
+    double2 t = tau[j];
+    if (t.x == 0.0 && t.y == 0.0) continue;
+    const double2* v = A + (size_t)j * n + j + 1;   // v[0] = 1 implicitly
+    int m = n - j - 1;
+    double2* bb = b + j + 1;
+    double2 s = cz();
+    for (int i = tid; i < m; i += NTU_CTA) s = cfmac(i == 0 ? make_double2(1.0, 0.0) : v[i], bb[i], s);
+    s = block_sum2(s, sred);
+    double2 f = adjoint ? cmul(cconj(t), s) : cmul(t, s);
+    for (int i = tid; i < m; i += NTU_CTA) bb[i] = csub(bb[i], cmul(f, i == 0 ? make_double2(1.0, 0.0) : v[i]));
+    __syncthreads();
+  }
+}
+
+// ------------------------------------ implicit symmetric tridiagonal QR
+// Eigenvalues of the real symmetric tridiagonal (d, e) (e[k] couples k and
+// k+1) by implicit QR sweeps with the Wilkinson shift.  A sweep on the
+// unreduced block [lo, hi] applies plane rotations G(k, k+1; c, s),
+// k = lo..hi-1, so that T <- G^T T G; the eigenvectors are the columns of
+// Z = G_1 G_2 ... G_m.
+
+// Deflate negligible couplings and find the trailing unreduced block.
+// Returns false when every eigenvalue has converged.
+__device__ inline bool qr_next_block(double* d, double* e, int& lo, int& hi) {
+  const double eps = 2.220446049250313e-16;
+  while (hi > 0) {
+    for (int k = 0; k < hi; ++k)
+      if (fabs(e[k]) <= eps * (fabs(d[k]) + fabs(d[k + 1]))) e[k] = 0.0;
+    if (e[hi - 1] == 0.0) { --hi; continue; }
+    lo = hi - 1;
+    while (lo > 0 && e[lo - 1] != 0.0) --lo;
+    return true;
+  }
+  return false;
+}
+
+// One bulge-chasing sweep on [lo, hi]; rotation t (acting on k = lo + t) is
+// returned in cbuf[t], sbuf[t].
+__device__ inline void qr_sweep(double* d, double* e, int lo, int hi, double* cbuf, double* sbuf) {
+  double a = d[hi - 1], b = e[hi - 1], cc = d[hi];
+  double dl = 0.5 * (a - cc);
+  double den = dl + copysign(hypot(dl, b), dl);
+  double mu = (den != 0.0) ? cc - b * b / den : cc - fabs(b);
+  double x = d[lo] - mu, z = e[lo];
+  for (int k = lo; k < hi; ++k) {
+    double r = hypot(x, z);
+    double c, s;
+    if (r == 0.0) { c = 1.0; s = 0.0; }
+    else { c = x / r; s = -z / r; }
+    if (k > lo) e[k - 1] = r;
+    double dk = d[k], dk1 = d[k + 1], ek = e[k];
+    double cs = c * s;
+    d[k] = c * c * dk - 2.0 * cs * ek + s * s * dk1;
+    d[k + 1] = s * s * dk + 2.0 * cs * ek + c * c * dk1;
+    e[k] = cs * (dk - dk1) + (c * c - s * s) * ek;
+    if (k + 1 < hi) {
+      double ek1 = e[k + 1];
+      z = -s * ek1;
+      e[k + 1] = c * ek1;
+      x = e[k];
+    }
+    cbuf[k - lo] = c;
+    sbuf[k - lo] = s;
+  }
+}
+
+// Single-thread driver that appends every rotation to a log and applies
+// Z^T to y on the fly.  Returns 0, or ST_NUMERIC on non-convergence or log
+// overflow.
+struct RotLog { double* c; double* s; int* k; int cap; int count; };
+
+__device__ inline int tridiag_qr(double* d, double* e, int n, RotLog& log, double2* y) {
+  log.count = 0;
+  int lo = 0, hi = n - 1, iters = 0;
+  while (qr_next_block(d, e, lo, hi)) {
+    if (++iters > 40 * n) return ST_NUMERIC;
+    int len = hi - lo;
+    if (log.count + len > log.cap) return ST_NUMERIC;
+    double* cb = log.c + log.count;
+    double* sb = log.s + log.count;
+    qr_sweep(d, e, lo, hi, cb, sb);
+    for (int t = 0; t < len; ++t) {
+      int k = lo + t;
+      log.k[log.count + t] = k;
+      if (y) {
+        double c = cb[t], s = sb[t];
+        double2 yk = y[k], yk1 = y[k + 1];
+        y[k] = make_double2(c * yk.x - s * yk1.x, c * yk.y - s * yk1.y);
+        y[k + 1] = make_double2(s * yk.x + c * yk1.x, s * yk.y + c * yk1.y);
+      }
+    }
+    log.count += len;
+  }
+  return 0;
+}
+
+// CTA driver that accumulates Z explicitly (row-major n x n, global): thread
+// 0 runs each sweep into the shared chain (2n doubles), then every thread
+// applies the chain to its own rows of Z.  Returns 0 or ST_NUMERIC.
+__device__ inline int cta_tridiag_qr_z(double* d, double* e, int n, double* Z, double* chain,
+                                       int* shared_state) {
+  const int tid = threadIdx.x;
+  for (size_t idx = tid; idx < (size_t)n * n; idx += NTU_CTA)
+    Z[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+  int lo = 0, hi = n - 1, iters = 0;   // meaningful in thread 0 only
+  __syncthreads();
+  while (true) {
+    if (tid == 0) {
+      int st = 0, more = qr_next_block(d, e, lo, hi) ? 1 : 0;
+      if (more && ++iters > 40 * n) { st = ST_NUMERIC; more = 0; }
+      if (more) qr_sweep(d, e, lo, hi, chain, chain + n);
+      shared_state[0] = more; shared_state[1] = lo; shared_state[2] = hi - lo;
+      shared_state[3] = st;
+    }
+    __syncthreads();
+    if (!shared_state[0]) break;
+    const int l0 = shared_state[1], len = shared_state[2];
+    for (int row = tid; row < n; row += NTU_CTA) {
+      double* z = Z + (size_t)row * n;
+      for (int t = 0; t < len; ++t) {
+        int k = l0 + t;
+        double c = chain[t], s = chain[n + t];
+        double zk = z[k], zk1 = z[k + 1];
+        z[k] = c * zk - s * zk1;
+        z[k + 1] = s * zk + c * zk1;
+      }
+    }
+    __syncthreads();
+  }
+  int st = shared_state[3];
+  __syncthreads();
+  return st;
+}
+
+// u <- Z u (rotations replayed in reverse), single thread.
+__device__ inline void rotlog_apply_z(const RotLog& log, double2* u) {
+  for (int t = log.count - 1; t >= 0; --t) {
+    int k = log.k[t];
+    double c = log.c[t], s = log.s[t];
+    double2 a = u[k], b = u[k + 1];
+    u[k] = make_double2(c * a.x + s * b.x, c * a.y + s * b.y);
+    u[k + 1] = make_double2(-s * a.x + c * b.x, -s * a.y + c * b.y);
+  }
+}
+
+}  // namespace ntu

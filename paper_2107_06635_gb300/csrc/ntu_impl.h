@@ -1,0 +1,116 @@
+// Internal declarations of the NTU library: the per-configuration plan
+// (sizes and contraction index tables), the device work space and the
+// kernel launchers that the C ABI (capi.cu) strings together.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/ntu.h"
+
+namespace ntu {
+
+// One batched complex GEMM of the environment contraction (Fig. 4):
+//   C[b][rowC[m] + colC[n]] = sum_k A[b][rowA[m] + kA[k]] * B[b][kB[k] + colB[n]]
+// with optional conjugation of A or B.  The six index tables map the
+// composite tensor indices to element offsets; they live in one device int
+// array at the given offsets.
+struct GemmOp {
+  int M, N, Kd;
+  int rowA, kA, kB, colB, rowC, colC;   // offsets into the table array
+  int conjA, conjB;
+  long long sA, sB, sC;                 // per-item strides (complex elements)
+};
+
+struct Plan {
+  int D, d, d_anc, dp, r, K, m, ng, nA;
+  long long szT, szQ, szR, szE1, szE2, szS2, szG;
+  GemmOp eL, eR, eTL, eBL, eTR, eBR;    // edge double tensors (Fig. 4(b))
+  GemmOp y, t1, t2, h;                  // half environment steps (Fig. 4(c,d))
+  GemmOp join;                          // join of the two halves (Fig. 4(d,e))
+  int* d_tab;                           // device index tables
+  int n_tab;
+};
+
+// Device work space for max_batch items.  Every pointer is the base of a
+// stack of per-item slices.
+struct Work {
+  int cap;               // items
+  double2 *GA, *GB;      // split gate halves, d*d*r each
+  double2 *Mg, *Qcm;     // gated matrices / Q scratch, 2 * m*K each (both sides)
+  double2 *QA, *QB, *RA, *RB;
+  // environment (element type: double2 for FP64, float2 for the mixed paths)
+  void *Tac, *Tbc, *QAc, *QBc, *EL, *ER, *ETL, *EBL, *ETR, *EBR, *Y, *T1, *T2, *HL, *HR, *graw;
+  double2 *g, *gscr, *gw;     // metric, Cholesky / eigen scratch, eigenvectors
+  double *gz, *geig;          // explicit Z (ng*ng) and d,e (2*ng) for the repair fallback
+  double2 *gtau, *gp;         // reflector factors, vector scratch (ng each)
+  double *diag;               // 3 per item
+  // ALS scratch
+  double2 *x0, *gx0, *Tm, *gA, *jv, *pv, *tauv;
+  double *dv, *ev, *rc, *rs;
+  int *rk;
+  int rotcap;
+  double2 *MA, *MB;
+  double *info;               // 4 per item
+  // outputs of a full update when the caller gives none
+  double2 *Ta_out, *Tb_out;
+  // inputs staged for host-pointer calls
+  double2 *Ta_in, *Tb_in, *G_in;
+  // unit cell of the context
+  double2 *A, *B, *cTa, *cTb, *cG, *op;
+  double2 *cA2, *cB2;
+  double2 *mscr1, *mscr2, *medge;   // measurement scratch
+  double2 *mval;
+};
+
+}  // namespace ntu
+
+struct ntu_ctx {
+  ntu_config cfg;
+  cudaStream_t stream;
+  bool own_stream;
+  ntu::Plan plan;
+  ntu::Work w;
+  int* d_status;
+  char err[320];
+  int launches;
+  int stage;          // 0 none, 1 after apply_gate, 2 after env_metric
+  int stage_bond;
+  size_t env_es;      // element size of the environment buffers
+  int profiling;
+  cudaEvent_t ev[6];
+};
+
+namespace ntu {
+
+// error helper: record message, return status
+int fail(ntu_ctx* c, int status, const char* fmt, ...);
+
+// plans and tables (k_env.cu)
+int plan_build(ntu_ctx* c);
+void plan_free(ntu_ctx* c);
+
+// launchers (return cudaError_t of the launch; they also count launches)
+cudaError_t launch_gate_qr(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
+                           const double2* G, int swap_sites, double2* QA, double2* RA,
+                           double2* QB, double2* RB);
+cudaError_t launch_env(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
+                       const double2* QA, const double2* QB, void* graw);
+cudaError_t launch_repair(ntu_ctx* c, int n, const void* graw, int raw_is_f32, double2* g,
+                          double* diag);
+cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
+                       const double2* RB, double2* MA, double2* MB, double* info);
+cudaError_t launch_recompose(ntu_ctx* c, int n, const double2* QA, const double2* QB,
+                             const double2* MA, const double2* MB, double2* Ta_out,
+                             double2* Tb_out);
+cudaError_t launch_orient(ntu_ctx* c, int bond, const double2* A, const double2* B,
+                          double2* Ta, double2* Tb);
+cudaError_t launch_deorient(ntu_ctx* c, int bond, const double2* Ta, const double2* Tb,
+                            double2* A, double2* B);
+cudaError_t launch_site_gate(ntu_ctx* c, double2* A, double2* B, const double2* op);
+cudaError_t launch_measure(ntu_ctx* c, const double2* T, const double2* N, const double2* op,
+                           double2* out);
+cudaError_t launch_copy_raw(ntu_ctx* c, int n, const void* graw, double2* g);
+size_t als_smem_bytes();
+
+}  // namespace ntu

@@ -1,0 +1,56 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/ntu.h declares, and rejects
+invalid configurations before touching the device."""
+import ctypes
+
+import pytest
+
+from paper_2107_06635_gb300 import build as B
+from paper_2107_06635_gb300 import ntu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ntu.load()
+
+
+def test_library_builds_for_sm103a(lib):
+    import os
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(B.LIB) and B.up_to_date()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = ntu.header_symbols()
+    assert len(names) >= 19
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(ntu._SIGS), "binding and header disagree"
+
+
+@pytest.mark.parametrize("field,value", [("D", 0), ("D", 9), ("d_phys", 1), ("r", 0), ("r", 5),
+                                          ("precision", 7), ("tau_kmin", 9), ("max_batch", 0)])
+def test_init_rejects_bad_config(lib, field, value):
+    cfg = ntu.Config(4, 2, 1, 2, 10, 0, 4, 15, 1)
+    if field == "tau_kmin":
+        cfg.tau_kmin, cfg.tau_kmax = 9, 5
+    else:
+        setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    st = lib.ntu_init(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert st == 1, lib.ntu_last_error(None)
+    assert h.value is None
+    assert lib.ntu_last_error(None)
+
+
+def test_init_rejects_too_few_rows(lib):
+    # D=1, d_p=2 gives a 2 x r gated matrix: r=4 would need 4 rows
+    cfg = ntu.Config(1, 2, 1, 4, 10, 0, 4, 15, 1)
+    h = ctypes.c_void_p()
+    assert lib.ntu_init(ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+
+
+def test_null_arguments(lib):
+    assert lib.ntu_init(None, None, None) == 1
+    assert lib.ntu_destroy(None) == 0
+    assert lib.ntu_sync(None) == 1

@@ -1,0 +1,335 @@
+"""GPU parity of the CUDA NTU path against the CPU oracle, stage by stage and
+end to end, through the C ABI.
+
+Tolerances: FP64 path rel-Frobenius(g) <= 1e-10 (and bit-exact on small
+integer inputs, where every partial sum is an exact integer), mixed FP32
+environment rel(g) <= 1e-4; delta within 1e-8 of the oracle on the FP64
+path and 1e-2 relative on the mixed path; <sigma_x> within 1e-6.
+Gauge-dependent outputs (Q, R, g, M, A', B') are compared element by element
+only on single calls with full-rank random inputs and gates with distinct
+operator-Schmidt values, where QR with a positive diagonal and SVD with the
+phase convention are unique.
+"""
+import numpy as np
+import pytest
+
+from oracle import ntu_oracle as O
+from paper_2107_06635_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _empty(shape):
+    return torch.empty(shape, dtype=torch.complex128, device="cuda")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _ctx(D, r=2, d_anc=1, sweeps=10, precision=0, max_batch=4, kmin=4, kmax=15):
+    from paper_2107_06635_gb300 import ntu
+    return ntu.Context(D, 2, d_anc, r, sweeps, precision, kmin, kmax, max_batch)
+
+
+def _oracle_stage(Ta, Tb, G, cfg):
+    GA, GB = O.gate_split(G, cfg.r)
+    QA, RA = O.qr_positive(O.gated_matrix(Ta, GA, cfg.d_anc, "left"))
+    QB, RB = O.qr_positive(O.gated_matrix(Tb, GB, cfg.d_anc, "right"))
+    return QA, RA, QB, RB
+
+
+def _items(seed, n, d_p, D):
+    rng = np.random.default_rng(seed)
+    Ta = np.stack([I.random_site_tensor(rng, d_p, D) for _ in range(n)])
+    Tb = np.stack([I.random_site_tensor(rng, d_p, D) for _ in range(n)])
+    G = np.stack([I.random_gate(rng) for _ in range(n)])
+    return Ta, Tb, G
+
+
+# ------------------------------------------------------------ gate + QR
+@pytest.mark.parametrize("D,r,d_anc", [(2, 2, 1), (3, 2, 1), (5, 2, 1), (4, 4, 1), (3, 2, 2)])
+def test_gate_qr_matches_oracle(D, r, d_anc):
+    n = 3
+    d_p = 2 * d_anc
+    Ta, Tb, G = _items(100 + D, n, d_p, D)
+    ctx = _ctx(D, r, d_anc, max_batch=n)
+    m, K = d_p * D ** 3, D * r
+    QA, RA, QB, RB = _empty((n, m, K)), _empty((n, K, K)), _empty((n, m, K)), _empty((n, K, K))
+    ctx.batch_gate_qr_dev(n, _dev(Ta), _dev(Tb), _dev(G), QA, RA, QB, RB)
+    ctx.sync()
+    cfg = O.Config(D=D, r=r, d_anc=d_anc)
+    for i in range(n):
+        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+        assert _rel(RA[i].cpu().numpy(), ra) < 1e-12
+        assert _rel(RB[i].cpu().numpy(), rb) < 1e-12
+        assert _rel(QA[i].cpu().numpy(), qa) < 1e-12
+        assert _rel(QB[i].cpu().numpy(), qb) < 1e-12
+
+
+# --------------------------------------------------------- environment
+@pytest.mark.parametrize("D,r", [(2, 2), (3, 2), (4, 2), (5, 2), (3, 4)])
+def test_env_matches_oracle_fp64(D, r):
+    n = 2
+    Ta, Tb, G = _items(200 + D, n, 2, D)
+    cfg = O.Config(D=D, r=r)
+    ctx = _ctx(D, r, max_batch=n)
+    Q = [_oracle_stage(Ta[i], Tb[i], G[i], cfg) for i in range(n)]
+    QA = np.stack([q[0] for q in Q])
+    QB = np.stack([q[2] for q in Q])
+    ng = (D * r) ** 2
+    g = _empty((n, ng, ng))
+    ctx.batch_env_dev(n, _dev(Ta), _dev(Tb), _dev(QA), _dev(QB), g)
+    ctx.sync()
+    for i in range(n):
+        ref = O.metric_raw(Ta[i], Tb[i], QA[i], QB[i], 2, D)
+        assert _rel(g[i].cpu().numpy(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("D,r", [(2, 2), (3, 2), (4, 1)])
+def test_env_bit_exact_on_integer_inputs(D, r):
+    """Small-integer tensors and isometries: every partial sum is an exact
+    integer in FP64, so any summation order gives the oracle's bits."""
+    rng = np.random.default_rng(300 + D)
+    n, d_p, K = 2, 2, D * r
+    Ta = np.stack([I.integer_site_tensor(rng, d_p, D, -2, 2) for _ in range(n)])
+    Tb = np.stack([I.integer_site_tensor(rng, d_p, D, -2, 2) for _ in range(n)])
+    m = d_p * D ** 3
+    QA = (rng.integers(-2, 3, (n, m, K)) + 1j * rng.integers(-2, 3, (n, m, K))).astype(np.complex128)
+    QB = (rng.integers(-2, 3, (n, m, K)) + 1j * rng.integers(-2, 3, (n, m, K))).astype(np.complex128)
+    ctx = _ctx(D, r, max_batch=n)
+    g = _empty((n, K * K, K * K))
+    ctx.batch_env_dev(n, _dev(Ta), _dev(Tb), _dev(QA), _dev(QB), g)
+    ctx.sync()
+    for i in range(n):
+        ref = O.metric_raw(Ta[i], Tb[i], QA[i], QB[i], d_p, D)
+        assert np.abs(ref).max() < 2 ** 52
+        assert np.array_equal(g[i].cpu().numpy(), ref)
+
+
+def test_env_mixed_fp32_within_budget():
+    D, r, n = 5, 2, 2
+    Ta, Tb, G = _items(400, n, 2, D)
+    cfg = O.Config(D=D, r=r)
+    ctx = _ctx(D, r, precision=1, max_batch=n)
+    Q = [_oracle_stage(Ta[i], Tb[i], G[i], cfg) for i in range(n)]
+    QA, QB = np.stack([q[0] for q in Q]), np.stack([q[2] for q in Q])
+    ng = (D * r) ** 2
+    g = _empty((n, ng, ng))
+    ctx.batch_env_dev(n, _dev(Ta), _dev(Tb), _dev(QA), _dev(QB), g)
+    ctx.sync()
+    for i in range(n):
+        ref = O.metric_raw(Ta[i], Tb[i], QA[i], QB[i], 2, D)
+        assert _rel(g[i].cpu().numpy(), ref) < 1e-4
+
+
+# --------------------------------------------------------------- repair
+def test_repair_cholesky_path_matches_oracle():
+    D, r, n = 3, 2, 2
+    Ta, Tb, G = _items(500, n, 2, D)
+    cfg = O.Config(D=D, r=r)
+    raws, refs = [], []
+    for i in range(n):
+        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+        raw = O.metric_raw(Ta[i], Tb[i], qa, qb, 2, D)
+        raws.append(raw)
+        refs.append(O.hermitise_repair(raw))
+    ctx = _ctx(D, r, max_batch=n)
+    g = _dev(np.stack(raws))
+    diag = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ctx.batch_repair_dev(n, g, diag)
+    ctx.sync()
+    for i in range(n):
+        assert _rel(g[i].cpu().numpy(), refs[i][0]) < 1e-12
+        dg = diag[i].cpu().numpy()
+        assert abs(dg[2] - refs[i][1][2]) < 1e-12
+        assert np.isnan(dg[1])          # certified positive definite, no repair
+
+
+def test_repair_clips_negative_eigenvalues():
+    """Indefinite Hermitian input: the eigen-repair fallback must match the
+    oracle's clipping."""
+    rng = np.random.default_rng(7)
+    n, K = 2, 6
+    ng = K * K
+    raws = []
+    for _ in range(n):
+        a = rng.standard_normal((ng, ng)) + 1j * rng.standard_normal((ng, ng))
+        h = a @ a.conj().T / ng
+        lam, w = np.linalg.eigh(h)
+        lam[:5] = -np.linspace(0.05, 0.2, 5)          # five negative modes
+        raws.append((w * lam) @ w.conj().T + 1e-3 * (rng.standard_normal((ng, ng))))
+    ctx = _ctx(3, 2, max_batch=n)
+    g = _dev(np.stack(raws))
+    diag = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ctx.batch_repair_dev(n, g, diag)
+    ctx.sync()
+    for i in range(n):
+        ref, rd = O.hermitise_repair(raws[i])
+        assert _rel(g[i].cpu().numpy(), ref) < 1e-11
+        dg = diag[i].cpu().numpy()
+        assert abs(dg[0] - rd[0]) < 1e-12 * max(1.0, rd[0])
+        assert abs(dg[1] - rd[1]) < 1e-10
+
+
+# ------------------------------------------------------------------ ALS
+@pytest.mark.parametrize("D,r,sweeps", [(2, 2, 3), (3, 2, 10), (4, 2, 5), (3, 4, 4)])
+def test_als_matches_oracle(D, r, sweeps):
+    n = 2
+    Ta, Tb, G = _items(600 + D, n, 2, D)
+    cfg = O.Config(D=D, r=r, sweeps=sweeps)
+    gs, RAs, RBs, refs = [], [], [], []
+    for i in range(n):
+        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+        g, _ = O.hermitise_repair(O.metric_raw(Ta[i], Tb[i], qa, qb, 2, D))
+        gs.append(g); RAs.append(ra); RBs.append(rb)
+        refs.append(O.als_truncate(g, ra, rb, D, sweeps, cfg.taus))
+    ctx = _ctx(D, r, sweeps=sweeps, max_batch=n)
+    K = D * r
+    MA, MB = _empty((n, K, D)), _empty((n, K, D))
+    info = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    ctx.batch_als_dev(n, _dev(np.stack(gs)), _dev(np.stack(RAs)), _dev(np.stack(RBs)), MA, MB, info)
+    ctx.sync()
+    for i in range(n):
+        ma, mb, eps, delta, eps0, tau = refs[i]
+        inf = info[i].cpu().numpy()
+        assert abs(inf[2] - eps0) < 1e-12 * eps0
+        assert abs(inf[1] - delta) < 1e-8
+        assert abs(inf[0] - eps) < 1e-8 * eps0
+        assert inf[3] == tau
+        assert _rel(MA[i].cpu().numpy(), ma) < 1e-8
+        assert _rel(MB[i].cpu().numpy(), mb) < 1e-8
+
+
+# ------------------------------------------------------- full update
+@pytest.mark.parametrize("D,precision", [(3, 0), (4, 0), (6, 0), (4, 1)])
+def test_batch_update_matches_oracle(D, precision):
+    n = 3
+    Ta, Tb, G = _items(700 + D, n, 2, D)
+    ctx = _ctx(D, 2, precision=precision, max_batch=n, kmin=4, kmax=15 if precision == 0 else 8)
+    Ta_o, Tb_o, info = ctx.batch_update_host(Ta, Tb, G)
+    cfg = O.Config(D=D, r=2)
+    for i in range(n):
+        A2, B2, inf = O.bond_update(Ta[i], Tb[i], G[i], cfg)
+        if precision == 0:
+            assert _rel(Ta_o[i], A2) < 1e-9
+            assert _rel(Tb_o[i], B2) < 1e-9
+            assert abs(info[i, 1] - inf.delta) < 1e-8
+        else:
+            assert abs(info[i, 1] - inf.delta) <= 1e-2 * inf.delta
+            pair = np.einsum("plurn,qrvwx->plunqvwx", Ta_o[i], Tb_o[i])
+            ref = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
+            assert _rel(pair, ref) < 1e-4
+
+
+def test_batch_update_host_and_dev_agree_and_empty_batch():
+    D, n = 3, 2
+    Ta, Tb, G = _items(800, n, 2, D)
+    ctx = _ctx(D, 2, max_batch=n)
+    a1, b1, i1 = ctx.batch_update_host(Ta, Tb, G)
+    ta, tb, gg = _dev(Ta), _dev(Tb), _dev(G)
+    oa, ob = torch.empty_like(ta), torch.empty_like(tb)
+    info = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    ctx.batch_update_dev(n, ta, tb, gg, oa, ob, info)
+    ctx.sync()
+    assert np.array_equal(oa.cpu().numpy(), a1)
+    assert np.array_equal(info.cpu().numpy(), i1)
+    ctx.batch_update_dev(0, ta, tb, gg, oa, ob, info)     # empty batch is a no-op
+    from paper_2107_06635_gb300.ntu import NTUError
+    with pytest.raises(NTUError):
+        ctx.batch_update_dev(n + 1, ta, tb, gg, oa, ob, info)
+
+
+# --------------------------------------------------------- unit cell
+def test_unit_cell_step_matches_oracle_config1():
+    """One Trotter step of the 2-site cell, D=3, seed 1, exp(-i 0.01 ZZ),
+    10 sweeps: R, g, delta per bond and the final state."""
+    A, B = I.random_pair(1, 2, 3)
+    G = I.zz_gate(0.01)
+    cfg = O.Config(D=3, r=2, sweeps=10)
+    ctx = _ctx(3, 2)
+    ctx.set_state(A, B)
+    Ao, Bo = A.copy(), B.copy()
+    for b in range(4):
+        RA, RB = ctx.apply_gate(b, G)
+        g, diag = ctx.env_metric(b)
+        res = ctx.als_truncate(b)
+        Ao, Bo, info = O.update_bond(Ao, Bo, b, G, cfg, keep=True)
+        assert _rel(RA @ RB.T, info.RA @ info.RB.T) < 1e-12
+        assert _rel(g, info.g) < 1e-10
+        assert abs(res["delta"] - info.delta) < 1e-8
+        assert res["tau"] == info.tau
+    A2, B2 = ctx.get_state()
+    assert _rel(A2, Ao) < 1e-9 and _rel(B2, Bo) < 1e-9
+
+
+def test_unit_cell_call_order_is_enforced():
+    from paper_2107_06635_gb300.ntu import NTUError
+    ctx = _ctx(2, 2)
+    A, B = I.random_pair(2, 2, 2)
+    ctx.set_state(A, B)
+    with pytest.raises(NTUError) as e:
+        ctx.env_metric(0)
+    assert e.value.status == 7
+    ctx.apply_gate(1, I.zz_gate(0.1))
+    with pytest.raises(NTUError):
+        ctx.env_metric(0)          # prepared bond was 1
+
+
+def test_step_product_state_single_site_exact():
+    """D=1, identity bond gates, field h: <sigma_z>(t) = cos(2 h t)."""
+    h, dt = 0.7, 0.05
+    ctx = _ctx(1, 1, sweeps=2)
+    A = I.plus_z_state(1)
+    ctx.set_state(A, A)
+    for step in range(1, 11):
+        deltas = ctx.step([I.identity_gate()] * 4, I.x_rotation(h * dt / 2))
+        for site in (0, 1):
+            z = ctx.measure(site, I.pauli("Z"))
+            assert abs(z - np.cos(2 * h * step * dt)) < 1e-12
+        assert np.all(deltas < 1e-14)
+
+
+def test_step_classical_quench_exact_at_D2():
+    ctx = _ctx(2, 2, sweeps=4)
+    A = I.plus_x_state(2)
+    ctx.set_state(A, A)
+    gates2, _ = I.tfim_real_time_gates(0.0, 0.05)
+    for _ in range(4):
+        deltas = ctx.step(gates2, None)
+        assert np.all(deltas <= 1e-12)
+
+
+def test_quench_observable_parity_d4():
+    """TFIM quench h=2.5, dt=0.01 from |+x> zero-padded to D=4: <sigma_x>
+    after each of 5 steps within 1e-6 of the oracle."""
+    D, steps = 4, 5
+    gates2, gate1 = I.tfim_real_time_gates(2.5, 0.01)
+    cfg = O.Config(D=D, r=2, sweeps=10)
+    A = I.plus_x_state(D)
+    B = I.plus_x_state(D)
+    ctx = _ctx(D, 2)
+    ctx.set_state(A, B)
+    for _ in range(steps):
+        ctx.step(gates2, gate1)
+        A, B, _ = O.ntu_step(A, B, gates2, gate1, cfg)
+        for site in (0, 1):
+            x_gpu = ctx.measure(site, I.pauli("X"))
+            x_ref = O.measure(A, B, site, I.pauli("X"), 1)
+            assert abs(x_gpu - x_ref) < 1e-6
+
+
+def test_measure_matches_oracle():
+    A, B = I.random_pair(9, 4, 3)
+    ctx = _ctx(3, 2, d_anc=2)
+    ctx.set_state(A, B)
+    for site in (0, 1):
+        for op in ("X", "Z"):
+            v = ctx.measure(site, I.pauli(op))
+            assert abs(v - O.measure(A, B, site, I.pauli(op), 2)) < 1e-12
