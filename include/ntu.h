@@ -179,6 +179,14 @@ int ntu_last_launch_count(const ntu_ctx* ctx);
 int ntu_set_profiling(ntu_ctx* ctx, int on);
 int ntu_stage_times(ntu_ctx* ctx, double* ms_out);
 
+/* Which solver path the device took, counted since the previous call (then
+ * reset): counts[0] ALS solves decided by the Cholesky certificate (every
+ * candidate tolerance keeps every eigenpair of g_A, Eq. 4), counts[1] ALS
+ * solves through the eigendecomposition, counts[2] metrics certified
+ * positive definite by Cholesky, counts[3] metrics repaired through the
+ * eigendecomposition.  Synchronises the context's stream. */
+int ntu_solver_paths(ntu_ctx* ctx, int* counts);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -22,6 +23,18 @@ int ntu::fail(ntu_ctx* c, int status, const char* fmt, ...) {
   vsnprintf(buf, 320, fmt, ap);
   va_end(ap);
   return status;
+}
+
+cudaError_t ntu::after_launch(ntu_ctx* c, const char* name) {
+  c->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && c->debug_sync) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  if (e != cudaSuccess && c->debug_sync)
+    fprintf(stderr, "ntu: kernel %s failed: %s\n", name, cudaGetErrorString(e));
+  return e;
 }
 
 static int cuda_check(ntu_ctx* c, cudaError_t e, const char* what) {
@@ -93,6 +106,7 @@ void carve(ntu_ctx* c, Carver& cv) {
   W.gx0 = cv.take<double2>(n * P.ng);
   W.Tm = cv.take<double2>(n * (size_t)P.ng * P.nA);
   W.gA = cv.take<double2>(n * (size_t)P.nA * P.nA);
+  W.gC = cv.take<double2>(n * (size_t)P.nA * P.nA);
   W.jv = cv.take<double2>(n * P.nA);
   W.pv = cv.take<double2>(n * P.nA);
   W.tauv = cv.take<double2>(n * P.nA);
@@ -187,9 +201,12 @@ extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
   real.dry = false;
   carve(c, real);
   // carve() filled every pointer; W.GA is the first slice, i.e. the block base
-  e = cudaMalloc(&c->d_status, sizeof(int));
+  e = cudaMalloc(&c->d_status, sizeof(int) * 8);
   if (e != cudaSuccess) { cudaFree(base); ntu_destroy(c); return fail(nullptr, NTU_ENOMEM, "status word"); }
-  cudaMemset(c->d_status, 0, sizeof(int));
+  cudaMemset(c->d_status, 0, sizeof(int) * 8);
+  c->d_paths = c->d_status + 4;
+  const char* dbg = getenv("NTU_DEBUG_SYNC");
+  c->debug_sync = (dbg && dbg[0] == '1') ? 1 : 0;
   cudaMemset(base, 0, dry.off);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     ntu_destroy(c);
@@ -220,6 +237,14 @@ extern "C" int ntu_sync(ntu_ctx* c) {
 }
 
 extern "C" int ntu_last_launch_count(const ntu_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" int ntu_solver_paths(ntu_ctx* c, int* counts) {
+  if (!c || !counts) return fail(c, NTU_EINVAL, "ntu_solver_paths: NULL argument");
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  CK(cudaMemcpy(counts, c->d_paths, 4 * sizeof(int), cudaMemcpyDeviceToHost), "read counters");
+  CK(cudaMemset(c->d_paths, 0, 4 * sizeof(int)), "reset counters");
+  return NTU_OK;
+}
 
 // ------------------------------------------------------------ unit cell
 extern "C" int ntu_set_state(ntu_ctx* c, const double* A, const double* B) {

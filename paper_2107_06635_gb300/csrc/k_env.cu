@@ -117,7 +117,7 @@ k_cgemm(GemmArgs g, const C2* __restrict__ A, const C2* __restrict__ B, C2* __re
 }
 
 template <typename C2>
-static void run_gemm(ntu_ctx* c, const GemmOp& op, int n, const void* A, const void* B, void* C) {
+static cudaError_t run_gemm(ntu_ctx* c, const GemmOp& op, int n, const void* A, const void* B, void* C) {
   GemmArgs a;
   const int* t = c->plan.d_tab;
   a.M = op.M; a.N = op.N; a.Kd = op.Kd;
@@ -130,7 +130,7 @@ static void run_gemm(ntu_ctx* c, const GemmOp& op, int n, const void* A, const v
   dim3 grid((op.N + BN - 1) / BN, (op.M + BM - 1) / BM, n);
   k_cgemm<C2, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, c->stream>>>(
       a, (const C2*)A, (const C2*)B, (C2*)C);
-  c->launches += 1;
+  return after_launch(c, "k_cgemm");
 }
 
 // --------------------------------------------------------------- plan
@@ -285,12 +285,12 @@ __global__ void k_to_f32(long long n, const double2* __restrict__ in, float2* __
     out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
-static void to_f32(ntu_ctx* c, long long n, const double2* in, void* out) {
+static cudaError_t to_f32(ntu_ctx* c, long long n, const double2* in, void* out) {
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   k_to_f32<<<(int)blocks, 256, 0, c->stream>>>(n, in, (float2*)out);
-  c->launches += 1;
+  return after_launch(c, "k_to_f32");
 }
 
 __global__ void k_to_f64(long long n, const float2* __restrict__ in, double2* __restrict__ out) {
@@ -305,48 +305,50 @@ cudaError_t launch_copy_raw(ntu_ctx* c, int n, const void* graw, double2* g) {
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   k_to_f64<<<(int)blocks, 256, 0, c->stream>>>(cnt, (const float2*)graw, g);
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_to_f64");
 }
 
+#define RG(x)                            \
+  do {                                   \
+    cudaError_t _e = (x);                \
+    if (_e != cudaSuccess) return _e;    \
+  } while (0)
+
 template <typename C2>
-static void env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, const void* QA,
+static cudaError_t env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, const void* QA,
                       const void* QB, void* graw) {
   const Plan& P = c->plan;
   Work& W = c->w;
-  run_gemm<C2>(c, P.eL, n, Tb, Tb, W.EL);
-  run_gemm<C2>(c, P.eTL, n, Tb, Tb, W.ETL);
-  run_gemm<C2>(c, P.eBL, n, Tb, Tb, W.EBL);
-  run_gemm<C2>(c, P.eR, n, Ta, Ta, W.ER);
-  run_gemm<C2>(c, P.eTR, n, Ta, Ta, W.ETR);
-  run_gemm<C2>(c, P.eBR, n, Ta, Ta, W.EBR);
+  RG(run_gemm<C2>(c, P.eL, n, Tb, Tb, W.EL));
+  RG(run_gemm<C2>(c, P.eTL, n, Tb, Tb, W.ETL));
+  RG(run_gemm<C2>(c, P.eBL, n, Tb, Tb, W.EBL));
+  RG(run_gemm<C2>(c, P.eR, n, Ta, Ta, W.ER));
+  RG(run_gemm<C2>(c, P.eTR, n, Ta, Ta, W.ETR));
+  RG(run_gemm<C2>(c, P.eBR, n, Ta, Ta, W.EBR));
   // left half: Q_A with E_L, E_TL, E_BL
-  run_gemm<C2>(c, P.y, n, QA, W.EL, W.Y);
-  run_gemm<C2>(c, P.t1, n, W.Y, QA, W.T1);
-  run_gemm<C2>(c, P.t2, n, W.ETL, W.T1, W.T2);
-  run_gemm<C2>(c, P.h, n, W.EBL, W.T2, W.HL);
+  RG(run_gemm<C2>(c, P.y, n, QA, W.EL, W.Y));
+  RG(run_gemm<C2>(c, P.t1, n, W.Y, QA, W.T1));
+  RG(run_gemm<C2>(c, P.t2, n, W.ETL, W.T1, W.T2));
+  RG(run_gemm<C2>(c, P.h, n, W.EBL, W.T2, W.HL));
   // right half: Q_B with E_R, E_TR, E_BR
-  run_gemm<C2>(c, P.y, n, QB, W.ER, W.Y);
-  run_gemm<C2>(c, P.t1, n, W.Y, QB, W.T1);
-  run_gemm<C2>(c, P.t2, n, W.ETR, W.T1, W.T2);
-  run_gemm<C2>(c, P.h, n, W.EBR, W.T2, W.HR);
-  run_gemm<C2>(c, P.join, n, W.HL, W.HR, graw);
+  RG(run_gemm<C2>(c, P.y, n, QB, W.ER, W.Y));
+  RG(run_gemm<C2>(c, P.t1, n, W.Y, QB, W.T1));
+  RG(run_gemm<C2>(c, P.t2, n, W.ETR, W.T1, W.T2));
+  RG(run_gemm<C2>(c, P.h, n, W.EBR, W.T2, W.HR));
+  RG(run_gemm<C2>(c, P.join, n, W.HL, W.HR, graw));
+  return cudaSuccess;
 }
 
 cudaError_t launch_env(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
                        const double2* QA, const double2* QB, void* graw) {
   const Plan& P = c->plan;
   Work& W = c->w;
-  if (c->cfg.precision == NTU_FP64) {
-    env_chain<double2>(c, n, Ta, Tb, QA, QB, graw);
-  } else {
-    to_f32(c, (long long)n * P.szT, Ta, W.Tac);
-    to_f32(c, (long long)n * P.szT, Tb, W.Tbc);
-    to_f32(c, (long long)n * P.szQ, QA, W.QAc);
-    to_f32(c, (long long)n * P.szQ, QB, W.QBc);
-    env_chain<float2>(c, n, W.Tac, W.Tbc, W.QAc, W.QBc, graw);
-  }
-  return cudaGetLastError();
+  if (c->cfg.precision == NTU_FP64) return env_chain<double2>(c, n, Ta, Tb, QA, QB, graw);
+  RG(to_f32(c, (long long)n * P.szT, Ta, W.Tac));
+  RG(to_f32(c, (long long)n * P.szT, Tb, W.Tbc));
+  RG(to_f32(c, (long long)n * P.szQ, QA, W.QAc));
+  RG(to_f32(c, (long long)n * P.szQ, QB, W.QBc));
+  return env_chain<float2>(c, n, W.Tac, W.Tbc, W.QAc, W.QBc, graw);
 }
 
 }  // namespace ntu

@@ -345,13 +345,16 @@ cudaError_t launch_gate_qr(ntu_ctx* c, int n, const double2* Ta, const double2* 
     attr = true;
   }
   k_gate_split<<<n, NTU_CTA, sm, c->stream>>>(P.d, P.r, swap_sites, G, W.GA, W.GB);
+  cudaError_t e = after_launch(c, "k_gate_split");
+  if (e != cudaSuccess) return e;
   int zsplit = (P.m * P.K + NTU_CTA * 8 - 1) / (NTU_CTA * 8);
   if (zsplit < 1) zsplit = 1;
   k_gated<<<dim3(n, 2, zsplit), NTU_CTA, 0, c->stream>>>(P.d, P.d_anc, P.D, P.r, Ta, Tb, W.GA,
                                                          W.GB, W.Mg);
+  e = after_launch(c, "k_gated");
+  if (e != cudaSuccess) return e;
   k_qr<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.m, P.K, W.Mg, W.Qcm, QA, RA, QB, RB);
-  c->launches += 3;
-  return cudaGetLastError();
+  return after_launch(c, "k_qr");
 }
 
 cudaError_t launch_recompose(ntu_ctx* c, int n, const double2* QA, const double2* QB,
@@ -360,31 +363,27 @@ cudaError_t launch_recompose(ntu_ctx* c, int n, const double2* QA, const double2
   const Plan& P = c->plan;
   k_recompose<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.dp, P.D, P.K, QA, QB, MA, MB, Ta_out,
                                                      Tb_out);
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_recompose");
 }
 
 cudaError_t launch_orient(ntu_ctx* c, int bond, const double2* A, const double2* B,
                           double2* Ta, double2* Tb) {
   const Plan& P = c->plan;
   k_orient<<<grid_for(P.szT), NTU_CTA, 0, c->stream>>>(P.dp, P.D, bond, A, B, Ta, Tb);
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_orient");
 }
 
 cudaError_t launch_deorient(ntu_ctx* c, int bond, const double2* Ta, const double2* Tb,
                             double2* A, double2* B) {
   const Plan& P = c->plan;
   k_deorient<<<grid_for(P.szT), NTU_CTA, 0, c->stream>>>(P.dp, P.D, bond, Ta, Tb, A, B);
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_deorient");
 }
 
 cudaError_t launch_site_gate(ntu_ctx* c, double2* A, double2* B, const double2* op) {
   const Plan& P = c->plan;
   k_site_gate<<<2, NTU_CTA, 0, c->stream>>>(P.d, P.d_anc, P.D, A, B, op);
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_site_gate");
 }
 
 cudaError_t launch_measure(ntu_ctx* c, const double2* T, const double2* N, const double2* op,
@@ -393,8 +392,7 @@ cudaError_t launch_measure(ntu_ctx* c, const double2* T, const double2* N, const
   Work& W = c->w;
   k_measure<<<1, NTU_CTA, 0, c->stream>>>(P.d, P.d_anc, P.D, T, N, op, W.mscr1, W.mscr2,
                                           W.medge, out);
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_measure");
 }
 
 }  // namespace ntu

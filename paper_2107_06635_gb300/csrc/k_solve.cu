@@ -32,11 +32,12 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
                                                     double* __restrict__ de,
                                                     double2* __restrict__ tau,
                                                     double2* __restrict__ pv,
-                                                    double* __restrict__ diag, int* status) {
+                                                    double* __restrict__ diag, int* status,
+                                                    int* paths) {
   extern __shared__ double chain[];      // 2 * ng
   __shared__ double sred[2 * NTU_WARPS];
   __shared__ int sh[4];
-  __shared__ int ok;
+  __shared__ int okflag;
   const int tid = threadIdx.x;
   const long long item = blockIdx.x;
   const size_t nn = (size_t)ng * ng;
@@ -57,27 +58,10 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
   n2 = block_sum(n2, sred);
   h2 = block_sum(h2, sred);
   const double herm = n2 > 0.0 ? sqrt(h2 / n2) : 0.0;
-  // 2. Cholesky of the lower triangle (column-major, right-looking)
-  if (tid == 0) ok = 1;
+  // 2. Cholesky of the lower triangle certifies positive definiteness
   __syncthreads();
-  for (int j = 0; j < ng; ++j) {
-    double piv = sc[(size_t)j * ng + j].x;
-    if (!(piv > 0.0) || !isfinite(piv)) { if (tid == 0) ok = 0; break; }
-    double rp = 1.0 / sqrt(piv);
-    double2* cj = sc + (size_t)j * ng;
-    for (int i = j + 1 + tid; i < ng; i += NTU_CTA) cj[i] = cscale(cj[i], rp);
-    __syncthreads();
-    const int m = ng - j - 1;
-    for (int idx = tid; idx < m * m; idx += NTU_CTA) {
-      int kk = idx / m, ii = idx % m;
-      if (ii < kk) continue;
-      int k = j + 1 + kk, i = j + 1 + ii;
-      double2* ck = sc + (size_t)k * ng;
-      ck[i] = csub(ck[i], cmul(cj[i], cconj(cj[k])));
-    }
-    __syncthreads();
-  }
-  __syncthreads();
+  int ok = cta_cholesky(sc, ng, 0.0, &okflag);
+  if (tid == 0 && paths) atomicAdd(paths + (ok ? 2 : 3), 1);
   double ratio = __longlong_as_double(0x7ff8000000000000ULL);   // NaN
   if (!ok) {
     // 3. full eigendecomposition and clipping of negative eigenvalues
@@ -145,6 +129,19 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
 }
 
 // ---------------------------------------------------------------- ALS
+// Candidate relative tolerances 1e-k of the pseudo-inverse (Eq. 4), as
+// correctly rounded decimal literals.
+__device__ __forceinline__ double als_tau(int k) {
+  switch (k) {
+    case 0: return 1e0;   case 1: return 1e-1;  case 2: return 1e-2;  case 3: return 1e-3;
+    case 4: return 1e-4;  case 5: return 1e-5;  case 6: return 1e-6;  case 7: return 1e-7;
+    case 8: return 1e-8;  case 9: return 1e-9;  case 10: return 1e-10; case 11: return 1e-11;
+    case 12: return 1e-12; case 13: return 1e-13; case 14: return 1e-14; case 15: return 1e-15;
+    case 16: return 1e-16; case 17: return 1e-17; case 18: return 1e-18; case 19: return 1e-19;
+    default: return 1e-20;
+  }
+}
+
 struct AlsShared {
   SvdSmem S;
   double2 MA[32 * 8];
@@ -153,13 +150,16 @@ struct AlsShared {
   double red[2 * NTU_WARPS];
   double eps0, tau_sel;
   int err;
+  int flag;
+  int n_fast, n_eig;
 };
 
 struct AlsArgs {
   int D, K, ng, nA, sweeps, kmin, kmax;
   const double2* g; const double2* RA; const double2* RB;
   double2* MA; double2* MB; double* info;
-  double2 *x0, *gx0, *Tm, *gA, *jv, *pv, *tauv;
+  int* path_counts;            // [fast, eig] solves, accumulated over items (may be NULL)
+  double2 *x0, *gx0, *Tm, *gA, *gC, *jv, *pv, *tauv;
   double *dv, *ev, *rc, *rs;
   int* rk;
   int rotcap;
@@ -183,6 +183,7 @@ __device__ void als_tilt(AlsShared& sm, const AlsArgs& a, int mode, const double
   }
   __syncthreads();
   cta_svd_small(sm.S, K);
+  if (tid == 0 && sm.S.bad) sm.err = ST_NUMERIC;
   for (int idx = tid; idx < K * D; idx += NTU_CTA) {
     int i = idx / D, q = idx % D;
     double2 u = cz(), vb = cz();
@@ -229,6 +230,41 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
   __syncthreads();
 }
 
+// Certified shortcut of the tolerance selection.  With B = max column sum of
+// |Re| + |Im| of gX (>= lambda_max) and tau_max the largest candidate, a
+// successful Cholesky factorisation of gX - (tau_max + 1e-12) B I proves
+// lambda_min > tau_max lambda_max (the 1e-12 B margin covers rounding), so every
+// candidate tolerance keeps every eigenpair: all candidates give the same
+// eps, the selection rule returns tau_max, and the pseudo-inverse is the
+// inverse.  Then M = gX^{-1} J is solved by Cholesky.  Returns 1 when solved;
+// 0 when not certified (gX untouched); 2 when certified but the unshifted
+// factorisation failed (gX overwritten; the caller rebuilds it).
+__device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2* gX,
+                              double2* gC, const double2* jv, double tau_max) {
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31, nA = a.nA;
+  double bmax = 0.0;
+  for (int c = wid; c < nA; c += NTU_WARPS) {
+    const double2* col = gX + (size_t)c * nA;
+    double s = 0.0;
+    for (int r = lid; r < nA; r += 32) s += fabs(col[r].x) + fabs(col[r].y);
+    s = warp_sum(s);
+    bmax = fmax(bmax, s);
+  }
+  bmax = block_max(bmax, sm.red);
+  for (int i = tid; i < nA * nA; i += NTU_CTA) gC[i] = gX[i];
+  __syncthreads();
+  if (!(bmax > 0.0) || !isfinite(bmax)) return 0;
+  if (!cta_cholesky(gC, nA, (tau_max + 1e-12) * bmax, &sm.flag)) return 0;
+  if (!cta_cholesky(gX, nA, 0.0, &sm.flag)) return 2;
+  for (int i = tid; i < nA; i += NTU_CTA) sm.y[i] = jv[i];
+  cta_cholesky_solve(gX, nA, sm.y);
+  double2* M = side == 0 ? sm.MA : sm.MB;
+  for (int i = tid; i < nA; i += NTU_CTA) M[i] = sm.y[i];
+  if (tid == 0) { sm.tau_sel = tau_max; sm.n_fast += 1; }
+  __syncthreads();
+  return 1;
+}
+
 // M = pinv_tau(gX) J with the tolerance of the grid that minimises
 // eps(tau) = eps0 - sum_{lambda_i > tau lambda_max} |y_i|^2 / lambda_i,
 // y = W^H J (Eq. 4 inserted in Eq. 3); ties within 1e-14 eps0 go to the
@@ -246,24 +282,21 @@ __device__ void als_solve(AlsShared& sm, const AlsArgs& a, int side, double2* gX
     if (st) sm.err = st;
     double lmax = dv[0];
     for (int i = 1; i < nA; ++i) lmax = fmax(lmax, dv[i]);
-    const double taus[21] = {1e0,   1e-1,  1e-2,  1e-3,  1e-4,  1e-5,  1e-6,
-                             1e-7,  1e-8,  1e-9,  1e-10, 1e-11, 1e-12, 1e-13,
-                             1e-14, 1e-15, 1e-16, 1e-17, 1e-18, 1e-19, 1e-20};
     int kmin = a.kmin < 0 ? 0 : a.kmin, kmax = a.kmax > 20 ? 20 : a.kmax;
-    double tsel = taus[kmin];
+    double tsel = als_tau(kmin);
     if (lmax > 0.0 && !st) {
       double emin = INFINITY;
       for (int k = kmin; k <= kmax; ++k) {
-        double thr = taus[k] * lmax, s = 0.0;
+        double thr = als_tau(k) * lmax, s = 0.0;
         for (int i = 0; i < nA; ++i)
           if (dv[i] > thr) s += cabs2(sm.y[i]) / dv[i];
         emin = fmin(emin, sm.eps0 - s);
       }
       for (int k = kmin; k <= kmax; ++k) {
-        double thr = taus[k] * lmax, s = 0.0;
+        double thr = als_tau(k) * lmax, s = 0.0;
         for (int i = 0; i < nA; ++i)
           if (dv[i] > thr) s += cabs2(sm.y[i]) / dv[i];
-        if (sm.eps0 - s <= emin + 1e-14 * sm.eps0) { tsel = taus[k]; break; }
+        if (sm.eps0 - s <= emin + 1e-14 * sm.eps0) { tsel = als_tau(k); break; }
       }
       double thr = tsel * lmax;
       for (int i = 0; i < nA; ++i)
@@ -273,6 +306,7 @@ __device__ void als_solve(AlsShared& sm, const AlsArgs& a, int side, double2* gX
       for (int i = 0; i < nA; ++i) sm.y[i] = cz();
     }
     sm.tau_sel = tsel;
+    sm.n_eig += 1;
   }
   __syncthreads();
   cta_apply_q(gX, nA, tauv, sm.y, false, sm.red);
@@ -305,7 +339,9 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   log.k = a.rk + item * (long long)a.rotcap;
   log.cap = a.rotcap;
   log.count = 0;
-  if (tid == 0) sm.err = 0;
+  double2* gC = a.gC + item * (long long)nA * nA;
+  const double tau_max = als_tau(a.kmin < 0 ? 0 : a.kmin);
+  if (tid == 0) { sm.err = 0; sm.n_fast = 0; sm.n_eig = 0; }
   // X0 = R_A R_B^T, x0 = vec(X0) with kA slow
   for (int idx = tid; idx < K * K; idx += NTU_CTA) {
     int i = idx / K, j = idx % K;
@@ -332,12 +368,13 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   // SVDU start (Fig. 2(c,d))
   als_tilt(sm, a, 2, x0);
   for (int s = 0; s < a.sweeps; ++s) {
-    als_tilt(sm, a, 0, nullptr);
-    als_reduced(sm, a, g, 0, Tm, gX, jv, gx0);
-    als_solve(sm, a, 0, gX, jv, pv, tauv, dv, ev, log);
-    als_tilt(sm, a, 1, nullptr);
-    als_reduced(sm, a, g, 1, Tm, gX, jv, gx0);
-    als_solve(sm, a, 1, gX, jv, pv, tauv, dv, ev, log);
+    for (int side = 0; side < 2; ++side) {
+      als_tilt(sm, a, side, nullptr);
+      als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
+      int f = als_solve_chol(sm, a, side, gX, gC, jv, tau_max);
+      if (f == 2) als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
+      if (f != 1) als_solve(sm, a, side, gX, jv, pv, tauv, dv, ev, log);
+    }
   }
   als_tilt(sm, a, 2, nullptr);      // balance (Fig. 5(d))
   // eps = x^H g x, x = vec(MA MB^T) - x0
@@ -369,6 +406,10 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
     a.info[item * 4 + 2] = e0v;
     a.info[item * 4 + 3] = sm.tau_sel;
     if (sm.err || !isfinite(delta) || !isfinite(eps)) raise_status(a.status, ST_NUMERIC);
+    if (a.path_counts) {
+      atomicAdd(a.path_counts + 0, sm.n_fast);
+      atomicAdd(a.path_counts + 1, sm.n_eig);
+    }
   }
 }
 
@@ -382,15 +423,15 @@ cudaError_t launch_repair(ntu_ctx* c, int n, const void* graw, int raw_is_f32, d
   if (raw_is_f32) {
     cudaFuncSetAttribute(k_repair<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_repair<float2><<<n, NTU_CTA, sm, c->stream>>>(P.ng, (const float2*)graw, g, W.gscr, W.gw,
-                                                    W.gz, W.geig, W.gtau, W.gp, diag, c->d_status);
+                                                    W.gz, W.geig, W.gtau, W.gp, diag, c->d_status,
+                                                    c->d_paths);
   } else {
     cudaFuncSetAttribute(k_repair<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_repair<double2><<<n, NTU_CTA, sm, c->stream>>>(P.ng, (const double2*)graw, g, W.gscr,
                                                      W.gw, W.gz, W.geig, W.gtau, W.gp, diag,
-                                                     c->d_status);
+                                                     c->d_status, c->d_paths);
   }
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_repair");
 }
 
 cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
@@ -401,14 +442,14 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   a.D = P.D; a.K = P.K; a.ng = P.ng; a.nA = P.nA; a.sweeps = c->cfg.als_sweeps;
   a.kmin = c->cfg.tau_kmin; a.kmax = c->cfg.tau_kmax;
   a.g = g; a.RA = RA; a.RB = RB; a.MA = MA; a.MB = MB; a.info = info;
-  a.x0 = W.x0; a.gx0 = W.gx0; a.Tm = W.Tm; a.gA = W.gA; a.jv = W.jv; a.pv = W.pv;
+  a.x0 = W.x0; a.gx0 = W.gx0; a.Tm = W.Tm; a.gA = W.gA; a.gC = W.gC; a.jv = W.jv; a.pv = W.pv;
+  a.path_counts = c->d_paths;
   a.tauv = W.tauv; a.dv = W.dv; a.ev = W.ev; a.rc = W.rc; a.rs = W.rs; a.rk = W.rk;
   a.rotcap = W.rotcap; a.status = c->d_status;
   size_t sm = sizeof(AlsShared);
   cudaFuncSetAttribute(k_als, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_als<<<n, NTU_CTA, sm, c->stream>>>(a);
-  c->launches += 1;
-  return cudaGetLastError();
+  return after_launch(c, "k_als");
 }
 
 }  // namespace ntu

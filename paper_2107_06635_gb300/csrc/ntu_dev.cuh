@@ -142,6 +142,7 @@ struct SvdSmem {
   double red[2 * NTU_WARPS];
   int perm[32];
   int rotated;
+  int bad;        // set when a singular value came out non-finite
 };
 
 __device__ inline void cta_svd_small(SvdSmem& S, int n) {
@@ -213,11 +214,21 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
     if (lane == 0) S.s[c] = sqrt(a);
   }
   __syncthreads();
-  if (tid < n) {          // rank of column tid in descending order (stable)
+  if (tid < 32) S.perm[tid] = tid;
+  if (tid == 0) {
+    int bad = 0;
+    for (int j = 0; j < n; ++j) bad |= !isfinite(S.s[j]);
+    S.bad = bad;
+  }
+  __syncthreads();
+  if (tid < n) {          // rank of column tid in descending order: a strict total
+    // order in which non-finite values rank last, so perm is a permutation
     double sv = S.s[tid];
+    if (!isfinite(sv)) sv = -1.0;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
       double sj = S.s[j];
+      if (!isfinite(sj)) sj = -1.0;
       rank += (sj > sv) || (sj == sv && j < tid);
     }
     S.perm[rank] = tid;
@@ -228,20 +239,20 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
     int r = i & 31, k = i >> 5;
     double2 u = cz();
     if (k < n && r < n) {
-      int src = S.perm[k];
+      int src = S.perm[k] & 31;
       double sv = S.s[src];
-      if (sv > 0.0) u = cscale(S.A[src * 32 + r], 1.0 / sv);
+      if (sv > 0.0 && isfinite(sv)) u = cscale(S.A[src * 32 + r], 1.0 / sv);
     }
     S.W[i] = u;
   }
   __syncthreads();
   for (int i = tid; i < 32 * 32; i += NTU_CTA) {
     int r = i & 31, k = i >> 5;
-    S.A[i] = (k < n && r < n) ? S.V[S.perm[k] * 32 + r] : cz();
+    S.A[i] = (k < n && r < n) ? S.V[(S.perm[k] & 31) * 32 + r] : cz();
   }
   __syncthreads();
   double sv_sorted = 0.0;
-  if (tid < n) sv_sorted = S.s[S.perm[tid]];
+  if (tid < n) sv_sorted = S.s[S.perm[tid] & 31];
   __syncthreads();
   if (tid < n) S.s[tid] = sv_sorted;
   // W = U (sorted), A = V (sorted); move V to V, U to A
@@ -261,7 +272,7 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
       if (m > 0.0 && sqrt(cabs2(S.A[k * 32 + r])) >= (1.0 - 1e-10) * m) piv = min(piv, r);
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(mask, piv, o));
-    if (m > 0.0) {
+    if (m > 0.0 && isfinite(m) && piv < n) {
       double2 up = S.A[k * 32 + piv];
       double a = sqrt(cabs2(up));
       double2 ph = make_double2(up.x / a, -up.y / a);
@@ -470,6 +481,58 @@ __device__ inline int cta_tridiag_qr_z(double* d, double* e, int n, double* Z, d
   int st = shared_state[3];
   __syncthreads();
   return st;
+}
+
+// ------------------------------------------------------------ Cholesky
+// In-place lower Cholesky factorisation of (A - shift * I) for a Hermitian A
+// (column-major, leading dimension n, lower triangle referenced).  Returns 1
+// if every pivot was positive and finite (the shifted matrix is numerically
+// positive definite), 0 otherwise.  `flag`: one shared int.
+__device__ inline int cta_cholesky(double2* __restrict__ A, int n, double shift, int* flag) {
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
+  if (tid == 0) *flag = 1;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    double piv = A[(size_t)j * n + j].x - shift;
+    if (!(piv > 0.0) || !isfinite(piv)) { if (tid == 0) *flag = 0; break; }
+    double sp = sqrt(piv), rp = 1.0 / sp;
+    double2* cj = A + (size_t)j * n;
+    __syncthreads();
+    if (tid == 0) cj[j] = make_double2(sp, 0.0);
+    for (int i = j + 1 + tid; i < n; i += NTU_CTA) cj[i] = cscale(cj[i], rp);
+    __syncthreads();
+    for (int k = j + 1 + wid; k < n; k += NTU_WARPS) {
+      double2 lk = cconj(cj[k]);
+      double2* ck = A + (size_t)k * n;
+      for (int i = k + lid; i < n; i += 32) ck[i] = csub(ck[i], cmul(cj[i], lk));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  int ok = *flag;
+  __syncthreads();
+  return ok;
+}
+
+// Solve (L L^H) x = b in place with the factor from cta_cholesky.
+__device__ inline void cta_cholesky_solve(const double2* __restrict__ L, int n, double2* b) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < n; ++j) {           // L y = b
+    __syncthreads();
+    double2 yj = cscale(b[j], 1.0 / L[(size_t)j * n + j].x);
+    __syncthreads();
+    if (tid == 0) b[j] = yj;
+    const double2* cj = L + (size_t)j * n;
+    for (int i = j + 1 + tid; i < n; i += NTU_CTA) b[i] = csub(b[i], cmul(cj[i], yj));
+  }
+  for (int j = n - 1; j >= 0; --j) {      // L^H x = y
+    __syncthreads();
+    double2 xj = cscale(b[j], 1.0 / L[(size_t)j * n + j].x);
+    __syncthreads();
+    if (tid == 0) b[j] = xj;
+    for (int i = tid; i < j; i += NTU_CTA) b[i] = csub(b[i], cmul(cconj(L[(size_t)i * n + j]), xj));
+  }
+  __syncthreads();
 }
 
 // u <- Z u (rotations replayed in reverse), single thread.

@@ -46,7 +46,7 @@ struct Work {
   double2 *gtau, *gp;         // reflector factors, vector scratch (ng each)
   double *diag;               // 3 per item
   // ALS scratch
-  double2 *x0, *gx0, *Tm, *gA, *jv, *pv, *tauv;
+  double2 *x0, *gx0, *Tm, *gA, *gC, *jv, *pv, *tauv;
   double *dv, *ev, *rc, *rs;
   int *rk;
   int rotcap;
@@ -79,12 +79,17 @@ struct ntu_ctx {
   size_t env_es;      // element size of the environment buffers
   int profiling;
   cudaEvent_t ev[6];
+  int* d_paths;       // [ALS Cholesky, ALS eigen, repair Cholesky, repair eigen] counts
+  int debug_sync;     // synchronise and check after every launch (NTU_DEBUG_SYNC=1)
 };
 
 namespace ntu {
 
 // error helper: record message, return status
 int fail(ntu_ctx* c, int status, const char* fmt, ...);
+// Called after every launch: counts it and, in debug mode, synchronises and
+// reports the first failing kernel by name.
+cudaError_t after_launch(ntu_ctx* c, const char* name);
 
 // plans and tables (k_env.cu)
 int plan_build(ntu_ctx* c);

@@ -118,6 +118,14 @@ def integer_site_tensor(rng: np.random.Generator, d_p: int, D: int, lo: int = -3
     return np.ascontiguousarray(t.astype(np.complex128))
 
 
+def sparse_integer_array(rng: np.random.Generator, shape, density: float) -> np.ndarray:
+    """Complex array with real and imaginary parts in {-1, 0, 1}, each entry
+    kept with probability `density` (else 0)."""
+    v = rng.integers(-1, 2, shape) + 1j * rng.integers(-1, 2, shape)
+    keep = rng.random(shape) < density
+    return np.ascontiguousarray((v * keep).astype(np.complex128))
+
+
 def product_state(psi: np.ndarray, D: int, d_anc: int = 1) -> np.ndarray:
     """A D=1 product state zero-padded to bond dimension D:
     T[p, 0, 0, 0, 0] = psi[p], all other entries 0."""

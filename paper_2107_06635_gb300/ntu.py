@@ -61,6 +61,7 @@ _SIGS = {
     "ntu_last_launch_count": [_P],
     "ntu_set_profiling": [_P, _I],
     "ntu_stage_times": [_P, _P],
+    "ntu_solver_paths": [_P, _P],
 }
 
 
@@ -248,3 +249,11 @@ class Context:
         ms = np.empty(5)
         self._ck(self.lib.ntu_stage_times(self.h, _ptr(ms)))
         return ms
+
+    def solver_paths(self):
+        """Counts since the last call: ALS Cholesky-certified solves, ALS
+        eigen solves, metrics certified PD, metrics eigen-repaired."""
+        c = np.zeros(4, dtype=np.int32)
+        self._ck(self.lib.ntu_solver_paths(self.h, _ptr(c)))
+        return {"als_cholesky": int(c[0]), "als_eigen": int(c[1]),
+                "repair_cholesky": int(c[2]), "repair_eigen": int(c[3])}
