@@ -34,6 +34,12 @@ cudaError_t ntu::after_launch(ntu_ctx* c, const char* name) {
   }
   if (e != cudaSuccess && c->debug_sync)
     fprintf(stderr, "ntu: kernel %s failed: %s\n", name, cudaGetErrorString(e));
+  if (e == cudaSuccess && c->debug_sync) {
+    int st[2] = {0, 0};
+    if (cudaMemcpy(st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess && st[0])
+      fprintf(stderr, "ntu: status %d (reason 0x%x) set by or before kernel %s (launch %d)\n",
+              st[0], st[1], name, c->launches);
+  }
   return e;
 }
 
@@ -141,15 +147,17 @@ void carve(ntu_ctx* c, Carver& cv) {
 }  // namespace
 
 static int check_status(ntu_ctx* c) {
-  int st = 0;
+  int st[2] = {0, 0};
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");
-  CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
-  if (st != 0) {
-    int zero = 0;
-    cudaMemcpy(c->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-    return fail(c, st, "device raised status %d (%s)", st,
-                st == NTU_ENUMERIC ? "non-finite value or solver non-convergence"
-                                   : "bounded wait ran out");
+  CK(cudaMemcpy(st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost), "read status");
+  if (st[0] != 0) {
+    int zero[2] = {0, 0};
+    cudaMemcpy(c->d_status, zero, sizeof(zero), cudaMemcpyHostToDevice);
+    return fail(c, st[0], "device raised status %d (%s; reason bits 0x%x: 1 SVD non-finite, "
+                "2 ALS eigen-solver, 4 ALS non-finite error, 8 repair eigen-solver, "
+                "16 metric trace not positive)", st[0],
+                st[0] == NTU_ENUMERIC ? "non-finite value or solver non-convergence"
+                                      : "bounded wait ran out", st[1]);
   }
   return NTU_OK;
 }

@@ -102,11 +102,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_qr(int m, int K, double2* __restric
   double2* Qc = Qcm + ((size_t)item * 2 + side) * m * K;
   for (int j = 0; j < K; ++j) {
     double2* col = M + (size_t)j * m;
-    double xn = 0.0;
-    for (int i = j + 1 + tid; i < m; i += NTU_CTA) xn += cabs2(col[i]);
-    xn = block_sum(xn, sred);
-    double2 alpha = col[j];
-    Reflector R = make_reflector(alpha, xn);
+    Reflector R = cta_reflector(col + j, m - j, sred);
     __syncthreads();
     for (int i = j + 1 + tid; i < m; i += NTU_CTA) col[i] = cmul(col[i], R.scale);
     if (tid == 0) { taus[j] = R.tau; betas[j] = R.beta; col[j] = make_double2(1.0, 0.0); }

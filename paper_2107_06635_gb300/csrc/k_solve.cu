@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
     __syncthreads();
     cta_hetrd(sc, ng, dd, ee, ta, pp, sred);
     int st = cta_tridiag_qr_z(dd, ee, ng, Zi, chain, sh);
-    if (st && tid == 0) raise_status(status, st);
+    if (st && tid == 0) raise_status(status, st, WHY_REPAIR_QR);
     // W = Q Z, one column per thread
     for (int k = tid; k < ng; k += NTU_CTA) {
       double2* col = Wi + (size_t)k * ng;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
   for (int i = tid; i < ng; i += NTU_CTA) tr += gi[(size_t)i * ng + i].x;
   tr = block_sum(tr, sred);
   if (!(tr > 0.0) || !isfinite(tr)) {
-    if (tid == 0) raise_status(status, ST_NUMERIC);
+    if (tid == 0) raise_status(status, ST_NUMERIC, WHY_REPAIR_TRACE);
     tr = 1.0;
   }
   const double inv = 1.0 / tr;
@@ -183,7 +183,7 @@ __device__ void als_tilt(AlsShared& sm, const AlsArgs& a, int mode, const double
   }
   __syncthreads();
   cta_svd_small(sm.S, K);
-  if (tid == 0 && sm.S.bad) sm.err = ST_NUMERIC;
+  if (tid == 0 && sm.S.bad) sm.err |= WHY_SVD_NONFINITE;
   for (int idx = tid; idx < K * D; idx += NTU_CTA) {
     int i = idx / D, q = idx % D;
     double2 u = cz(), vb = cz();
@@ -279,7 +279,7 @@ __device__ void als_solve(AlsShared& sm, const AlsArgs& a, int side, double2* gX
   cta_apply_q(gX, nA, tauv, sm.y, true, sm.red);
   if (tid == 0) {
     int st = tridiag_qr(dv, ev, nA, log, sm.y);
-    if (st) sm.err = st;
+    if (st) sm.err |= WHY_ALS_QR;
     double lmax = dv[0];
     for (int i = 1; i < nA; ++i) lmax = fmax(lmax, dv[i]);
     int kmin = a.kmin < 0 ? 0 : a.kmin, kmax = a.kmax > 20 ? 20 : a.kmax;
@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
     a.info[item * 4 + 1] = delta;
     a.info[item * 4 + 2] = e0v;
     a.info[item * 4 + 3] = sm.tau_sel;
-    if (sm.err || !isfinite(delta) || !isfinite(eps)) raise_status(a.status, ST_NUMERIC);
+    if (sm.err || !isfinite(delta) || !isfinite(eps))
+      raise_status(a.status, ST_NUMERIC, sm.err | ((!isfinite(delta) || !isfinite(eps)) ? WHY_ALS_NONFINITE : 0));
     if (a.path_counts) {
       atomicAdd(a.path_counts + 0, sm.n_fast);
       atomicAdd(a.path_counts + 1, sm.n_eig);

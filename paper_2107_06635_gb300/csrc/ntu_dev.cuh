@@ -39,9 +39,15 @@ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+// a / b by Smith's method (no squares of b, so no underflow or overflow for
+// tiny or huge b).
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  double den = cabs2(b);
-  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, den = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  }
+  double r = b.x / b.y, den = b.y + b.x * r;
+  return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
 }
 
 // --------------------------------------------------------------- reductions
@@ -102,8 +108,16 @@ __device__ __forceinline__ double block_max(double v, double* sbuf) {
 // Error codes a kernel may raise through the status word (same values as
 // ntu_status in include/ntu.h).
 enum { ST_NUMERIC = 4, ST_TIMEOUT = 5 };
-__device__ __forceinline__ void raise_status(int* status, int code) {
-  if (status) atomicMax(status, code);
+// Reason bits recorded next to the status word (status[1]).
+enum {
+  WHY_SVD_NONFINITE = 1, WHY_ALS_QR = 2, WHY_ALS_NONFINITE = 4, WHY_REPAIR_QR = 8,
+  WHY_REPAIR_TRACE = 16
+};
+__device__ __forceinline__ void raise_status(int* status, int code, int why = 0) {
+  if (status) {
+    atomicMax(status, code);
+    if (why) atomicOr(status + 1, why);
+  }
 }
 
 // ------------------------------------------------- Householder reflectors
@@ -112,14 +126,31 @@ __device__ __forceinline__ void raise_status(int* status, int code) {
 // (the convention of the standard complex Householder QR).  Given alpha and
 // ||x||^2, returns tau, beta and the factor that scales x into v.
 struct Reflector { double2 tau; double beta; double2 scale; };
-__device__ __forceinline__ Reflector make_reflector(double2 alpha, double xnorm2) {
+
+// CTA-wide reflector of the vector v[0..len) = [alpha; x].  The norm is taken
+// of the vector divided by its largest component, so that entries far below
+// the square root of the smallest normal number neither vanish from nor
+// zero out the norm.  Reads v only; every thread returns the same result.
+__device__ inline Reflector cta_reflector(const double2* v, int len, double* sred) {
+  const int tid = threadIdx.x;
+  double mx = 0.0;
+  for (int i = 1 + tid; i < len; i += NTU_CTA) mx = fmax(mx, fmax(fabs(v[i].x), fabs(v[i].y)));
+  mx = block_max(mx, sred);
+  const double2 alpha = v[0];
+  const double amax = fmax(mx, fmax(fabs(alpha.x), fabs(alpha.y)));
+  double xs2 = 0.0;
+  if (mx > 0.0) {
+    const double inv = 1.0 / amax;
+    for (int i = 1 + tid; i < len; i += NTU_CTA) xs2 += cabs2(cscale(v[i], inv));
+  }
+  xs2 = block_sum(xs2, sred);
   Reflector r;
-  if (xnorm2 == 0.0 && alpha.y == 0.0) {
+  if (mx == 0.0 && alpha.y == 0.0) {
     r.tau = cz(); r.beta = alpha.x; r.scale = make_double2(1.0, 0.0);
     return r;
   }
-  double nrm = sqrt(cabs2(alpha) + xnorm2);
-  double beta = alpha.x >= 0.0 ? -nrm : nrm;
+  const double nrm = amax * sqrt(cabs2(cscale(alpha, 1.0 / amax)) + xs2);
+  const double beta = alpha.x >= 0.0 ? -nrm : nrm;
   r.beta = beta;
   r.tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
   r.scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
@@ -297,11 +328,7 @@ __device__ inline void cta_hetrd(double2* __restrict__ A, int n, double* d, doub
   for (int j = 0; j < n - 1; ++j) {
     const int m = n - j - 1;                 // length of the reflected part
     double2* col = A + (size_t)j * n + j + 1;   // A[j+1:, j]
-    double xn = 0.0;
-    for (int i = 1 + tid; i < m; i += NTU_CTA) xn += cabs2(col[i]);
-    xn = block_sum(xn, sred);
-    double2 alpha = col[0];
-    Reflector R = make_reflector(alpha, xn);
+    Reflector R = cta_reflector(col, m, sred);
     __syncthreads();
     for (int i = 1 + tid; i < m; i += NTU_CTA) col[i] = cmul(col[i], R.scale);
     if (tid == 0) {
