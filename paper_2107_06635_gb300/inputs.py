@@ -143,6 +143,20 @@ def plus_z_state(D: int) -> np.ndarray:
     return product_state(np.array([1, 0]), D)
 
 
+def quench_start(D: int, mix: float = 1e-2, seed: int = 123):
+    """Initial (A, B) of the transverse-field quench: the polarised state
+    |+x> zero-padded to bond dimension D plus a seeded random admixture of
+    relative weight `mix`, which lifts the exact zero modes of the padded
+    bonds (with mix=0 the pair is the bare padded product state)."""
+    rng = np.random.default_rng(seed)
+    A = plus_x_state(D)
+    B = plus_x_state(D)
+    if mix:
+        A = A + mix * random_site_tensor(rng, 2, D)
+        B = B + mix * random_site_tensor(rng, 2, D)
+    return A / np.linalg.norm(A), B / np.linalg.norm(B)
+
+
 def purification_state(D: int) -> np.ndarray:
     """Infinite-temperature purification: (|00> + |11>)/sqrt(2) on
     (physical, ancilla) at every site, p = s_phys * 2 + s_anc."""
