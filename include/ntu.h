@@ -187,6 +187,28 @@ int ntu_stage_times(ntu_ctx* ctx, double* ms_out);
  * eigendecomposition.  Synchronises the context's stream. */
 int ntu_solver_paths(ntu_ctx* ctx, int* counts);
 
+/* ---- a stage for callers that cannot allocate device memory ----------- */
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc (a framework that owns all device memory through
+ * its own pool, or code that must not trigger the device-wide
+ * synchronisation of cudaMalloc/cudaFree), and so cannot create an ntu_ctx.
+ * It computes exactly what ntu_batch_gate_qr_dev computes for one item
+ * (gate split, gate application, QR with positive diag(R)) from device
+ * pointers Ta, Tb (d_p D^4 complex each), gate (d_phys^4 complex) into
+ * QA, QB ((d_p D^3) x K) and RA, RB (K x K), queued on `stream` (NULL: the
+ * legacy default stream), and allocates nothing: its scratch is one fixed
+ * 4 MiB array in device memory, held by every GPU that loads the library
+ * until the process exits.  Sizes needing more than 4 MiB of scratch
+ * (16 * (2 d^2 r + 4 (d_p D^3)(D r)) bytes) are rejected with NTU_EINVAL.
+ * The first call on a device looks up the array's device address, so make
+ * that first call before any stream capture.  Every call reuses the same
+ * array: calls that overlap on the GPU (different streams, or several host
+ * threads) race on it and must be serialised by the caller.  Errors are
+ * reported through ntu_last_error(NULL). */
+int ntu_gate_qr_noalloc(int D, int d_phys, int d_anc, int r, const double* Ta,
+                        const double* Tb, const double* gate, double* QA, double* RA,
+                        double* QB, double* RB, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ _SIGS = {
     "ntu_set_profiling": [_P, _I],
     "ntu_stage_times": [_P, _P],
     "ntu_solver_paths": [_P, _P],
+    "ntu_gate_qr_noalloc": [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P],
 }
 
 
