@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_qr(int m, int K, double2* __restric
         for (int i = j + lid; i < m; i += 32) dot = cfmac(col[i], cc[i], dot);
         dot = warp_sum2(dot);
         double2 f = cmul(ct, dot);
-        for (int i = j + lid; i < m; i += 32) cc[i] = csub(cc[i], cmul(f, col[i]));
+        for (int i = j + lid; i < m; i += 32) cc[i] = cfms(f, col[i], cc[i]);
       }
       __syncthreads();
     }
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_qr(int m, int K, double2* __restric
       for (int i = j + lid; i < m; i += 32) dot = cfmac(v[i], qc[i], dot);
       dot = warp_sum2(dot);
       double2 f = cmul(t, dot);
-      for (int i = j + lid; i < m; i += 32) qc[i] = csub(qc[i], cmul(f, v[i]));
+      for (int i = j + lid; i < m; i += 32) qc[i] = cfms(f, v[i], qc[i]);
     }
     __syncthreads();
   }

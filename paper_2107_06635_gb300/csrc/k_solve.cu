@@ -147,6 +147,7 @@ struct AlsShared {
   double2 MA[32 * 8];
   double2 MB[32 * 8];
   double2 y[256];
+  double2 y2[256];
   double red[2 * NTU_WARPS];
   double eps0, tau_sel;
   int err;
@@ -213,9 +214,11 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
     Tm[idx] = acc;
   }
   __syncthreads();
-  // gX[(f',q'),(f,q)] = sum_c' conj(F[c'][q']) Tm[f'*sf + c'*sc][(f,q)]
+  // gX[(f',q'),(f,q)] = sum_c' conj(F[c'][q']) Tm[f'*sf + c'*sc][(f,q)], lower
+  // triangle only (gX is Hermitian; als_mirror fills the rest when needed)
   for (int idx = tid; idx < nA * nA; idx += NTU_CTA) {
     int col = idx / nA, row = idx % nA, f1 = row / D, q1 = row % D;
+    if (row < col) continue;
     double2 acc = cz();
     for (int c = 0; c < K; ++c)
       acc = cfmac(F[c * D + q1], Tm[(size_t)(f1 * sf + c * sc) * nA + col], acc);
@@ -232,37 +235,84 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
 
 // Certified shortcut of the tolerance selection.  With B = max column sum of
 // |Re| + |Im| of gX (>= lambda_max) and tau_max the largest candidate, a
-// successful Cholesky factorisation of gX - (tau_max + 1e-12) B I proves
-// lambda_min > tau_max lambda_max (the 1e-12 B margin covers rounding), so every
-// candidate tolerance keeps every eigenpair: all candidates give the same
-// eps, the selection rule returns tau_max, and the pseudo-inverse is the
-// inverse.  Then M = gX^{-1} J is solved by Cholesky.  Returns 1 when solved;
-// 0 when not certified (gX untouched); 2 when certified but the unshifted
-// factorisation failed (gX overwritten; the caller rebuilds it).
-__device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2* gX,
+// successful Cholesky factorisation L L^H = gX - sigma I, sigma = (tau_max +
+// 1e-12) B, proves lambda_min > tau_max lambda_max (the 1e-12 B margin covers
+// rounding), so every candidate tolerance keeps every eigenpair: all
+// candidates give the same eps, the selection rule returns tau_max, and the
+// pseudo-inverse is the inverse.  M = gX^{-1} J then follows from the same
+// factor by the fixed-point iteration (L L^H) v_{k+1} = J - sigma v_k (its
+// fixed point solves gX v = J), which contracts by
+// sigma / (lambda_min - sigma).  Reads only the lower triangle
+// of gX and leaves gX untouched.  Returns 1 when solved, 0 otherwise.
+__device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, const double2* gX,
                               double2* gC, const double2* jv, double tau_max) {
   const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31, nA = a.nA;
   double bmax = 0.0;
   for (int c = wid; c < nA; c += NTU_WARPS) {
-    const double2* col = gX + (size_t)c * nA;
     double s = 0.0;
-    for (int r = lid; r < nA; r += 32) s += fabs(col[r].x) + fabs(col[r].y);
+    for (int r = c + lid; r < nA; r += 32) {               // column c, rows >= c
+      double2 v = gX[(size_t)c * nA + r];
+      s += fabs(v.x) + fabs(v.y);
+    }
+    for (int r = lid; r < c; r += 32) {                     // row c, columns < c
+      double2 v = gX[(size_t)r * nA + c];
+      s += fabs(v.x) + fabs(v.y);
+    }
     s = warp_sum(s);
     bmax = fmax(bmax, s);
   }
   bmax = block_max(bmax, sm.red);
-  for (int i = tid; i < nA * nA; i += NTU_CTA) gC[i] = gX[i];
+  for (int idx = tid; idx < nA * nA; idx += NTU_CTA)
+    if (idx % nA >= idx / nA) gC[idx] = gX[idx];
   __syncthreads();
   if (!(bmax > 0.0) || !isfinite(bmax)) return 0;
-  if (!cta_cholesky(gC, nA, (tau_max + 1e-12) * bmax, &sm.flag)) return 0;
-  if (!cta_cholesky(gX, nA, 0.0, &sm.flag)) return 2;
-  for (int i = tid; i < nA; i += NTU_CTA) sm.y[i] = jv[i];
-  cta_cholesky_solve(gX, nA, sm.y);
+  const double sigma = (tau_max + 1e-12) * bmax;
+  if (!cta_cholesky(gC, nA, sigma, &sm.flag)) return 0;
+  if (wid == 0) {
+    for (int i = lid; i < nA; i += 32) sm.y[i] = cz();
+    __syncwarp();
+    int conv = 0;
+    double prev = INFINITY;
+    for (int it = 0; it < 60 && !conv; ++it) {
+      for (int i = lid; i < nA; i += 32) {
+        double2 v = sm.y[i], j = jv[i];
+        sm.y2[i] = make_double2(fma(-sigma, v.x, j.x), fma(-sigma, v.y, j.y));
+      }
+      __syncwarp();
+      warp_cholesky_solve(gC, nA, sm.y2);
+      double diff = 0.0, vmax = 0.0;
+      for (int i = lid; i < nA; i += 32) {
+        double2 n = sm.y2[i], o = sm.y[i];
+        diff = fmax(diff, fabs(n.x - o.x) + fabs(n.y - o.y));
+        vmax = fmax(vmax, fabs(n.x) + fabs(n.y));
+        sm.y[i] = n;
+      }
+      diff = warp_max(diff);
+      vmax = warp_max(vmax);
+      __syncwarp();
+      if (diff <= 1e-15 * vmax) conv = 1;                         // converged
+      else if (it >= 3 && diff >= 0.5 * prev && diff <= 1e-13 * vmax) conv = 1;  // rounding floor
+      prev = diff;
+    }
+    if (lid == 0) sm.flag = conv;
+  }
+  __syncthreads();
+  if (!sm.flag) return 0;
   double2* M = side == 0 ? sm.MA : sm.MB;
   for (int i = tid; i < nA; i += NTU_CTA) M[i] = sm.y[i];
   if (tid == 0) { sm.tau_sel = tau_max; sm.n_fast += 1; }
   __syncthreads();
   return 1;
+}
+
+// Fill the upper triangle of gX from its lower triangle (the eigen path
+// works on full storage).
+__device__ void als_mirror(double2* gX, int nA) {
+  for (int idx = threadIdx.x; idx < nA * nA; idx += NTU_CTA) {
+    int col = idx / nA, row = idx % nA;
+    if (row < col) gX[idx] = cconj(gX[(size_t)row * nA + col]);
+  }
+  __syncthreads();
 }
 
 // M = pinv_tau(gX) J with the tolerance of the grid that minimises
@@ -371,9 +421,10 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
     for (int side = 0; side < 2; ++side) {
       als_tilt(sm, a, side, nullptr);
       als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
-      int f = als_solve_chol(sm, a, side, gX, gC, jv, tau_max);
-      if (f == 2) als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
-      if (f != 1) als_solve(sm, a, side, gX, jv, pv, tauv, dv, ev, log);
+      if (!als_solve_chol(sm, a, side, gX, gC, jv, tau_max)) {
+        als_mirror(gX, nA);
+        als_solve(sm, a, side, gX, jv, pv, tauv, dv, ev, log);
+      }
     }
   }
   als_tilt(sm, a, 2, nullptr);      // balance (Fig. 5(d))

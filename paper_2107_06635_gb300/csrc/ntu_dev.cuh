@@ -36,6 +36,18 @@ __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {
   c.y = fma(a.x, b.y, c.y); c.y = fma(-a.y, b.x, c.y);
   return c;
 }
+// c - a * b
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+  c.x = fma(-a.x, b.x, c.x); c.x = fma(a.y, b.y, c.x);
+  c.y = fma(-a.x, b.y, c.y); c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+// c - a * conj(b)
+__device__ __forceinline__ double2 cfmsc(double2 a, double2 b, double2 c) {
+  c.x = fma(-a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y); c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
@@ -352,15 +364,15 @@ __device__ inline void cta_hetrd(double2* __restrict__ A, int n, double* d, doub
       for (int i = tid; i < m; i += NTU_CTA) vp = cfmac(col[i], p[i], vp);
       vp = block_sum2(vp, sred);
       double2 f = cscale(cmul(cconj(R.tau), vp), 0.5);
-      for (int i = tid; i < m; i += NTU_CTA) p[i] = csub(p[i], cmul(f, col[i]));
+      for (int i = tid; i < m; i += NTU_CTA) p[i] = cfms(f, col[i], p[i]);
       __syncthreads();
       // A22 -= v w^H + w v^H
       for (int idx = tid; idx < m * m; idx += NTU_CTA) {
         int k = idx % m, i = idx / m;          // row k, column i
         double2 a = A22[(size_t)i * n + k];
         double2 vk = col[k], wk = p[k], vi = col[i], wi = p[i];
-        a = csub(a, cmul(vk, cconj(wi)));
-        a = csub(a, cmul(wk, cconj(vi)));
+        a = cfmsc(vk, wi, a);
+        a = cfmsc(wk, vi, a);
         A22[(size_t)i * n + k] = a;
       }
       __syncthreads();
@@ -385,7 +397,7 @@ __device__ inline void cta_apply_q(const double2* __restrict__ A, int n, const d
     for (int i = tid; i < m; i += NTU_CTA) s = cfmac(i == 0 ? make_double2(1.0, 0.0) : v[i], bb[i], s);
     s = block_sum2(s, sred);
     double2 f = adjoint ? cmul(cconj(t), s) : cmul(t, s);
-    for (int i = tid; i < m; i += NTU_CTA) bb[i] = csub(bb[i], cmul(f, i == 0 ? make_double2(1.0, 0.0) : v[i]));
+    for (int i = tid; i < m; i += NTU_CTA) bb[i] = cfms(f, i == 0 ? make_double2(1.0, 0.0) : v[i], bb[i]);
     __syncthreads();
   }
 }
@@ -529,9 +541,9 @@ __device__ inline int cta_cholesky(double2* __restrict__ A, int n, double shift,
     for (int i = j + 1 + tid; i < n; i += NTU_CTA) cj[i] = cscale(cj[i], rp);
     __syncthreads();
     for (int k = j + 1 + wid; k < n; k += NTU_WARPS) {
-      double2 lk = cconj(cj[k]);
+      const double2 lk = cj[k];
       double2* ck = A + (size_t)k * n;
-      for (int i = k + lid; i < n; i += 32) ck[i] = csub(ck[i], cmul(cj[i], lk));
+      for (int i = k + lid; i < n; i += 32) ck[i] = cfmsc(cj[i], lk, ck[i]);
     }
     __syncthreads();
   }
@@ -539,6 +551,28 @@ __device__ inline int cta_cholesky(double2* __restrict__ A, int n, double shift,
   int ok = *flag;
   __syncthreads();
   return ok;
+}
+
+// Solve (L L^H) x = b in place with the factor from cta_cholesky, by one
+// warp (no CTA barriers): lane l owns the entries i = l (mod 32) of b, which
+// lives in shared memory.  Must be called by all 32 lanes of one warp.
+__device__ inline void warp_cholesky_solve(const double2* __restrict__ L, int n, double2* b) {
+  const int lid = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {           // L y = b
+    if ((j & 31) == lid) b[j] = cscale(b[j], 1.0 / L[(size_t)j * n + j].x);
+    __syncwarp();
+    const double2 yj = b[j];
+    const double2* cj = L + (size_t)j * n;
+    for (int i = j + 1 + ((lid - j - 1) & 31); i < n; i += 32) b[i] = cfms(cj[i], yj, b[i]);
+    __syncwarp();
+  }
+  for (int j = n - 1; j >= 0; --j) {      // L^H x = y
+    if ((j & 31) == lid) b[j] = cscale(b[j], 1.0 / L[(size_t)j * n + j].x);
+    __syncwarp();
+    const double2 xj = b[j];
+    for (int i = lid; i < j; i += 32) b[i] = cfmsc(xj, L[(size_t)i * n + j], b[i]);
+    __syncwarp();
+  }
 }
 
 // Solve (L L^H) x = b in place with the factor from cta_cholesky.
