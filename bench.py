@@ -63,6 +63,22 @@ def als_flops(D, r, sweeps):
     return sweeps * per_sweep + 2 * 8.0 * ng * ng
 
 
+def env_roof(precision, achieved, peaks):
+    """Environment throughput against the peak of the pipe it runs on: the
+    BF16 tensor cores (measured dense peak; the split products issue 3x the
+    algorithmic flops), FP32 FMA or FP64."""
+    if precision == "bf16x3":
+        peak = peaks.get("bf16_tflops", 1900.0) * 1e12
+        return {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "issued_frac": 3 * achieved / peak,
+                "peak_source": "measured bf16 dense (MEASURED_PEAKS.json)"}
+    peak = FP32_SIMT_PEAK if precision == "fp32" else FP64_PEAK
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "nominal from unit counts and clocks"}
+
+
 # ------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -244,9 +260,12 @@ def run_ours(args):
         ctx.paths = ctx.solver_paths()
         return ctx, t_step, np.mean(stages, axis=0), launches
 
+    head = {"bf16x3": ntu.NTU_MIXED_BF16X3, "fp32": ntu.NTU_MIXED_FP32,
+            "fp64": ntu.NTU_FP64}[args.precision]
     clocks = ClockSampler(local)
     clocks.start()
-    ctx, t_mixed, st_mixed, launches = measure(ntu.NTU_MIXED_FP32, args.steps, args.warmup, 8)
+    ctx, t_mixed, st_mixed, launches = measure(head, args.steps, args.warmup,
+                                               15 if head == ntu.NTU_FP64 else 8)
     clk = clocks.stop()
     ms_mixed = max_over_ranks(statistics.mean(t_mixed))
     value = world * B / (ms_mixed / 1e3)
@@ -278,17 +297,22 @@ def run_ours(args):
     ctx.close()
     del ctx
 
-    # plain FP64 path on the same GPU, same batch
-    fp64 = None
-    if not args.no_fp64:
-        ctx64, t64, st64, _ = measure(ntu.NTU_FP64, args.fp64_steps, 1, 15)
-        ms64 = max_over_ranks(statistics.mean(t64))
-        fp64 = {"value": world * B / (ms64 / 1e3), "unit": "bond updates/s",
-                "ms_per_step": ms64,
-                "env_tflops": B * env_flops(D, r) / (st64[1] / 1e3) / 1e12,
-                "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
-                                     [round(x, 3) for x in st64]))}
-        ctx64.close()
+    # the other precisions on the same GPU, same batch
+    others = {}
+    names = {ntu.NTU_MIXED_BF16X3: "bf16x3_path", ntu.NTU_MIXED_FP32: "fp32_env_path",
+             ntu.NTU_FP64: "fp64_path"}
+    for prec in (ntu.NTU_MIXED_BF16X3, ntu.NTU_MIXED_FP32, ntu.NTU_FP64):
+        if prec == head or (prec == ntu.NTU_FP64 and args.no_fp64):
+            continue
+        cx, tt, st, _ = measure(prec, args.fp64_steps, 1, 15 if prec == ntu.NTU_FP64 else 8)
+        ms = max_over_ranks(statistics.mean(tt))
+        others[names[prec]] = {
+            "value": world * B / (ms / 1e3), "unit": "bond updates/s", "ms_per_step": ms,
+            "env_tflops": B * env_flops(D, r) / (st[1] / 1e3) / 1e12,
+            "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
+                                 [round(float(x), 3) for x in st]))}
+        cx.close()
+    fp64 = others.get("fp64_path")
 
     if rank != 0:
         return
@@ -307,21 +331,23 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "bond updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 env + c128 solvers", "data": "synthetic",
-        "config": workload_config(args, "mixed: FP32 environment, FP64 solvers"),
+        "dtype": {"bf16x3": "split-bf16 env (fp32 acc) + c128 solvers",
+                  "fp32": "c64 env + c128 solvers", "fp64": "c128"}[args.precision],
+        "data": "synthetic",
+        "config": workload_config(args, {
+            "bf16x3": "mixed: split-BF16 tcgen05 environment with FP32 accumulation, FP64 solvers",
+            "fp32": "mixed: FP32 environment, FP64 solvers",
+            "fp64": "FP64 throughout"}[args.precision]),
         "roofline": {"kernel": "k_als (ALS truncation, Fig. 5)", "bound": "alu",
                      "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK, "traffic": None,
                      "peak_source": "nominal FP64 derived from unit counts and clocks"},
-        "env_roofline": {"bound": "alu (FP32 SIMT)", "achieved": env_achieved / 1e12,
-                         "peak": FP32_SIMT_PEAK / 1e12, "unit": "TFLOP/s",
-                         "frac": env_achieved / FP32_SIMT_PEAK,
-                         "tensor_peak_bf16_measured": peaks.get("bf16_tflops")},
+        "env_roofline": env_roof(args.precision, env_achieved, peaks),
         "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
                              [round(float(x), 3) for x in st_mixed])),
         "delta_median": float(np.median(delta_mixed)),
         "solver_paths": paths_mixed,
-        "fp64_path": fp64,
+        **others,
         "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": {"value": world * B / e2e_s, "unit": "bond updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -344,6 +370,7 @@ def main():
     ap.add_argument("--r", type=int, default=2)
     ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--sweeps", type=int, default=10)
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

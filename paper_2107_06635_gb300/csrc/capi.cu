@@ -88,17 +88,31 @@ void carve(ntu_ctx* c, Carver& cv) {
   W.Tbc = mixed ? (void*)cv.take<char>(n * P.szT * es) : nullptr;
   W.QAc = mixed ? (void*)cv.take<char>(n * P.szQ * es) : nullptr;
   W.QBc = mixed ? (void*)cv.take<char>(n * P.szQ * es) : nullptr;
+  const bool tc = c->cfg.precision == NTU_MIXED_BF16X3;
   W.EL = cv.take<char>(n * P.szE1 * es);
   W.ER = cv.take<char>(n * P.szE1 * es);
-  W.ETL = cv.take<char>(n * P.szE2 * es);
-  W.EBL = cv.take<char>(n * P.szE2 * es);
-  W.ETR = cv.take<char>(n * P.szE2 * es);
-  W.EBR = cv.take<char>(n * P.szE2 * es);
   W.Y = cv.take<char>(n * P.szQ * es);
-  W.T1 = cv.take<char>(n * P.szS2 * es);
-  W.T2 = cv.take<char>(n * P.szS2 * es);
-  W.HL = cv.take<char>(n * P.szS2 * es);
-  W.HR = cv.take<char>(n * P.szS2 * es);
+  if (!tc) {
+    W.ETL = cv.take<char>(n * P.szE2 * es);
+    W.EBL = cv.take<char>(n * P.szE2 * es);
+    W.ETR = cv.take<char>(n * P.szE2 * es);
+    W.EBR = cv.take<char>(n * P.szE2 * es);
+    W.T1 = cv.take<char>(n * P.szS2 * es);
+    W.T2 = cv.take<char>(n * P.szS2 * es);
+    W.HL = cv.take<char>(n * P.szS2 * es);
+    W.HR = cv.take<char>(n * P.szS2 * es);
+  } else {
+    // split BF16 operands (2 bytes each, rows x [hi | lo])
+    const size_t bE = (size_t)P.rowsE * 2 * P.krpE * 2, bT = (size_t)P.rowsT * 2 * P.krpE * 2;
+    W.ETLd = cv.take<char>(n * bE);
+    W.EBLd = cv.take<char>(n * bE);
+    W.ETRd = cv.take<char>(n * bE);
+    W.EBRd = cv.take<char>(n * bE);
+    W.T1s = cv.take<char>(n * bT);
+    W.T2s = cv.take<char>(n * bT);
+    W.HLd = cv.take<char>(n * (size_t)P.rowsHL * 2 * P.krpJ * 2);
+    W.HRs = cv.take<char>(n * (size_t)P.rowsHR * 2 * P.krpJ * 2);
+  }
   W.graw = cv.take<double2>(n * P.szG);
   W.g = cv.take<double2>(n * P.szG);
   W.gscr = cv.take<double2>(n * P.szG);
@@ -176,8 +190,6 @@ extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
     return fail(nullptr, NTU_EINVAL, "d_p*D^2 < r: gated matrix has fewer rows than columns");
   if (f.als_sweeps < 0 || f.als_sweeps > 1000) return fail(nullptr, NTU_EINVAL, "als_sweeps=%d", f.als_sweeps);
   if (f.precision < 0 || f.precision > 2) return fail(nullptr, NTU_EINVAL, "precision=%d", f.precision);
-  if (f.precision == NTU_MIXED_BF16X3)
-    return fail(nullptr, NTU_EUNSUPPORTED, "NTU_MIXED_BF16X3 is not available in this build");
   if (f.tau_kmin < 0 || f.tau_kmax > 20 || f.tau_kmin > f.tau_kmax)
     return fail(nullptr, NTU_EINVAL, "tau_kmin=%d tau_kmax=%d", f.tau_kmin, f.tau_kmax);
   if (f.max_batch < 1 || f.max_batch > 65535) return fail(nullptr, NTU_EINVAL, "max_batch=%d", f.max_batch);
@@ -216,6 +228,21 @@ extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
   const char* dbg = getenv("NTU_DEBUG_SYNC");
   c->debug_sync = (dbg && dbg[0] == '1') ? 1 : 0;
   cudaMemset(base, 0, dry.off);
+  if (f.precision == NTU_MIXED_BF16X3) {
+    int prop = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&prop, cudaDevAttrComputeCapabilityMajor, dev);
+    if (prop != 10) {
+      ntu_destroy(c);
+      return fail(nullptr, NTU_EUNSUPPORTED,
+                  "NTU_MIXED_BF16X3 needs a compute capability 10.x GPU (tcgen05)");
+    }
+    st = tc_plan_maps(c);
+    if (st != NTU_OK) {
+      ntu_destroy(c);
+      return fail(nullptr, st, "tensor maps of the split operands");
+    }
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     ntu_destroy(c);
     return fail(nullptr, NTU_ECUDA, "device synchronize after allocation");

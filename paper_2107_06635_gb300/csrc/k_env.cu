@@ -33,6 +33,8 @@ struct GemmArgs {
   const int* rowA; const int* kA; const int* kB; const int* colB; const int* rowC; const int* colC;
   int conjA, conjB;
   long long sA, sB, sC;
+  const int* rowK; const int* colK;
+  int mode, pitch, krp_out;
 };
 
 // Tile BM x BN per CTA, BK-deep k chunks, each thread TM x TN outputs.
@@ -108,6 +110,20 @@ k_cgemm(GemmArgs g, const C2* __restrict__ A, const C2* __restrict__ B, C2* __re
     int m = m0 + ty + i * (BM / TM);
     if (m >= g.M) continue;
     long long rc = g.rowC[m];
+    if constexpr (sizeof(C2) == 8) {
+      if (g.mode != 0) {      // split BF16 operand of a tensor-core GEMM
+        __nv_bfloat16* ob = (__nv_bfloat16*)C + b * g.sC;
+        const long long rk = g.rowK[m];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          int n = n0 + tx + j * (BN / TN);
+          if (n < g.N)
+            store_split(ob, rc + g.colC[n], rk + g.colK[n], g.pitch, g.krp_out,
+                        (float)acc[i][j].x, (float)acc[i][j].y, g.mode == 2);
+        }
+        continue;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       int n = n0 + tx + j * (BN / TN);
@@ -125,6 +141,9 @@ static cudaError_t run_gemm(ntu_ctx* c, const GemmOp& op, int n, const void* A, 
   a.rowC = t + op.rowC; a.colC = t + op.colC;
   a.conjA = op.conjA; a.conjB = op.conjB;
   a.sA = op.sA; a.sB = op.sB; a.sC = op.sC;
+  a.mode = op.mode; a.pitch = op.pitch; a.krp_out = op.krp_out;
+  a.rowK = op.mode ? t + op.rowK : nullptr;
+  a.colK = op.mode ? t + op.colK : nullptr;
   constexpr int BM = 64, BN = 64, TM = 4, TN = 4;
   constexpr int BK = sizeof(C2) == 16 ? 8 : 16;
   dim3 grid((op.N + BN - 1) / BN, (op.M + BM - 1) / BM, n);
@@ -173,8 +192,10 @@ int plan_build(ntu_ctx* c) {
   auto op = [&](int M, int N, int Kd, int rowA, int kA, int kB, int colB, int rowC, int colC,
                 int cA, int cB, long long sA, long long sB, long long sC) {
     GemmOp o;
+    memset(&o, 0, sizeof(o));
     o.M = M; o.N = N; o.Kd = Kd; o.rowA = rowA; o.kA = kA; o.kB = kB; o.colB = colB;
     o.rowC = rowC; o.colC = colC; o.conjA = cA; o.conjB = cB; o.sA = sA; o.sB = sB; o.sC = sC;
+    o.mode = 0; o.rowK = o.colK = -1;
     return o;
   };
   // ---- edge double tensors, Gram form E = T^T conj(T) over the closed legs
@@ -264,6 +285,83 @@ int plan_build(ntu_ctx* c) {
     int rC = T.add({{K, K}, {K, (long long)K * K2}});
     int cC = T.add({{K, 1}, {K, K2}});
     P.join = op((int)K2, (int)K2, (int)D4, rA, kk, kk, rA, rC, cC, 0, 0, P.szS2, P.szS2, P.szG);
+    // ---- split-BF16 tensor-core variant: geometry of the split operands
+    auto up = [](long long x, long long q) { return (x + q - 1) / q * q; };
+    P.krpE = up(2 * D2, 64);                    // real K of t2 / h: (u,u') or (n,n')
+    P.krpJ = up(2 * D4, 64);                    // real K of the join: h
+    P.rowsE = 128 * ((D2 + 63) / 64);           // doubled edge operands
+    P.rowsT = up(D2 * K2, 128);                 // T1 / T2 as B operands
+    P.rowsHL = 128 * ((K2 + 63) / 64);          // doubled H_L
+    P.rowsHR = up(K2, 128);                     // H_R
+    const int pE = (int)(2 * P.krpE), pJ = (int)(2 * P.krpJ);
+    // edge tensors E[(x,y),(x',y')] as doubled A operands of t2 / h:
+    // complex row (x, x'), complex column (y, y')
+    int erC = T.add({{D, D}, {D, 0}}), ecC = T.add({{D, 1}, {D, 0}});
+    int erK = T.add({{D, 0}, {D, D}}), ecK = T.add({{D, 0}, {D, 1}});
+    auto as_split = [&](GemmOp o, int mode, long long sC, int pitch, int krp) {
+      o.rowC = erC; o.colC = ecC; o.rowK = erK; o.colK = ecK;
+      o.mode = mode; o.sC = sC; o.pitch = pitch; o.krp_out = krp;
+      return o;
+    };
+    P.e2TL = as_split(P.eTL, 2, P.rowsE * pE, pE, (int)P.krpE);
+    P.e2BL = as_split(P.eBL, 2, P.rowsE * pE, pE, (int)P.krpE);
+    P.e2TR = as_split(P.eTR, 2, P.rowsE * pE, pE, (int)P.krpE);
+    P.e2BR = as_split(P.eBR, 2, P.rowsE * pE, pE, (int)P.krpE);
+    // The composite column indices below are ordered so that each producer's
+    // fastest column index is the consumer's K index: the split stores then
+    // run along rows (coalesced) instead of across them.
+    const long long KD2 = K * D2;
+    // T1[(u,n,k),(u',n',k')] as the B operand of t2, with the GEMM's columns
+    // ordered (n',k',u'): row (k,k',n,n'), column (u,u')
+    P.t1s = P.t1;
+    P.t1s.colB = T.add({{D, K}, {K, 1}, {D, DK}});
+    P.t1s.rowC = T.add({{D, 0}, {D, D}, {K, KD2}});
+    P.t1s.colC = T.add({{D, 1}, {K, D2}, {D, 0}});
+    P.t1s.rowK = T.add({{D, D}, {D, 0}, {K, 0}});
+    P.t1s.colK = T.add({{D, 0}, {K, 0}, {D, 1}});
+    P.t1s.mode = 1; P.t1s.sC = P.rowsT * pE; P.t1s.pitch = pE; P.t1s.krp_out = (int)P.krpE;
+    // t2: C[(ht,ht'),(k,k',n,n')] -> B operand of h: row (k,k',ht,ht'), column (n,n')
+    TcOp t2;
+    memset(&t2, 0, sizeof(t2));
+    t2.rowC = T.add({{D, D}, {D, 1}});
+    t2.colC = T.add({{K, KD2}, {K, D2}, {D, 0}, {D, 0}});
+    t2.rowK = T.add({{D, 0}, {D, 0}});
+    t2.colK = T.add({{K, 0}, {K, 0}, {D, D}, {D, 1}});
+    t2.mode = 1;
+    t2.mtiles = (int)(P.rowsE / 128);
+    t2.args.kTiles = (int)(P.krpE / 64); t2.args.krp = (int)P.krpE;
+    t2.args.Mc = (int)D2; t2.args.N = (int)D2K2;
+    t2.args.pitch = pE; t2.args.krp_out = (int)P.krpE; t2.args.sOut = P.rowsT * pE;
+    P.tc_t2L = t2;
+    P.tc_t2R = t2;
+    // h: C[(hb,hb'),(k,k',ht,ht')] -> join operand: complex column
+    // h = (hb,hb',ht,ht'); H_L doubled (A) with complex row (k,k'), H_R plain
+    // (B) with row (k',k) so that the join writes g along its rows
+    TcOp h;
+    memset(&h, 0, sizeof(h));
+    h.rowC = T.add({{D, 0}, {D, 0}});
+    h.colC = T.add({{K, K}, {K, 1}, {D, 0}, {D, 0}});
+    h.rowK = T.add({{D, D3}, {D, D2}});
+    h.colK = T.add({{K, 0}, {K, 0}, {D, D}, {D, 1}});
+    const int hcolR = T.add({{K, 1}, {K, K}, {D, 0}, {D, 0}});
+    h.mtiles = (int)(P.rowsE / 128);
+    h.args.kTiles = (int)(P.krpE / 64); h.args.krp = (int)P.krpE;
+    h.args.Mc = (int)D2; h.args.N = (int)D2K2;
+    h.args.pitch = pJ; h.args.krp_out = (int)P.krpJ;
+    P.tc_hL = h;
+    P.tc_hL.mode = 2; P.tc_hL.args.sOut = P.rowsHL * pJ;
+    P.tc_hR = h;
+    P.tc_hR.mode = 1; P.tc_hR.args.sOut = P.rowsHR * pJ; P.tc_hR.colC = hcolR;
+    // join: g[(k',j'),(k,j)] = sum_h H_L[(k,k'),h] H_R[(j,j'),h], B rows (j',j)
+    TcOp jn;
+    memset(&jn, 0, sizeof(jn));
+    jn.rowC = rC; jn.colC = T.add({{K, K2}, {K, 1}}); jn.rowK = -1; jn.colK = -1;
+    jn.mode = 0;
+    jn.mtiles = (int)(P.rowsHL / 128);
+    jn.args.kTiles = (int)(P.krpJ / 64); jn.args.krp = (int)P.krpJ;
+    jn.args.Mc = (int)K2; jn.args.N = (int)K2;
+    jn.args.sOut = P.szG;
+    P.tc_join = jn;
   }
   P.n_tab = (int)T.tab.size();
   if (cudaMalloc(&P.d_tab, sizeof(int) * P.n_tab) != cudaSuccess) return NTU_ENOMEM;
@@ -339,6 +437,55 @@ static cudaError_t env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, 
   return cudaSuccess;
 }
 
+// Tensor maps of the split operands (the work space is fixed at init, so
+// the maps are encoded once).
+int tc_plan_maps(ntu_ctx* c) {
+  Plan& P = c->plan;
+  Work& W = c->w;
+  const long long cap = W.cap, pE = 2 * P.krpE, pJ = 2 * P.krpJ;
+  int st = NTU_OK;
+  auto mk = [&](CUtensorMap* m, void* base, long long cols, long long rows) {
+    if (st == NTU_OK) st = tc_make_map(m, base, cols, rows, cap);
+  };
+  mk(&P.tc_t2L.mapA, W.ETLd, pE, P.rowsE);
+  mk(&P.tc_t2R.mapA, W.ETRd, pE, P.rowsE);
+  mk(&P.tc_t2L.mapB, W.T1s, pE, P.rowsT);
+  P.tc_t2R.mapB = P.tc_t2L.mapB;
+  mk(&P.tc_hL.mapA, W.EBLd, pE, P.rowsE);
+  mk(&P.tc_hR.mapA, W.EBRd, pE, P.rowsE);
+  mk(&P.tc_hL.mapB, W.T2s, pE, P.rowsT);
+  P.tc_hR.mapB = P.tc_hL.mapB;
+  mk(&P.tc_join.mapA, W.HLd, pJ, P.rowsHL);
+  mk(&P.tc_join.mapB, W.HRs, pJ, P.rowsHR);
+  return st;
+}
+
+// Environment with split-BF16 tensor-core products (Fig. 4): the small edge
+// and Y products stay on the FP32 pipes; t1 writes its result as the B
+// operand of t2, the edge tensors as the doubled A operands of t2 / h, and
+// t2, h and the join run on tcgen05 (k_tc.cu).
+static cudaError_t env_chain_bf16x3(ntu_ctx* c, int n, const void* Ta, const void* Tb,
+                                    const void* QA, const void* QB, void* graw) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  RG(run_gemm<float2>(c, P.eL, n, Tb, Tb, W.EL));
+  RG(run_gemm<float2>(c, P.eR, n, Ta, Ta, W.ER));
+  RG(run_gemm<float2>(c, P.e2TL, n, Tb, Tb, W.ETLd));
+  RG(run_gemm<float2>(c, P.e2BL, n, Tb, Tb, W.EBLd));
+  RG(run_gemm<float2>(c, P.e2TR, n, Ta, Ta, W.ETRd));
+  RG(run_gemm<float2>(c, P.e2BR, n, Ta, Ta, W.EBRd));
+  RG(run_gemm<float2>(c, P.y, n, QA, W.EL, W.Y));
+  RG(run_gemm<float2>(c, P.t1s, n, W.Y, QA, W.T1s));
+  RG(launch_tc_gemm(c, P.tc_t2L, n, W.T2s));
+  RG(launch_tc_gemm(c, P.tc_hL, n, W.HLd));
+  RG(run_gemm<float2>(c, P.y, n, QB, W.ER, W.Y));
+  RG(run_gemm<float2>(c, P.t1s, n, W.Y, QB, W.T1s));
+  RG(launch_tc_gemm(c, P.tc_t2R, n, W.T2s));
+  RG(launch_tc_gemm(c, P.tc_hR, n, W.HRs));
+  RG(launch_tc_gemm(c, P.tc_join, n, graw));
+  return cudaSuccess;
+}
+
 cudaError_t launch_env(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
                        const double2* QA, const double2* QB, void* graw) {
   const Plan& P = c->plan;
@@ -348,6 +495,8 @@ cudaError_t launch_env(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
   RG(to_f32(c, (long long)n * P.szT, Tb, W.Tbc));
   RG(to_f32(c, (long long)n * P.szQ, QA, W.QAc));
   RG(to_f32(c, (long long)n * P.szQ, QB, W.QBc));
+  if (c->cfg.precision == NTU_MIXED_BF16X3)
+    return env_chain_bf16x3(c, n, W.Tac, W.Tbc, W.QAc, W.QBc, graw);
   return env_chain<float2>(c, n, W.Tac, W.Tbc, W.QAc, W.QBc, graw);
 }
 

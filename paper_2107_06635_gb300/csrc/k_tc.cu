@@ -1,0 +1,198 @@
+// Tensor-core (tcgen05) GEMMs of the environment contraction (Fig. 4) for
+// the NTU_MIXED_BF16X3 precision.
+//
+// A complex product C = A B^T is computed as one real GEMM: B keeps its
+// interleaved (re, im) storage as a real K-major row of length 2K, and A is
+// "doubled": complex row r becomes the real rows [Re, -Im, Re, -Im, ...] and
+// [Im, Re, Im, Re, ...], placed 64 rows apart inside a 128-row tile, so that
+// one 128 x N accumulator tile holds Re C in lanes 0-63 and Im C in lanes
+// 64-127.  Each operand is stored split, x = hi + lo with hi = bf16(x) and
+// lo = bf16(x - hi), as [hi | lo] halves of its row, and the kernel
+// accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory.
+//
+// Operands are fetched by TMA (128-byte swizzle) through a 3-stage mbarrier
+// pipeline; one thread issues tcgen05.mma (M=128, N=128, K=16 per
+// instruction); the epilogue reads TMEM and writes the result through
+// separable index tables either as complex FP32 or directly as the split
+// BF16 operand of the next GEMM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include "ntu_dev.cuh"
+#include "ntu_impl.h"
+#include "tc_sm103.cuh"
+
+namespace ntu {
+
+namespace {
+constexpr int TBM = 128, TBN = 128, TBK = 64, TSTAGES = 3;
+constexpr int TILE_A = TBM * TBK * 2, TILE_B = TBN * TBK * 2;
+constexpr long long WAIT_LIMIT = 1ll << 28;
+constexpr int SM_STAGE = TBN + 1;                 // staging pitch (floats)
+constexpr size_t TC_SMEM = (size_t)TSTAGES * (TILE_A + TILE_B) + 1024 + 256;
+static_assert((size_t)TBM * SM_STAGE * 4 <= (size_t)TSTAGES * (TILE_A + TILE_B),
+              "epilogue staging must fit in the pipeline buffers");
+}  // namespace
+
+// MODE 0: complex FP32 output at out[rowC[m] + colC[n]].
+// MODE 1: split B operand: row rowC[m] + colC[n], complex column
+//         rowK[m] + colK[n] of a [rows][2 krp] BF16 array.
+// MODE 2: split doubled A operand: as MODE 1 but complex row r goes to the
+//         real rows (r/64)*128 + r%64 (Re part) and +64 (Im part).
+template <int MODE>
+__global__ void __launch_bounds__(128) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                 const __grid_constant__ CUtensorMap tmB,
+                                                 TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + TSTAGES * TILE_A;
+  uint64_t* full = (uint64_t*)(sB + TSTAGES * TILE_B);
+  uint64_t* empty = full + TSTAGES;
+  uint64_t* accf = empty + TSTAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n0 = blockIdx.x * TBN, mt = blockIdx.y, z = blockIdx.z;
+  if (tid == 0) {
+    for (int s = 0; s < TSTAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    tc::mbar_init(accf, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, TBN);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const int total = 3 * a.kTiles;
+  int issued = 0;                       // TMA stages armed by the producer
+  if (warp == 0 && lane == 0) {
+    for (int it = 0; it < total; ++it) {
+      const int s = it % TSTAGES, u = it / TSTAGES;
+      if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, WAIT_LIMIT)) {
+        raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+        break;
+      }
+      const int p = it / a.kTiles, kt = it % a.kTiles;
+      const int xa = (p == 2 ? a.krp : 0) + kt * TBK, xb = (p == 1 ? a.krp : 0) + kt * TBK;
+      tc::mbar_expect_tx(&full[s], TILE_A + TILE_B);
+      tc::tma_load_3d(sA + s * TILE_A, &tmA, &full[s], xa, mt * TBM, z);
+      tc::tma_load_3d(sB + s * TILE_B, &tmB, &full[s], xb, n0, z);
+      issued = it + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = tc::idesc_bf16_f32(TBM, TBN);
+    for (int it = 0; it < total; ++it) {
+      const int s = it % TSTAGES, u = it / TSTAGES;
+      if (!tc::mbar_wait(&full[s], u & 1, WAIT_LIMIT)) {
+        raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+        break;
+      }
+      tc::fence_after_sync();
+      const uint64_t ad = tc::sdesc_k128(tc::smem_u32(sA + s * TILE_A));
+      const uint64_t bd = tc::sdesc_k128(tc::smem_u32(sB + s * TILE_B));
+#pragma unroll
+      for (int kk = 0; kk < TBK / 16; ++kk)
+        tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (it | kk) != 0);
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(accf);
+  }
+  __syncwarp();
+  bool ok = tc::mbar_wait(accf, 0, WAIT_LIMIT);
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok && lane == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+  if (warp == 0 && lane == 0 && issued > 0) {
+    // make sure no TMA copy is still landing in shared memory before reuse
+    for (int it = issued - TSTAGES < 0 ? 0 : issued - TSTAGES; it < issued; ++it)
+      if (!tc::mbar_wait(&full[it % TSTAGES], (it / TSTAGES) & 1, WAIT_LIMIT))
+        raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+  }
+  tc::fence_after_sync();
+  __syncthreads();
+  float* stage = (float*)smem;         // [128][SM_STAGE], reuses the pipeline buffers
+  if (ok) {
+    const int row = warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < TBN; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) stage[row * SM_STAGE + c + i] = v[i];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TBN);
+  if (!ok) return;
+  for (int idx = tid; idx < 64 * TBN; idx += 128) {
+    const int j = idx / TBN, nn = idx % TBN;
+    const int m = mt * 64 + j, n = n0 + nn;
+    if (m >= a.Mc || n >= a.N) continue;
+    const float re = stage[j * SM_STAGE + nn], im = stage[(64 + j) * SM_STAGE + nn];
+    if (MODE == 0) {
+      float2* o = (float2*)a.out + (long long)z * a.sOut;
+      o[(long long)a.rowC[m] + a.colC[n]] = make_float2(re, im);
+    } else {
+      __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
+      store_split(o, (long long)a.rowC[m] + a.colC[n], (long long)a.rowK[m] + a.colK[n],
+                  a.pitch, a.krp_out, re, im, MODE == 2);
+    }
+  }
+}
+
+// --------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  return enc;
+}
+
+// 3-D map of a [items][rows][cols] BF16 array with 64 x 128 boxes and the
+// 128-byte swizzle.  cols must be a multiple of 64 (so every row pitch and
+// every box start are 16-byte aligned).
+int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return NTU_EUNSUPPORTED;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)items};
+  cuuint64_t strides[2] = {(cuuint64_t)cols * 2, (cuuint64_t)cols * rows * 2};
+  cuuint32_t box[3] = {TBK, TBM, 1}, es[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? NTU_OK : NTU_ECUDA;
+}
+
+cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out) {
+  TcArgs a = op.args;
+  const int* t = c->plan.d_tab;
+  a.rowC = t + op.rowC; a.colC = t + op.colC;
+  a.rowK = op.rowK >= 0 ? t + op.rowK : nullptr;
+  a.colK = op.colK >= 0 ? t + op.colK : nullptr;
+  a.out = out;
+  a.err = c->d_status;
+  dim3 grid((a.N + TBN - 1) / TBN, op.mtiles, n);
+  static bool attr[3] = {false, false, false};
+  if (op.mode == 0) {
+    if (!attr[0]) { cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[0] = true; }
+    k_tc_gemm<0><<<grid, 128, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a);
+  } else if (op.mode == 1) {
+    if (!attr[1]) { cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[1] = true; }
+    k_tc_gemm<1><<<grid, 128, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a);
+  } else {
+    if (!attr[2]) { cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[2] = true; }
+    k_tc_gemm<2><<<grid, 128, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a);
+  }
+  return after_launch(c, "k_tc_gemm");
+}
+
+}  // namespace ntu

@@ -4,6 +4,7 @@
 // implicit symmetric tridiagonal QR).  All CTA routines assume
 // blockDim.x == NTU_CTA threads.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -49,6 +50,38 @@ __device__ __forceinline__ double2 cfmsc(double2 a, double2 b, double2 c) {
   return c;
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// x = hi + lo with hi = bf16(x) and lo = bf16(x - hi): the split operands of
+// the three-pass tensor-core products.
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Store complex value (re, im) of complex row r, complex column kc into a
+// split [hi | lo] BF16 operand with row pitch `pitch` and lo offset `krp`.
+// doubled = 0: interleaved (re, im) row (a B operand).  doubled = 1: the
+// real rows (r/64)*128 + r%64 and +64 receive (re, -im) and (im, re) (a
+// doubled A operand: one real GEMM then yields Re in the first 64 and Im in
+// the last 64 rows of each 128-row tile).
+__device__ __forceinline__ void store_split(__nv_bfloat16* base, long long r, long long kc,
+                                            int pitch, int krp, float re, float im,
+                                            int doubled) {
+  __nv_bfloat16 h0, l0, h1, l1;
+  split_bf16(re, h0, l0);
+  split_bf16(im, h1, l1);
+  if (!doubled) {
+    __nv_bfloat16* p = base + r * pitch + 2 * kc;
+    p[0] = h0; p[1] = h1; p[krp] = l0; p[krp + 1] = l1;
+  } else {
+    __nv_bfloat16 hm, lm;
+    split_bf16(-im, hm, lm);
+    __nv_bfloat16* pr = base + ((r / 64) * 128 + (r % 64)) * pitch + 2 * kc;
+    __nv_bfloat16* pi = pr + 64LL * pitch;
+    pr[0] = h0; pr[1] = hm; pr[krp] = l0; pr[krp + 1] = lm;
+    pi[0] = h1; pi[1] = h0; pi[krp] = l1; pi[krp + 1] = l0;
+  }
+}
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
 // a / b by Smith's method (no squares of b, so no underflow or overflow for
@@ -123,7 +156,7 @@ enum { ST_NUMERIC = 4, ST_TIMEOUT = 5 };
 // Reason bits recorded next to the status word (status[1]).
 enum {
   WHY_SVD_NONFINITE = 1, WHY_ALS_QR = 2, WHY_ALS_NONFINITE = 4, WHY_REPAIR_QR = 8,
-  WHY_REPAIR_TRACE = 16
+  WHY_REPAIR_TRACE = 16, WHY_TC_WAIT = 32
 };
 __device__ __forceinline__ void raise_status(int* status, int code, int why = 0) {
   if (status) {

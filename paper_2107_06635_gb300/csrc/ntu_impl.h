@@ -2,6 +2,7 @@
 // (sizes and contraction index tables), the device work space and the
 // kernel launchers that the C ABI (capi.cu) strings together.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -14,12 +15,38 @@ namespace ntu {
 //   C[b][rowC[m] + colC[n]] = sum_k A[b][rowA[m] + kA[k]] * B[b][kB[k] + colB[n]]
 // with optional conjugation of A or B.  The six index tables map the
 // composite tensor indices to element offsets; they live in one device int
-// array at the given offsets.
+// array at the given offsets.  mode 1 / 2 (FP32 path only) write the result
+// instead as the split-BF16 operand of a tensor-core GEMM (see k_tc.cu):
+// row rowC[m] + colC[n], complex column rowK[m] + colK[n], row pitch
+// `pitch` BF16 elements, lo half at +krp_out; mode 2 doubles the rows.
 struct GemmOp {
   int M, N, Kd;
   int rowA, kA, kB, colB, rowC, colC;   // offsets into the table array
   int conjA, conjB;
-  long long sA, sB, sC;                 // per-item strides (complex elements)
+  long long sA, sB, sC;                 // per-item strides (elements of the output)
+  int mode, rowK, colK, pitch, krp_out;
+};
+
+// Arguments of one tensor-core GEMM (k_tc.cu) as seen by the kernel.
+struct TcArgs {
+  int kTiles;            // 64-wide K tiles per split pass
+  int krp;               // padded real K of one half ([hi | lo] rows are 2 krp wide)
+  int Mc, N;             // valid complex rows, valid columns
+  const int *rowC, *colC, *rowK, *colK;
+  void* out;
+  long long sOut;        // per-item stride of the output (elements)
+  int pitch, krp_out;    // split outputs: row pitch and lo offset (BF16 elements)
+  int* err;
+};
+
+// A tensor-core GEMM of the plan: operand tensor maps, kernel arguments,
+// table offsets and output mode (0 complex FP32, 1 split operand, 2 split
+// doubled operand).
+struct TcOp {
+  CUtensorMap mapA, mapB;
+  TcArgs args;
+  int rowC, colC, rowK, colK;
+  int mode, mtiles;
 };
 
 struct Plan {
@@ -28,6 +55,12 @@ struct Plan {
   GemmOp eL, eR, eTL, eBL, eTR, eBR;    // edge double tensors (Fig. 4(b))
   GemmOp y, t1, t2, h;                  // half environment steps (Fig. 4(c,d))
   GemmOp join;                          // join of the two halves (Fig. 4(d,e))
+  // split-BF16 tensor-core variant (NTU_MIXED_BF16X3)
+  GemmOp e2TL, e2BL, e2TR, e2BR;        // edge tensors written as doubled A operands
+  GemmOp t1s;                           // T1 written as the B operand of t2
+  TcOp tc_t2L, tc_t2R, tc_hL, tc_hR, tc_join;
+  long long krpE, krpJ;                 // padded real K of the t2/h and join GEMMs
+  long long rowsE, rowsT, rowsHL, rowsHR;  // allocated rows of the split operands
   int* d_tab;                           // device index tables
   int n_tab;
 };
@@ -41,6 +74,8 @@ struct Work {
   double2 *QA, *QB, *RA, *RB;
   // environment (element type: double2 for FP64, float2 for the mixed paths)
   void *Tac, *Tbc, *QAc, *QBc, *EL, *ER, *ETL, *EBL, *ETR, *EBR, *Y, *T1, *T2, *HL, *HR, *graw;
+  // split-BF16 operands of the tensor-core environment
+  void *ETLd, *EBLd, *ETRd, *EBRd, *T1s, *T2s, *HLd, *HRs;
   double2 *g, *gscr, *gw;     // metric, Cholesky / eigen scratch, eigenvectors
   double *gz, *geig;          // explicit Z (ng*ng) and d,e (2*ng) for the repair fallback
   double2 *gtau, *gp;         // reflector factors, vector scratch (ng each)
@@ -117,5 +152,10 @@ cudaError_t launch_measure(ntu_ctx* c, const double2* T, const double2* N, const
                            double2* out);
 cudaError_t launch_copy_raw(ntu_ctx* c, int n, const void* graw, double2* g);
 size_t als_smem_bytes();
+
+// tensor-core environment (k_tc.cu, k_env.cu)
+int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items);
+int tc_plan_maps(ntu_ctx* c);
+cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out);
 
 }  // namespace ntu

@@ -134,6 +134,25 @@ def test_env_mixed_fp32_within_budget():
         assert _rel(g[i].cpu().numpy(), ref) < 1e-4
 
 
+@pytest.mark.parametrize("D,r", [(3, 2), (5, 2), (8, 2), (4, 4)])
+def test_env_bf16x3_tensor_cores_within_budget(D, r):
+    """Split-BF16 tcgen05 environment: rel-Frobenius(g) <= 1e-4 against the
+    FP64 oracle, on full tiles (D=8), ragged tiles (D=5, D=3) and r=4."""
+    n = 2
+    Ta, Tb, G = _items(450 + D, n, 2, D)
+    cfg = O.Config(D=D, r=r)
+    ctx = _ctx(D, r, precision=2, max_batch=n)
+    Q = [_oracle_stage(Ta[i], Tb[i], G[i], cfg) for i in range(n)]
+    QA, QB = np.stack([q[0] for q in Q]), np.stack([q[2] for q in Q])
+    ng = (D * r) ** 2
+    g = _empty((n, ng, ng))
+    ctx.batch_env_dev(n, _dev(Ta), _dev(Tb), _dev(QA), _dev(QB), g)
+    ctx.sync()
+    for i in range(n):
+        ref = O.metric_raw(Ta[i], Tb[i], QA[i], QB[i], 2, D)
+        assert _rel(g[i].cpu().numpy(), ref) < 1e-4
+
+
 # --------------------------------------------------------------- repair
 def test_repair_cholesky_path_matches_oracle():
     D, r, n = 3, 2, 2
@@ -227,7 +246,7 @@ def test_als_matches_oracle(D, r, sweeps, kmin):
 
 
 # ------------------------------------------------------- full update
-@pytest.mark.parametrize("D,precision", [(3, 0), (4, 0), (6, 0), (4, 1)])
+@pytest.mark.parametrize("D,precision", [(3, 0), (4, 0), (6, 0), (4, 1), (4, 2), (6, 2)])
 def test_batch_update_matches_oracle(D, precision):
     n = 3
     Ta, Tb, G = _items(700 + D, n, 2, D)
