@@ -221,10 +221,10 @@ extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
   real.dry = false;
   carve(c, real);
   // carve() filled every pointer; W.GA is the first slice, i.e. the block base
-  e = cudaMalloc(&c->d_status, sizeof(int) * 8);
+  e = cudaMalloc(&c->d_status, sizeof(int) * 16);
   if (e != cudaSuccess) { cudaFree(base); ntu_destroy(c); return fail(nullptr, NTU_ENOMEM, "status word"); }
-  cudaMemset(c->d_status, 0, sizeof(int) * 8);
-  c->d_paths = c->d_status + 4;
+  cudaMemset(c->d_status, 0, sizeof(int) * 16);
+  c->d_paths = c->d_status + 8;
   const char* dbg = getenv("NTU_DEBUG_SYNC");
   c->debug_sync = (dbg && dbg[0] == '1') ? 1 : 0;
   cudaMemset(base, 0, dry.off);
@@ -276,8 +276,8 @@ extern "C" int ntu_last_launch_count(const ntu_ctx* c) { return c ? c->launches 
 extern "C" int ntu_solver_paths(ntu_ctx* c, int* counts) {
   if (!c || !counts) return fail(c, NTU_EINVAL, "ntu_solver_paths: NULL argument");
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");
-  CK(cudaMemcpy(counts, c->d_paths, 4 * sizeof(int), cudaMemcpyDeviceToHost), "read counters");
-  CK(cudaMemset(c->d_paths, 0, 4 * sizeof(int)), "reset counters");
+  CK(cudaMemcpy(counts, c->d_paths, 5 * sizeof(int), cudaMemcpyDeviceToHost), "read counters");
+  CK(cudaMemset(c->d_paths, 0, 5 * sizeof(int)), "reset counters");
   return NTU_OK;
 }
 

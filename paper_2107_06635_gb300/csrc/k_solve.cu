@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
   // 2. Cholesky of the lower triangle certifies positive definiteness
   __syncthreads();
   int ok = cta_cholesky(sc, ng, 0.0, &okflag);
-  if (tid == 0 && paths) atomicAdd(paths + (ok ? 2 : 3), 1);
+  if (tid == 0 && paths) atomicAdd(paths + (ok ? 3 : 4), 1);
   double ratio = __longlong_as_double(0x7ff8000000000000ULL);   // NaN
   if (!ok) {
     // 3. full eigendecomposition and clipping of negative eigenvalues
@@ -148,18 +148,20 @@ struct AlsShared {
   double2 MB[32 * 8];
   double2 y[256];
   double2 y2[256];
+  double2 p[256];
+  double2 ap[256];
   double red[2 * NTU_WARPS];
   double eps0, tau_sel;
   int err;
   int flag;
-  int n_fast, n_eig;
+  int n_cg, n_fast, n_eig;
 };
 
 struct AlsArgs {
   int D, K, ng, nA, sweeps, kmin, kmax;
   const double2* g; const double2* RA; const double2* RB;
   double2* MA; double2* MB; double* info;
-  int* path_counts;            // [fast, eig] solves, accumulated over items (may be NULL)
+  int* path_counts;            // [Gershgorin+CG, shifted Cholesky, eigen] solves (may be NULL)
   double2 *x0, *gx0, *Tm, *gA, *gC, *jv, *pv, *tauv;
   double *dv, *ev, *rc, *rs;
   int* rk;
@@ -233,40 +235,101 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
   __syncthreads();
 }
 
-// Certified shortcut of the tolerance selection.  With B = max column sum of
-// |Re| + |Im| of gX (>= lambda_max) and tau_max the largest candidate, a
-// successful Cholesky factorisation L L^H = gX - sigma I, sigma = (tau_max +
-// 1e-12) B, proves lambda_min > tau_max lambda_max (the 1e-12 B margin covers
-// rounding), so every candidate tolerance keeps every eigenpair: all
-// candidates give the same eps, the selection rule returns tau_max, and the
-// pseudo-inverse is the inverse.  M = gX^{-1} J then follows from the same
-// factor by the fixed-point iteration (L L^H) v_{k+1} = J - sigma v_k (its
-// fixed point solves gX v = J), which contracts by
-// sigma / (lambda_min - sigma).  Reads only the lower triangle
-// of gX and leaves gX untouched.  Returns 1 when solved, 0 otherwise.
-__device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, const double2* gX,
+// Certified shortcut of the tolerance selection.  With B >= lambda_max of gX
+// and tau_max the largest candidate, a proof that lambda_min > sigma =
+// (tau_max + 1e-12) B (the 1e-12 B margin covers rounding) means every
+// candidate tolerance keeps every eigenpair: all candidates give the same
+// eps, the selection rule returns tau_max, and the pseudo-inverse is the
+// inverse.  Two proofs are tried in turn.  Tier 1: the Gershgorin discs
+// (B = max_i d_i + s_i) lie right of sigma; M = gX^{-1} J then comes from
+// conjugate gradients.  Tier 2: gX - sigma I has a Cholesky factor L L^H;
+// M then follows from the fixed-point iteration (L L^H) v_{k+1} = J -
+// sigma v_k (its fixed point solves gX v = J), which contracts by
+// sigma / (lambda_min - sigma).  Both read the lower triangle of gX (tier 1
+// mirrors it into the upper one).  Returns 1 when solved, 0 when neither
+// proof holds or an iteration stalls; the caller then takes the eigen path.
+__device__ void als_mirror(double2* gX, int nA);
+
+__device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2* gX,
                               double2* gC, const double2* jv, double tau_max) {
   const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31, nA = a.nA;
-  double bmax = 0.0;
-  for (int c = wid; c < nA; c += NTU_WARPS) {
+  // Gershgorin discs from the lower triangle: d_i = Re gX[i][i] and
+  // s_i = sum_{j != i} (|Re| + |Im|) of row i >= sum_{j != i} |gX[i][j]|, so
+  // every eigenvalue lies in [min(d - s), max(d + s)].
+  double glo = INFINITY, ghi = -INFINITY;
+  for (int i = wid; i < nA; i += NTU_WARPS) {
     double s = 0.0;
-    for (int r = c + lid; r < nA; r += 32) {               // column c, rows >= c
-      double2 v = gX[(size_t)c * nA + r];
+    for (int j = i + 1 + lid; j < nA; j += 32) {           // column i below the diagonal
+      double2 v = gX[(size_t)i * nA + j];
       s += fabs(v.x) + fabs(v.y);
     }
-    for (int r = lid; r < c; r += 32) {                     // row c, columns < c
-      double2 v = gX[(size_t)r * nA + c];
+    for (int j = lid; j < i; j += 32) {                     // row i left of the diagonal
+      double2 v = gX[(size_t)j * nA + i];
       s += fabs(v.x) + fabs(v.y);
     }
     s = warp_sum(s);
-    bmax = fmax(bmax, s);
+    const double d = gX[(size_t)i * nA + i].x;
+    glo = fmin(glo, d - s);
+    ghi = fmax(ghi, d + s);
   }
-  bmax = block_max(bmax, sm.red);
+  glo = block_min(glo, sm.red);
+  const double bmax = block_max(ghi, sm.red);               // >= lambda_max
+  if (!(bmax > 0.0) || !isfinite(bmax) || !isfinite(glo)) return 0;
+  const double sigma = (tau_max + 1e-12) * bmax;
+  if (glo > sigma) {
+    // Tier 1: the discs alone prove lambda_min > tau_max lambda_max; solve
+    // gX v = J by conjugate gradients on the full matrix.
+    als_mirror(gX, nA);
+    for (int i = tid; i < nA; i += NTU_CTA) {
+      sm.y[i] = cz(); sm.y2[i] = jv[i]; sm.p[i] = jv[i];
+    }
+    double rs = 0.0;
+    for (int i = tid; i < nA; i += NTU_CTA) rs += cabs2(jv[i]);
+    rs = block_sum(rs, sm.red);
+    const double stop = 1e-30 * rs;                          // |r| <= 1e-15 |J|
+    int conv = rs == 0.0;
+    for (int it = 0; it < 80 && !conv; ++it) {
+      for (int i = tid; i < nA; i += NTU_CTA) {
+        double2 acc = cz();
+        for (int j = 0; j < nA; ++j) acc = cfma(gX[(size_t)j * nA + i], sm.p[j], acc);
+        sm.ap[i] = acc;
+      }
+      double pap = 0.0;
+      for (int i = tid; i < nA; i += NTU_CTA) pap += cmulc(sm.p[i], sm.ap[i]).x;
+      pap = block_sum(pap, sm.red);
+      if (!(pap > 0.0)) break;
+      const double alpha = rs / pap;
+      double rn = 0.0;
+      for (int i = tid; i < nA; i += NTU_CTA) {
+        double2 x = sm.y[i], r = sm.y2[i], p = sm.p[i], q = sm.ap[i];
+        x.x = fma(alpha, p.x, x.x); x.y = fma(alpha, p.y, x.y);
+        r.x = fma(-alpha, q.x, r.x); r.y = fma(-alpha, q.y, r.y);
+        sm.y[i] = x; sm.y2[i] = r;
+        rn += cabs2(r);
+      }
+      rn = block_sum(rn, sm.red);
+      if (rn <= stop) { conv = 1; break; }
+      const double beta = rn / rs;
+      rs = rn;
+      for (int i = tid; i < nA; i += NTU_CTA) {
+        double2 r = sm.y2[i], p = sm.p[i];
+        sm.p[i] = make_double2(fma(beta, p.x, r.x), fma(beta, p.y, r.y));
+      }
+      __syncthreads();
+    }
+    if (conv) {
+      double2* M = side == 0 ? sm.MA : sm.MB;
+      for (int i = tid; i < nA; i += NTU_CTA) M[i] = sm.y[i];
+      if (tid == 0) { sm.tau_sel = tau_max; sm.n_cg += 1; }
+      __syncthreads();
+      return 1;
+    }
+    __syncthreads();
+  }
+  // Tier 2: a Cholesky factorisation of gX - sigma I proves the same bound.
   for (int idx = tid; idx < nA * nA; idx += NTU_CTA)
     if (idx % nA >= idx / nA) gC[idx] = gX[idx];
   __syncthreads();
-  if (!(bmax > 0.0) || !isfinite(bmax)) return 0;
-  const double sigma = (tau_max + 1e-12) * bmax;
   if (!cta_cholesky(gC, nA, sigma, &sm.flag)) return 0;
   if (wid == 0) {
     for (int i = lid; i < nA; i += 32) sm.y[i] = cz();
@@ -391,7 +454,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   log.count = 0;
   double2* gC = a.gC + item * (long long)nA * nA;
   const double tau_max = als_tau(a.kmin < 0 ? 0 : a.kmin);
-  if (tid == 0) { sm.err = 0; sm.n_fast = 0; sm.n_eig = 0; }
+  if (tid == 0) { sm.err = 0; sm.n_cg = 0; sm.n_fast = 0; sm.n_eig = 0; }
   // X0 = R_A R_B^T, x0 = vec(X0) with kA slow
   for (int idx = tid; idx < K * K; idx += NTU_CTA) {
     int i = idx / K, j = idx % K;
@@ -459,8 +522,9 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
     if (sm.err || !isfinite(delta) || !isfinite(eps))
       raise_status(a.status, ST_NUMERIC, sm.err | ((!isfinite(delta) || !isfinite(eps)) ? WHY_ALS_NONFINITE : 0));
     if (a.path_counts) {
-      atomicAdd(a.path_counts + 0, sm.n_fast);
-      atomicAdd(a.path_counts + 1, sm.n_eig);
+      atomicAdd(a.path_counts + 0, sm.n_cg);
+      atomicAdd(a.path_counts + 1, sm.n_fast);
+      atomicAdd(a.path_counts + 2, sm.n_eig);
     }
   }
 }

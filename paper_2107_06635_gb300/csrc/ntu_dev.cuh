@@ -138,6 +138,18 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double* sbuf) {
   for (int i = 0; i < NTU_WARPS; ++i) { t.x += sbuf[2 * i]; t.y += sbuf[2 * i + 1]; }
   return t;
 }
+__device__ __forceinline__ double block_min(double v, double* sbuf) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sbuf[w] = v;
+  __syncthreads();
+  double t = sbuf[0];
+#pragma unroll
+  for (int i = 1; i < NTU_WARPS; ++i) t = fmin(t, sbuf[i]);
+  return t;
+}
 __device__ __forceinline__ double block_max(double v, double* sbuf) {
   v = warp_max(v);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -235,6 +247,13 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
   const int lane = tid & 15;
   const unsigned mask = 0xffffu << ((tid & 16));
   const double tol = fmax(1e-15, 2.3e-16 * n);
+  // Frobenius norm^2 of the input: pairs whose inner product is below
+  // 1e-30 of it belong to the numerical null space and are not rotated
+  // (their rounding-level inner products would otherwise never converge).
+  double fro = 0.0;
+  for (int i = tid; i < 32 * 32; i += NTU_CTA) fro += cabs2(S.A[i]);
+  fro = block_sum(fro, S.red);
+  const double gnull = 1e-30 * fro;
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) S.rotated = 0;
     __syncthreads();
@@ -258,7 +277,7 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
             ga.y += __shfl_xor_sync(mask, ga.y, o);
           }
           double g = sqrt(cabs2(ga));
-          if (g > 0.0 && g > tol * sqrt(al * be)) {
+          if (g > gnull && g > tol * sqrt(al * be)) {
             // rotate (p, q) so that the pair becomes orthogonal
             double zeta = (be - al) / (2.0 * g);
             double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));

@@ -252,9 +252,10 @@ class Context:
         return ms
 
     def solver_paths(self):
-        """Counts since the last call: ALS Cholesky-certified solves, ALS
-        eigen solves, metrics certified PD, metrics eigen-repaired."""
-        c = np.zeros(4, dtype=np.int32)
+        """Counts since the last call: ALS solves certified by Gershgorin
+        discs (CG solve), by shifted Cholesky (refinement solve), ALS eigen
+        solves, metrics certified PD, metrics eigen-repaired."""
+        c = np.zeros(5, dtype=np.int32)
         self._ck(self.lib.ntu_solver_paths(self.h, _ptr(c)))
-        return {"als_cholesky": int(c[0]), "als_eigen": int(c[1]),
-                "repair_cholesky": int(c[2]), "repair_eigen": int(c[3])}
+        return {"als_gershgorin": int(c[0]), "als_cholesky": int(c[1]), "als_eigen": int(c[2]),
+                "repair_cholesky": int(c[3]), "repair_eigen": int(c[4])}

@@ -231,15 +231,57 @@ def test_als_matches_oracle(D, r, sweeps, kmin):
     paths = ctx.solver_paths()
     solves = n * 2 * sweeps
     if kmin == 4:
-        assert paths["als_cholesky"] == solves and paths["als_eigen"] == 0
+        # random-tensor metrics give diagonally dominant g_A: the discs decide
+        assert paths["als_gershgorin"] + paths["als_cholesky"] == solves
+        assert paths["als_gershgorin"] > 0 and paths["als_eigen"] == 0
     else:
-        assert paths["als_cholesky"] == 0 and paths["als_eigen"] == solves
+        assert paths["als_gershgorin"] + paths["als_cholesky"] == 0
+        assert paths["als_eigen"] == solves
     for i in range(n):
         ma, mb, eps, delta, eps0, tau = refs[i]
         inf = info[i].cpu().numpy()
         assert abs(inf[2] - eps0) < 1e-12 * eps0
         assert abs(inf[1] - delta) < 1e-8
         assert abs(inf[0] - eps) < 1e-8 * eps0
+        assert inf[3] == tau
+        assert _rel(MA[i].cpu().numpy(), ma) < 1e-8
+        assert _rel(MB[i].cpu().numpy(), mb) < 1e-8
+
+
+@pytest.mark.parametrize("spread,path", [(30.0, "als_cholesky"), (1e7, "als_eigen")])
+def test_als_dense_metric_paths(spread, path):
+    """A dense metric g = W diag(lam) W^H (W Haar-random, lam geometric on
+    [1, spread]) makes g_A far from diagonally dominant.  With spread 30 the
+    discs fail but the shifted Cholesky proves every tolerance of the grid
+    keeps every eigenpair; with spread 1e7 the smallest eigenvalues fall below
+    tau_max lambda_max and the full selection of Eq. 4 must run."""
+    D, r, sweeps, n = 3, 2, 4, 2
+    K = D * r
+    ng = K * K
+    rng = np.random.default_rng(4242)
+    gs, RAs, RBs, refs = [], [], [], []
+    cfg = O.Config(D=D, r=r, sweeps=sweeps)
+    for _ in range(n):
+        a = rng.standard_normal((ng, ng)) + 1j * rng.standard_normal((ng, ng))
+        w, _ = np.linalg.qr(a)
+        g = (w * np.geomspace(1.0, spread, ng)) @ w.conj().T
+        g = 0.5 * (g + g.conj().T)
+        RA = rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K))
+        RB = rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K))
+        gs.append(g); RAs.append(RA); RBs.append(RB)
+        refs.append(O.als_truncate(g, RA, RB, D, sweeps, cfg.taus))
+    ctx = _ctx(D, r, sweeps=sweeps, max_batch=n, kmin=4)
+    MA, MB = _empty((n, K, D)), _empty((n, K, D))
+    info = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    ctx.solver_paths()
+    ctx.batch_als_dev(n, _dev(np.stack(gs)), _dev(np.stack(RAs)), _dev(np.stack(RBs)), MA, MB, info)
+    ctx.sync()
+    assert ctx.solver_paths()[path] == n * 2 * sweeps
+    for i in range(n):
+        ma, mb, eps, delta, eps0, tau = refs[i]
+        inf = info[i].cpu().numpy()
+        assert abs(inf[2] - eps0) < 1e-12 * eps0
+        assert abs(inf[1] - delta) < 1e-9
         assert inf[3] == tau
         assert _rel(MA[i].cpu().numpy(), ma) < 1e-8
         assert _rel(MB[i].cpu().numpy(), mb) < 1e-8
