@@ -53,14 +53,16 @@ def env_flops(D, r, d_p=2):
 
 
 def als_flops(D, r, sweeps):
-    """Real FP64 flops of the ALS stage of one bond update: per sweep two
-    reduced-metric builds (8 (K^4 D + K^3 D^2) each) and two Hermitian
-    tridiagonalisations of n_A = K D ((16/3) n_A^3 each), plus g x0 and the
-    final error (8 n_g^2 each)."""
+    """Algorithmic real FP64 flops of the ALS stage of one bond update (Fig. 5):
+    per half sweep the Hermitian reduced metric g_A, K^4 D + K^3 D^2 complex
+    multiply-adds of which the lower triangle needs half, and the residual
+    J - g_A m of the solve (one n_A x n_A product, n_A = K D); plus g x0 and
+    the final error (8 n_g^2 each).  The K x D SVDs of the tilts are not
+    counted."""
     K = D * r
     nA, ng = K * D, K * K
-    per_sweep = 2 * 8.0 * (K ** 4 * D + K ** 3 * D * D) + 2 * (16.0 / 3.0) * nA ** 3
-    return sweeps * per_sweep + 2 * 8.0 * ng * ng
+    half = 8.0 * (K ** 4 * D + K ** 3 * D * D) / 2 + 8.0 * nA * nA
+    return sweeps * 2 * half + 2 * 8.0 * ng * ng
 
 
 def env_roof(precision, achieved, peaks):

@@ -276,8 +276,8 @@ extern "C" int ntu_last_launch_count(const ntu_ctx* c) { return c ? c->launches 
 extern "C" int ntu_solver_paths(ntu_ctx* c, int* counts) {
   if (!c || !counts) return fail(c, NTU_EINVAL, "ntu_solver_paths: NULL argument");
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");
-  CK(cudaMemcpy(counts, c->d_paths, 5 * sizeof(int), cudaMemcpyDeviceToHost), "read counters");
-  CK(cudaMemset(c->d_paths, 0, 5 * sizeof(int)), "reset counters");
+  CK(cudaMemcpy(counts, c->d_paths, 6 * sizeof(int), cudaMemcpyDeviceToHost), "read counters");
+  CK(cudaMemset(c->d_paths, 0, 6 * sizeof(int)), "reset counters");
   return NTU_OK;
 }
 

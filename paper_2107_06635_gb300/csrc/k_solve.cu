@@ -17,12 +17,14 @@ __device__ __forceinline__ double2 ld2(const float2* p) {
 }
 
 // ------------------------------------------------------------- repair
-// g <- (g + g^H)/2; if a Cholesky factorisation of g succeeds, g is
-// positive definite and clipping its negative eigenvalues would change
-// nothing; otherwise g = W diag(max(lambda, 0)) W^H from a full
+// g <- (g + g^H)/2.  g is positive definite, and clipping its negative
+// eigenvalues would change nothing, when the Gershgorin discs of the rows
+// lie right of zero (min_i d_i - s_i > 0, s_i = sum_{j != i} |Re| + |Im| >=
+// sum_{j != i} |g_ij|) or, failing that, when a Cholesky factorisation of g
+// succeeds; otherwise g = W diag(max(lambda, 0)) W^H from a full
 // eigendecomposition.  Finally g /= trace(g).
-// diag = [||g - g^H|| / ||g||, lambda_min / lambda_max (NaN on the Cholesky
-// path), log(trace)].
+// diag = [||g - g^H|| / ||g||, lambda_min / lambda_max (NaN on the two
+// certified paths), log(trace)].
 template <typename C2in>
 __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restrict__ graw,
                                                     double2* __restrict__ g,
@@ -38,30 +40,63 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
   __shared__ double sred[2 * NTU_WARPS];
   __shared__ int sh[4];
   __shared__ int okflag;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
   const long long item = blockIdx.x;
   const size_t nn = (size_t)ng * ng;
   const C2in* gr = graw + item * nn;
   double2* gi = g + item * nn;
   double2* sc = scr + item * nn;
-  // 1. Hermitise
-  double n2 = 0.0, h2 = 0.0;
+  // 1. Hermiticity defect, Gershgorin discs and trace of the Hermitian part,
+  // one warp per row
+  double n2 = 0.0, h2 = 0.0, glo = INFINITY, trw = 0.0;
+  for (int r = wid; r < ng; r += NTU_WARPS) {
+    double sr = 0.0, dr = 0.0;
+    for (int c = lid; c < ng; c += 32) {
+      double2 a = ld2(gr + (size_t)r * ng + c), b = ld2(gr + (size_t)c * ng + r);
+      double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+      n2 += cabs2(a);
+      h2 += cabs2(make_double2(a.x - b.x, a.y + b.y));
+      if (c == r) dr = h.x;
+      else sr += fabs(h.x) + fabs(h.y);
+    }
+    sr = warp_sum(sr);
+    dr = warp_sum(dr);                   // one lane holds the diagonal
+    glo = fmin(glo, dr - sr * (1.0 + 1e-12));   // margin for the rounding of s
+    trw += dr;
+  }
+  if (lid != 0) trw = 0.0;
+  n2 = block_sum(n2, sred);
+  h2 = block_sum(h2, sred);
+  glo = block_min(glo, sred);
+  const double trg = block_sum(trw, sred);
+  const double herm = n2 > 0.0 ? sqrt(h2 / n2) : 0.0;
+  if (glo > 0.0 && isfinite(glo) && trg > 0.0 && isfinite(trg)) {
+    // certified by the discs: write (g + g^H) / (2 tr) directly
+    const double inv = 1.0 / trg;
+    for (size_t idx = tid; idx < nn; idx += NTU_CTA) {
+      int r = idx / ng, c = idx % ng;
+      double2 a = ld2(gr + idx), b = ld2(gr + (size_t)c * ng + r);
+      gi[idx] = cscale(make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y)), inv);
+    }
+    if (tid == 0) {
+      if (paths) atomicAdd(paths + 3, 1);
+      diag[item * 3 + 0] = herm;
+      diag[item * 3 + 1] = __longlong_as_double(0x7ff8000000000000ULL);   // NaN
+      diag[item * 3 + 2] = log(trg);
+    }
+    return;
+  }
   for (size_t idx = tid; idx < nn; idx += NTU_CTA) {
     int r = idx / ng, c = idx % ng;
     double2 a = ld2(gr + idx), b = ld2(gr + (size_t)c * ng + r);
     double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
-    n2 += cabs2(a);
-    h2 += cabs2(make_double2(a.x - b.x, a.y + b.y));
     gi[idx] = h;
     sc[(size_t)c * ng + r] = h;          // column-major copy
   }
-  n2 = block_sum(n2, sred);
-  h2 = block_sum(h2, sred);
-  const double herm = n2 > 0.0 ? sqrt(h2 / n2) : 0.0;
   // 2. Cholesky of the lower triangle certifies positive definiteness
   __syncthreads();
   int ok = cta_cholesky(sc, ng, 0.0, &okflag);
-  if (tid == 0 && paths) atomicAdd(paths + (ok ? 3 : 4), 1);
+  if (tid == 0 && paths) atomicAdd(paths + (ok ? 4 : 5), 1);
   double ratio = __longlong_as_double(0x7ff8000000000000ULL);   // NaN
   if (!ok) {
     // 3. full eigendecomposition and clipping of negative eigenvalues
@@ -150,6 +185,7 @@ struct AlsShared {
   double2 y2[256];
   double2 p[256];
   double2 ap[256];
+  double2 ph[32];
   double red[2 * NTU_WARPS];
   double eps0, tau_sel;
   int err;
@@ -199,6 +235,82 @@ __device__ void als_tilt(AlsShared& sm, const AlsArgs& a, int mode, const double
   __syncthreads();
 }
 
+// Tilt (modes 0, 1) or balance (mode 2) from the factors of the previous
+// half step without forming X = MA MB^T.  One factor is an isometry left by
+// the previous SVD, the other (Y) came out of the last solve.  Mode 1: Y = MA
+// and MB = conj(V), so X = Y V^H; with Y = P S Q^H, U = P and V' = V Q, hence
+// MA = P and MB = MB conj(Q) S.  Modes 0 and 2: Y = MB and MA = U, so
+// X = MA conj(Q) S P^T, U' = MA conj(Q) and V' = conj(P), hence MA = U' S and
+// MB = P (mode 0), or MA = U' sqrt(S) and MB = P sqrt(S) (mode 2).  U' gets
+// the phase convention of the square SVD, V' the same phases.  The thin SVD
+// of the K x D factor replaces the SVD of the K x K product of rank D.
+// Returns 0 with MA and MB untouched when Y is numerically rank deficient
+// (s_min <= 1e-14 s_max): the null directions of X then come from the square
+// SVD of als_tilt.
+__device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
+  const int tid = threadIdx.x, K = a.K, D = a.D;
+  const double2* Y = mode == 1 ? sm.MA : sm.MB;
+  const double2* Z = mode == 1 ? sm.MB : sm.MA;
+  for (int idx = tid; idx < 32 * 32; idx += NTU_CTA) {
+    int i = idx & 31, q = idx >> 5;
+    sm.S.A[idx] = (i < K && q < D) ? Y[i * D + q] : cz();
+  }
+  __syncthreads();
+  cta_svd_cols(sm.S, K, D, mode == 1);
+  if (sm.S.bad || !(sm.S.s[D - 1] > 1e-14 * sm.S.s[0])) return 0;
+  // W = Z conj(Q), K x D column-major
+  for (int idx = tid; idx < 32 * 32; idx += NTU_CTA) {
+    int i = idx & 31, q = idx >> 5;
+    double2 acc = cz();
+    if (i < K && q < D)
+      for (int p = 0; p < D; ++p) acc = cfma(Z[i * D + p], cconj(sm.S.V[q * 32 + p]), acc);
+    sm.S.W[idx] = acc;
+  }
+  __syncthreads();
+  if (mode == 1) {
+    for (int idx = tid; idx < K * D; idx += NTU_CTA) {
+      int i = idx / D, q = idx % D;
+      sm.MA[idx] = sm.S.A[q * 32 + i];
+      sm.MB[idx] = cscale(sm.S.W[q * 32 + i], sm.S.s[q]);
+    }
+    __syncthreads();
+    return 1;
+  }
+  // phase of each column of U' = W: its first entry within 1e-10 of the
+  // largest modulus becomes real positive
+  const int grp = tid >> 4, lane = tid & 15;
+  const unsigned mask = 0xffffu << (tid & 16);
+  for (int k = grp; k < D; k += 16) {
+    double mx = 0.0;
+    for (int r = lane; r < K; r += 16) mx = fmax(mx, cabs2(sm.S.W[k * 32 + r]));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(mask, mx, o));
+    mx = sqrt(mx);
+    int piv = 1 << 30;
+    for (int r = lane; r < K; r += 16)
+      if (mx > 0.0 && sqrt(cabs2(sm.S.W[k * 32 + r])) >= (1.0 - 1e-10) * mx) piv = min(piv, r);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(mask, piv, o));
+    double2 ph = make_double2(1.0, 0.0);
+    if (mx > 0.0 && isfinite(mx) && piv < K) {
+      double2 up = sm.S.W[k * 32 + piv];
+      double am = sqrt(cabs2(up));
+      ph = make_double2(up.x / am, -up.y / am);
+    }
+    if (lane == 0) sm.ph[k] = ph;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < K * D; idx += NTU_CTA) {
+    int i = idx / D, q = idx % D;
+    const double sv = sm.S.s[q], rs = mode == 2 ? sqrt(sv) : 1.0;
+    const double2 ph = sm.ph[q];
+    sm.MA[idx] = cscale(cmul(sm.S.W[q * 32 + i], ph), mode == 2 ? rs : sv);
+    sm.MB[idx] = cscale(cmul(sm.S.A[q * 32 + i], cconj(ph)), rs);
+  }
+  __syncthreads();
+  return 1;
+}
+
 // Reduced metric and source for the free side (Fig. 5(b,c)).  side 0: the
 // A step, free index i of (i, j), fixed F = MB; side 1: the B step, free j,
 // F = MA.  gX is written column-major (nA x nA), J into a.jv.
@@ -207,9 +319,11 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
   const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
   const double2* F = side == 0 ? sm.MB : sm.MA;
   const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
-  // Tm[r][(f,q)] = sum_c g[r][f*sf + c*sc] F[c][q]
+  // Tm[r][(f,q)] = sum_c g[r][f*sf + c*sc] F[c][q], only where the free
+  // index of row r is >= f: the lower triangle of gX below reads no other
   for (int idx = tid; idx < ng * nA; idx += NTU_CTA) {
     int r = idx / nA, fq = idx % nA, f = fq / D, q = fq % D;
+    if ((side == 0 ? r / K : r % K) < f) continue;
     const double2* gr = g + (size_t)r * ng + f * sf;
     double2 acc = cz();
     for (int c = 0; c < K; ++c) acc = cfma(gr[c * sc], F[c * D + q], acc);
@@ -278,16 +392,25 @@ __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2
   const double sigma = (tau_max + 1e-12) * bmax;
   if (glo > sigma) {
     // Tier 1: the discs alone prove lambda_min > tau_max lambda_max; solve
-    // gX v = J by conjugate gradients on the full matrix.
+    // gX v = J by conjugate gradients on the full matrix, started from the
+    // current factor (the tilt left it in the gauge of the fixed side, so
+    // near convergence of the sweeps it already solves the system).
     als_mirror(gX, nA);
+    const double2* M0 = side == 0 ? sm.MA : sm.MB;
+    double js = 0.0, rs = 0.0;
     for (int i = tid; i < nA; i += NTU_CTA) {
-      sm.y[i] = cz(); sm.y2[i] = jv[i]; sm.p[i] = jv[i];
+      double2 r = jv[i];
+      for (int j = 0; j < nA; ++j) r = cfms(gX[(size_t)j * nA + i], M0[j], r);
+      sm.y[i] = M0[i]; sm.y2[i] = r; sm.p[i] = r;
+      js += cabs2(jv[i]);
+      rs += cabs2(r);
     }
-    double rs = 0.0;
-    for (int i = tid; i < nA; i += NTU_CTA) rs += cabs2(jv[i]);
+    js = block_sum(js, sm.red);
     rs = block_sum(rs, sm.red);
-    const double stop = 1e-30 * rs;                          // |r| <= 1e-15 |J|
-    int conv = rs == 0.0;
+    const double stop = 1e-30 * js;                          // |r| <= 1e-15 |J|
+    const double floor2 = 1e-26 * js;                        // |r| <= 1e-13 |J|
+    int conv = rs <= stop;
+    double prev = rs;
     for (int it = 0; it < 80 && !conv; ++it) {
       for (int i = tid; i < nA; i += NTU_CTA) {
         double2 acc = cz();
@@ -308,7 +431,9 @@ __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2
         rn += cabs2(r);
       }
       rn = block_sum(rn, sm.red);
-      if (rn <= stop) { conv = 1; break; }
+      // converged, or stalled at the rounding floor of the recursion
+      if (rn <= stop || (it >= 2 && rn > 0.25 * prev && rn <= floor2)) { conv = 1; break; }
+      prev = rn;
       const double beta = rn / rs;
       rs = rn;
       for (int i = tid; i < nA; i += NTU_CTA) {
@@ -332,7 +457,8 @@ __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2
   __syncthreads();
   if (!cta_cholesky(gC, nA, sigma, &sm.flag)) return 0;
   if (wid == 0) {
-    for (int i = lid; i < nA; i += 32) sm.y[i] = cz();
+    const double2* M0 = side == 0 ? sm.MA : sm.MB;
+    for (int i = lid; i < nA; i += 32) sm.y[i] = M0[i];     // warm start
     __syncwarp();
     int conv = 0;
     double prev = INFINITY;
@@ -478,11 +604,13 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   e0 = block_sum(e0, sm.red);
   if (tid == 0) sm.eps0 = e0;
   __syncthreads();
-  // SVDU start (Fig. 2(c,d))
-  als_tilt(sm, a, 2, x0);
+  // SVDU start (Fig. 2(c,d)).  X0 = U S V^H gives the balanced start
+  // (U sqrt(S), conj(V) sqrt(S)) whose first tilt is (U S, conj(V)): with
+  // sweeps to run, the start goes straight to the tilted pair.
+  als_tilt(sm, a, a.sweeps > 0 ? 0 : 2, x0);
   for (int s = 0; s < a.sweeps; ++s) {
     for (int side = 0; side < 2; ++side) {
-      als_tilt(sm, a, side, nullptr);
+      if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
       als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
       if (!als_solve_chol(sm, a, side, gX, gC, jv, tau_max)) {
         als_mirror(gX, nA);
@@ -490,7 +618,8 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
       }
     }
   }
-  als_tilt(sm, a, 2, nullptr);      // balance (Fig. 5(d))
+  // balance (Fig. 5(d))
+  if (a.sweeps > 0 && !als_tilt_fast(sm, a, 2)) als_tilt(sm, a, 2, nullptr);
   // eps = x^H g x, x = vec(MA MB^T) - x0
   double2* xv = Tm;
   for (int idx = tid; idx < ng; idx += NTU_CTA) {

@@ -215,13 +215,15 @@ __device__ inline Reflector cta_reflector(const double2* v, int len, double* sre
 }
 
 // -------------------------------------------------- one-sided Jacobi SVD
-// SVD of an n x n complex matrix (n <= 32) held column-major in shared
-// memory with leading dimension 32.  On exit U (in A's storage) holds the
-// left singular vectors sorted by descending singular value, s the values,
-// V the right singular vectors, and each column pair carries the phase
-// convention "first entry of u within 1e-10 of the largest modulus is real
-// positive".  Columns with zero singular value are returned as zero vectors.
-// Work space: W (32 x 32 complex) and sw (>= 3*32 doubles + 32 ints).
+// SVD of an m x n complex matrix (m, n <= 32) held column-major in shared
+// memory with leading dimension 32: A V = U diag(s).  On exit A's first n
+// columns hold the left singular vectors U (m x n) sorted by descending
+// singular value, s the values, V (n x n) the right singular vectors.  With
+// phase != 0 each column pair carries the convention "first entry of u within
+// 1e-10 of the largest modulus is real positive".  Columns with zero singular
+// value are returned as zero vectors.  For m < n the trailing n - m values
+// are zero.  Work space: W (32 x 32 complex) and sw (>= 3*32 doubles + 32
+// ints).
 struct SvdSmem {
   double2 A[32 * 32];
   double2 V[32 * 32];
@@ -233,20 +235,21 @@ struct SvdSmem {
   int bad;        // set when a singular value came out non-finite
 };
 
-__device__ inline void cta_svd_small(SvdSmem& S, int n) {
+__device__ inline void cta_svd_cols(SvdSmem& S, int m, int n, int phase) {
   const int tid = threadIdx.x;
   const int np = (n + 1) & ~1;          // even number of columns (virtual zero col)
   // V = identity
   for (int i = tid; i < 32 * 32; i += NTU_CTA) {
     int r = i & 31, c = i >> 5;
     S.V[i] = make_double2(r == c ? 1.0 : 0.0, 0.0);
-    if (c >= n || r >= n) S.A[i] = cz();
+    if (c >= n || r >= m) S.A[i] = cz();
   }
   __syncthreads();
   const int grp = tid >> 4;             // 16 groups of 16 lanes
   const int lane = tid & 15;
   const unsigned mask = 0xffffu << ((tid & 16));
-  const double tol = fmax(1e-15, 2.3e-16 * n);
+  const double tol = fmax(1e-15, 2.3e-16 * m);
+  const double tol2 = tol * tol;
   // Frobenius norm^2 of the input: pairs whose inner product is below
   // 1e-30 of it belong to the numerical null space and are not rotated
   // (their rounding-level inner products would otherwise never converge).
@@ -265,7 +268,7 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
         if (p > q) { int tmp = p; p = q; q = tmp; }
         if (q < n) {
           double al = 0.0, be = 0.0; double2 ga = cz();
-          for (int r = lane; r < n; r += 16) {
+          for (int r = lane; r < m; r += 16) {
             double2 ap = S.A[p * 32 + r], aq = S.A[q * 32 + r];
             al += cabs2(ap); be += cabs2(aq); ga = cfmac(ap, aq, ga);
           }
@@ -276,17 +279,23 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
             ga.x += __shfl_xor_sync(mask, ga.x, o);
             ga.y += __shfl_xor_sync(mask, ga.y, o);
           }
-          double g = sqrt(cabs2(ga));
-          if (g > gnull && g > tol * sqrt(al * be)) {
-            // rotate (p, q) so that the pair becomes orthogonal
-            double zeta = (be - al) / (2.0 * g);
-            double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-            double2 ph = make_double2(ga.x / g, -ga.y / g);     // e^{-i phi}
-            for (int r = lane; r < n; r += 16) {
+          const double g2 = cabs2(ga);
+          const double rg = g2 > 0.0 ? rsqrt(g2) : 0.0;      // 1 / |<a_p, a_q>|
+          if (g2 * rg > gnull && g2 > tol2 * (al * be)) {
+            // rotate (p, q) so that the pair becomes orthogonal: with
+            // zeta = (|a_q|^2 - |a_p|^2) / (2 |g|), t = sign(zeta) /
+            // (|zeta| + sqrt(1 + zeta^2)) is the smaller root of
+            // t^2 + 2 zeta t - 1 = 0, c = 1 / sqrt(1 + t^2), s = c t
+            const double zeta = (be - al) * (0.5 * rg);
+            const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = rsqrt(1.0 + tt * tt), s = c * tt;
+            const double2 ph = make_double2(ga.x * rg, -ga.y * rg);     // e^{-i phi}
+            for (int r = lane; r < m; r += 16) {
               double2 ap = S.A[p * 32 + r], aq = cmul(S.A[q * 32 + r], ph);
               S.A[p * 32 + r] = make_double2(c * ap.x - s * aq.x, c * ap.y - s * aq.y);
               S.A[q * 32 + r] = make_double2(s * ap.x + c * aq.x, s * ap.y + c * aq.y);
+            }
+            for (int r = lane; r < n; r += 16) {
               double2 vp = S.V[p * 32 + r], vq = cmul(S.V[q * 32 + r], ph);
               S.V[p * 32 + r] = make_double2(c * vp.x - s * vq.x, c * vp.y - s * vq.y);
               S.V[q * 32 + r] = make_double2(s * vp.x + c * vq.x, s * vp.y + c * vq.y);
@@ -303,7 +312,7 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
   // singular values = column norms
   for (int c = grp; c < n; c += 16) {
     double a = 0.0;
-    for (int r = lane; r < n; r += 16) a += cabs2(S.A[c * 32 + r]);
+    for (int r = lane; r < m; r += 16) a += cabs2(S.A[c * 32 + r]);
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(mask, a, o);
     if (lane == 0) S.s[c] = sqrt(a);
@@ -329,11 +338,11 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
     S.perm[rank] = tid;
   }
   __syncthreads();
-  // gather into W (U) and A's old storage reused for sorted V via W swap
+  // gather the normalised, sorted columns (U) into W
   for (int i = tid; i < 32 * 32; i += NTU_CTA) {
     int r = i & 31, k = i >> 5;
     double2 u = cz();
-    if (k < n && r < n) {
+    if (k < n && r < m) {
       int src = S.perm[k] & 31;
       double sv = S.s[src];
       if (sv > 0.0 && isfinite(sv)) u = cscale(S.A[src * 32 + r], 1.0 / sv);
@@ -341,6 +350,7 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
     S.W[i] = u;
   }
   __syncthreads();
+  // sorted V into A's storage, then V <- A and A <- W
   for (int i = tid; i < 32 * 32; i += NTU_CTA) {
     int r = i & 31, k = i >> 5;
     S.A[i] = (k < n && r < n) ? S.V[(S.perm[k] & 31) * 32 + r] : cz();
@@ -350,35 +360,36 @@ __device__ inline void cta_svd_small(SvdSmem& S, int n) {
   if (tid < n) sv_sorted = S.s[S.perm[tid] & 31];
   __syncthreads();
   if (tid < n) S.s[tid] = sv_sorted;
-  // W = U (sorted), A = V (sorted); move V to V, U to A
   for (int i = tid; i < 32 * 32; i += NTU_CTA) { S.V[i] = S.A[i]; }
   __syncthreads();
   for (int i = tid; i < 32 * 32; i += NTU_CTA) { S.A[i] = S.W[i]; }
   __syncthreads();
+  if (!phase) return;
   // phase convention, one group per column
   for (int k = grp; k < n; k += 16) {
-    double m = 0.0;
-    for (int r = lane; r < n; r += 16) m = fmax(m, cabs2(S.A[k * 32 + r]));
+    double mx = 0.0;
+    for (int r = lane; r < m; r += 16) mx = fmax(mx, cabs2(S.A[k * 32 + r]));
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(mask, m, o));
-    m = sqrt(m);
+    for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(mask, mx, o));
+    mx = sqrt(mx);
     int piv = 1 << 30;
-    for (int r = lane; r < n; r += 16)
-      if (m > 0.0 && sqrt(cabs2(S.A[k * 32 + r])) >= (1.0 - 1e-10) * m) piv = min(piv, r);
+    for (int r = lane; r < m; r += 16)
+      if (mx > 0.0 && sqrt(cabs2(S.A[k * 32 + r])) >= (1.0 - 1e-10) * mx) piv = min(piv, r);
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(mask, piv, o));
-    if (m > 0.0 && isfinite(m) && piv < n) {
+    if (mx > 0.0 && isfinite(mx) && piv < m) {
       double2 up = S.A[k * 32 + piv];
       double a = sqrt(cabs2(up));
       double2 ph = make_double2(up.x / a, -up.y / a);
-      for (int r = lane; r < n; r += 16) {
-        S.A[k * 32 + r] = cmul(S.A[k * 32 + r], ph);
-        S.V[k * 32 + r] = cmul(S.V[k * 32 + r], ph);
-      }
+      for (int r = lane; r < m; r += 16) S.A[k * 32 + r] = cmul(S.A[k * 32 + r], ph);
+      for (int r = lane; r < n; r += 16) S.V[k * 32 + r] = cmul(S.V[k * 32 + r], ph);
     }
   }
   __syncthreads();
 }
+
+// Square n x n case with the phase convention.
+__device__ inline void cta_svd_small(SvdSmem& S, int n) { cta_svd_cols(S, n, n, 1); }
 
 // --------------------------------------- Hermitian tridiagonalisation
 // A (n x n complex Hermitian, column-major, leading dim n, global memory) is

@@ -114,7 +114,8 @@ struct ntu_ctx {
   size_t env_es;      // element size of the environment buffers
   int profiling;
   cudaEvent_t ev[6];
-  int* d_paths;       // [ALS Gershgorin+CG, ALS shifted Cholesky, ALS eigen, repair Cholesky, repair eigen]
+  int* d_paths;       // [ALS Gershgorin+CG, ALS shifted Cholesky, ALS eigen,
+                      //  repair Gershgorin, repair Cholesky, repair eigen]
   int debug_sync;     // synchronise and check after every launch (NTU_DEBUG_SYNC=1)
 };
 

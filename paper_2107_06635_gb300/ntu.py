@@ -254,8 +254,10 @@ class Context:
     def solver_paths(self):
         """Counts since the last call: ALS solves certified by Gershgorin
         discs (CG solve), by shifted Cholesky (refinement solve), ALS eigen
-        solves, metrics certified PD, metrics eigen-repaired."""
-        c = np.zeros(5, dtype=np.int32)
+        solves; metrics certified PD by Gershgorin discs, by Cholesky, and
+        metrics eigen-repaired."""
+        c = np.zeros(6, dtype=np.int32)
         self._ck(self.lib.ntu_solver_paths(self.h, _ptr(c)))
         return {"als_gershgorin": int(c[0]), "als_cholesky": int(c[1]), "als_eigen": int(c[2]),
-                "repair_cholesky": int(c[3]), "repair_eigen": int(c[4])}
+                "repair_gershgorin": int(c[3]), "repair_cholesky": int(c[4]),
+                "repair_eigen": int(c[5])}

@@ -154,24 +154,47 @@ def test_env_bf16x3_tensor_cores_within_budget(D, r):
 
 
 # --------------------------------------------------------------- repair
-def test_repair_cholesky_path_matches_oracle():
+@pytest.mark.parametrize("kind", ["network", "dense"])
+def test_repair_certified_paths_match_oracle(kind):
+    """Positive definite input: nothing to clip.  Metrics of random site
+    tensors are often diagonally dominant, so the Gershgorin discs certify
+    them, else the Cholesky factorisation does; a dense positive definite
+    matrix W diag(lam) W^H (Haar W, lam in [1, 30]) is far from diagonally
+    dominant and needs the Cholesky factorisation."""
     D, r, n = 3, 2, 2
-    Ta, Tb, G = _items(500, n, 2, D)
-    cfg = O.Config(D=D, r=r)
     raws, refs = [], []
-    for i in range(n):
-        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
-        raw = O.metric_raw(Ta[i], Tb[i], qa, qb, 2, D)
-        raws.append(raw)
-        refs.append(O.hermitise_repair(raw))
+    if kind == "network":
+        Ta, Tb, G = _items(500, n, 2, D)
+        cfg = O.Config(D=D, r=r)
+        for i in range(n):
+            qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+            raws.append(O.metric_raw(Ta[i], Tb[i], qa, qb, 2, D))
+    else:
+        rng = np.random.default_rng(11)
+        ng = (D * r) ** 2
+        for i in range(n):
+            a = rng.standard_normal((ng, ng)) + 1j * rng.standard_normal((ng, ng))
+            w, _ = np.linalg.qr(a)
+            h = (w * np.geomspace(1.0, 30.0, ng)) @ w.conj().T
+            raws.append(h + 1e-3 * rng.standard_normal((ng, ng)))    # small anti-Hermitian part
+    refs = [O.hermitise_repair(x) for x in raws]
     ctx = _ctx(D, r, max_batch=n)
     g = _dev(np.stack(raws))
     diag = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ctx.solver_paths()
     ctx.batch_repair_dev(n, g, diag)
     ctx.sync()
+    paths = ctx.solver_paths()
+    if kind == "network":
+        # of these two metrics the first is diagonally dominant (min_i d_i - s_i
+        # = +0.21 max d), the second is not (-0.19 max d)
+        assert paths["repair_gershgorin"] == 1 and paths["repair_cholesky"] == 1
+    else:
+        assert paths["repair_cholesky"] == n
     for i in range(n):
         assert _rel(g[i].cpu().numpy(), refs[i][0]) < 1e-12
         dg = diag[i].cpu().numpy()
+        assert abs(dg[0] - refs[i][1][0]) < 1e-12 * max(1.0, refs[i][1][0])
         assert abs(dg[2] - refs[i][1][2]) < 1e-12
         assert np.isnan(dg[1])          # certified positive definite, no repair
 
