@@ -186,6 +186,8 @@ struct AlsShared {
   double2 p[256];
   double2 ap[256];
   double2 ph[32];
+  float4 Fdf[32 * 8];
+  int cumX[257];               // item offsets of the row blocks of the double-FP32 build
   double red[2 * NTU_WARPS];
   double eps0, tau_sel;
   int err;
@@ -203,6 +205,8 @@ struct AlsArgs {
   int* rk;
   int rotcap;
   int* status;
+  int df;                      // build the reduced metric in double-FP32 arithmetic
+  float4* gdf;                 // n x ng^2 scratch: g split into FP32 pairs
 };
 
 // X = MA MB^T -> SVD -> (MA, MB) by mode: 0 tilt before the A step
@@ -311,6 +315,140 @@ __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
   return 1;
 }
 
+// ------------------------------------------- double-FP32 arithmetic
+// A real number x is carried as an unevaluated sum hi + lo of two FP32
+// values (hi = fl32(x), lo = fl32(x - hi)), good to about 2^-48 relative; a
+// complex number as float4 (re_hi, im_hi, re_lo, im_lo).  Products use the
+// exact FMA residual of hi * hi plus the two cross terms (lo * lo is below
+// the format's precision); sums keep the rounding error of the high part
+// exactly (two-sum) and add all low-order terms in FP32.  The explicitly
+// rounded intrinsics keep the compiler from contracting the error terms.
+// On this GPU FP32 issues at 64x the FP64 rate, so the ~12 FP32 operations
+// of a real multiply-add cost less than a sixth of one FP64 FMA.
+__device__ __forceinline__ float4 df_split(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, ih, __double2float_rn(v.x - (double)rh),
+                     __double2float_rn(v.y - (double)ih));
+}
+__device__ __forceinline__ double2 df_join(float4 a) {
+  return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+}
+// (sh, sl) += (xh + xl) (yh + yl)
+__device__ __forceinline__ void df_mac1(float& sh, float& sl, float xh, float xl, float yh,
+                                        float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float t = __fadd_rn(sh, p);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+// acc += a * b, or conj(a) * b with CONJ
+template <bool CONJ>
+__device__ __forceinline__ void df_cmac(float4& acc, float4 a, float4 b) {
+  const float s = CONJ ? -1.0f : 1.0f;
+  df_mac1(acc.x, acc.z, a.x, a.z, b.x, b.z);                  // re += ar br
+  df_mac1(acc.x, acc.z, -s * a.y, -s * a.w, b.y, b.w);        // re -+= ai bi
+  df_mac1(acc.y, acc.w, a.x, a.z, b.y, b.w);                  // im += ar bi
+  df_mac1(acc.y, acc.w, s * a.y, s * a.w, b.x, b.z);          // im +-= ai br
+}
+
+// g (FP64) -> gdf = g 2^-e in FP32 pairs, with 2^e the power of two nearest
+// above max |Re|, |Im| (an exact scaling that keeps every entry in FP32
+// range).  Returns e.
+__device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng) {
+  const int tid = threadIdx.x;
+  const size_t nn = (size_t)ng * ng;
+  double mx = 0.0;
+  for (size_t i = tid; i < nn; i += NTU_CTA) mx = fmax(mx, fmax(fabs(g[i].x), fabs(g[i].y)));
+  mx = block_max(mx, sm.red);
+  const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
+  for (size_t i = tid; i < nn; i += NTU_CTA) {
+    double2 v = g[i];
+    gdf[i] = df_split(make_double2(scalbn(v.x, -e), scalbn(v.y, -e)));
+  }
+  __syncthreads();
+  return e;
+}
+
+// als_reduced in double-FP32 arithmetic: same contractions and the same
+// block lower triangle, each thread holding four q columns in registers;
+// gX comes out in FP64 (scaled back by 2^e).  F (the isometric factor) is
+// split into sm.Fdf.
+__device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gdf, int e,
+                               int side, float4* Tmdf, double2* gX) {
+  const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
+  const double2* F = side == 0 ? sm.MB : sm.MA;
+  const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
+  const int nq = (D + 3) >> 2;
+  for (int i = tid; i < K * D; i += NTU_CTA) sm.Fdf[i] = df_split(F[i]);
+  __syncthreads();
+  // Tm[r][(f,q)] = sum_c g[r][f*sf + c*sc] F[c][q] for free(r) = fp >= f.
+  // Work items (pair t = (fp, f), c', q block) are enumerated densely, so
+  // every lane and every thread does the same amount of work.
+  const int npair = K * (K + 1) / 2;
+  for (int idx = tid; idx < npair * K * nq; idx += NTU_CTA) {
+    const int qb = idx % nq, cp = (idx / nq) % K, t = idx / (nq * K);
+    int fp = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((fp + 1) * (fp + 2) / 2 <= t) ++fp;
+    while (fp > 0 && fp * (fp + 1) / 2 > t) --fp;
+    const int f = t - fp * (fp + 1) / 2;
+    const int r = side == 0 ? fp * K + cp : cp * K + fp;
+    const float4* gr = gdf + (size_t)r * ng + f * sf;
+    const int q0 = qb * 4;
+    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+    for (int c = 0; c < K; ++c) {
+      const float4 gv = gr[c * sc];
+      const float4* Fc = sm.Fdf + c * D + q0;
+      df_cmac<false>(acc0, gv, Fc[0]);
+      if (q0 + 1 < D) df_cmac<false>(acc1, gv, Fc[1]);
+      if (q0 + 2 < D) df_cmac<false>(acc2, gv, Fc[2]);
+      if (q0 + 3 < D) df_cmac<false>(acc3, gv, Fc[3]);
+    }
+    float4* out = Tmdf + (size_t)r * nA + f * D + q0;
+    out[0] = acc0;
+    if (q0 + 1 < D) out[1] = acc1;
+    if (q0 + 2 < D) out[2] = acc2;
+    if (q0 + 3 < D) out[3] = acc3;
+  }
+  __syncthreads();
+  // gX[(f1,q1),col] = sum_c conj(F[c][q1]) Tm[f1*sf + c*sc][col], rows >= col.
+  // Row block b = (f1, q block) pairs with the columns col <= its last row;
+  // sm.cumX[b] counts the items of the blocks before b.
+  const int nb = K * nq;
+  for (int idx = tid; idx < sm.cumX[nb]; idx += NTU_CTA) {
+    int lo = 0, hi = nb;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (sm.cumX[mid] <= idx) lo = mid; else hi = mid;
+    }
+    const int col = idx - sm.cumX[lo], qb = lo % nq, f1 = lo / nq;
+    const int q0 = qb * 4, row0 = f1 * D + q0;
+    const int nr = min(4, D - q0);
+    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+    for (int c = 0; c < K; ++c) {
+      const float4 tv = Tmdf[(size_t)(f1 * sf + c * sc) * nA + col];
+      const float4* Fc = sm.Fdf + c * D + q0;
+      df_cmac<true>(acc0, Fc[0], tv);
+      if (nr > 1) df_cmac<true>(acc1, Fc[1], tv);
+      if (nr > 2) df_cmac<true>(acc2, Fc[2], tv);
+      if (nr > 3) df_cmac<true>(acc3, Fc[3], tv);
+    }
+    double2* outc = gX + (size_t)col * nA;
+    const float4 accs[4] = {acc0, acc1, acc2, acc3};
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < nr && row0 + t >= col) {
+        double2 v = df_join(accs[t]);
+        outc[row0 + t] = make_double2(scalbn(v.x, e), scalbn(v.y, e));
+      }
+  }
+  __syncthreads();
+}
+
 // Reduced metric and source for the free side (Fig. 5(b,c)).  side 0: the
 // A step, free index i of (i, j), fixed F = MB; side 1: the B step, free j,
 // F = MA.  gX is written column-major (nA x nA), J into a.jv.
@@ -340,7 +478,16 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
       acc = cfmac(F[c * D + q1], Tm[(size_t)(f1 * sf + c * sc) * nA + col], acc);
     gX[idx] = acc;
   }
-  for (int row = tid; row < nA; row += NTU_CTA) {
+  __syncthreads();
+}
+
+// Source J of the free side: J[(f,q)] = sum_c conj(F[c][q]) (g x0)[f*sf + c*sc].
+__device__ void als_source(AlsShared& sm, const AlsArgs& a, int side, double2* jv,
+                           const double2* gx0) {
+  const int K = a.K, D = a.D, nA = a.nA;
+  const double2* F = side == 0 ? sm.MB : sm.MA;
+  const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
+  for (int row = threadIdx.x; row < nA; row += NTU_CTA) {
     int f1 = row / D, q1 = row % D;
     double2 acc = cz();
     for (int c = 0; c < K; ++c) acc = cfmac(F[c * D + q1], gx0[f1 * sf + c * sc], acc);
@@ -604,6 +751,23 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   e0 = block_sum(e0, sm.red);
   if (tid == 0) sm.eps0 = e0;
   __syncthreads();
+  const float4* gdf = nullptr;
+  int ge = 0;
+  if (a.df) {
+    if (tid == 0) {
+      const int nq = (D + 3) >> 2;
+      int acc = 0;
+      for (int b = 0; b < K * nq; ++b) {
+        sm.cumX[b] = acc;
+        const int q0 = (b % nq) * 4;
+        acc += (b / nq) * D + q0 + min(4, D - q0);     // columns 0 .. last row of block b
+      }
+      sm.cumX[K * nq] = acc;
+    }
+    __syncthreads();
+    ge = als_split_g(sm, g, a.gdf + item * (long long)ng * ng, ng);
+    gdf = a.gdf + item * (long long)ng * ng;
+  }
   // SVDU start (Fig. 2(c,d)).  X0 = U S V^H gives the balanced start
   // (U sqrt(S), conj(V) sqrt(S)) whose first tilt is (U S, conj(V)): with
   // sweeps to run, the start goes straight to the tilted pair.
@@ -611,7 +775,9 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   for (int s = 0; s < a.sweeps; ++s) {
     for (int side = 0; side < 2; ++side) {
       if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
-      als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
+      if (a.df) als_reduced_df(sm, a, gdf, ge, side, reinterpret_cast<float4*>(Tm), gX);
+      else als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
+      als_source(sm, a, side, jv, gx0);
       if (!als_solve_chol(sm, a, side, gX, gC, jv, tau_max)) {
         als_mirror(gX, nA);
         als_solve(sm, a, side, gX, jv, pv, tauv, dv, ev, log);
@@ -691,6 +857,8 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   a.path_counts = c->d_paths;
   a.tauv = W.tauv; a.dv = W.dv; a.ev = W.ev; a.rc = W.rc; a.rs = W.rs; a.rk = W.rk;
   a.rotcap = W.rotcap; a.status = c->d_status;
+  a.df = c->cfg.precision != NTU_FP64;
+  a.gdf = reinterpret_cast<float4*>(W.gscr);
   size_t sm = sizeof(AlsShared);
   cudaFuncSetAttribute(k_als, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_als<<<n, NTU_CTA, sm, c->stream>>>(a);

@@ -271,6 +271,37 @@ def test_als_matches_oracle(D, r, sweeps, kmin):
         assert _rel(MB[i].cpu().numpy(), mb) < 1e-8
 
 
+@pytest.mark.parametrize("D,precision", [(3, 1), (4, 2), (6, 2)])
+def test_als_double_fp32_build_matches_oracle(D, precision):
+    """Mixed contexts build the reduced metric g_A in double-FP32 arithmetic
+    (pairs of FP32 values, about 2^-48 relative) and solve in FP64.  On the
+    same FP64 metric the result stays within 1e-9 of the FP64 oracle, far
+    inside the mixed path's 1e-4 environment budget."""
+    n, r, sweeps = 2, 2, 10
+    Ta, Tb, G = _items(650 + D, n, 2, D)
+    cfg = O.Config(D=D, r=r, sweeps=sweeps, tau_exponents=tuple(range(4, 9)))
+    gs, RAs, RBs, refs = [], [], [], []
+    for i in range(n):
+        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+        g, _ = O.hermitise_repair(O.metric_raw(Ta[i], Tb[i], qa, qb, 2, D))
+        gs.append(g); RAs.append(ra); RBs.append(rb)
+        refs.append(O.als_truncate(g, ra, rb, D, sweeps, cfg.taus))
+    ctx = _ctx(D, r, sweeps=sweeps, precision=precision, max_batch=n, kmin=4, kmax=8)
+    K = D * r
+    MA, MB = _empty((n, K, D)), _empty((n, K, D))
+    info = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    ctx.batch_als_dev(n, _dev(np.stack(gs)), _dev(np.stack(RAs)), _dev(np.stack(RBs)), MA, MB, info)
+    ctx.sync()
+    for i in range(n):
+        ma, mb, eps, delta, eps0, tau = refs[i]
+        inf = info[i].cpu().numpy()
+        assert abs(inf[2] - eps0) < 1e-12 * eps0
+        assert abs(inf[1] - delta) < 1e-10
+        assert inf[3] == tau
+        assert _rel(MA[i].cpu().numpy(), ma) < 1e-9
+        assert _rel(MB[i].cpu().numpy(), mb) < 1e-9
+
+
 @pytest.mark.parametrize("spread,path", [(30.0, "als_cholesky"), (1e7, "als_eigen")])
 def test_als_dense_metric_paths(spread, path):
     """A dense metric g = W diag(lam) W^H (W Haar-random, lam geometric on
