@@ -10,11 +10,14 @@
 // lo = bf16(x - hi), as [hi | lo] halves of its row, and the kernel
 // accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory.
 //
-// Operands are fetched by TMA (128-byte swizzle) through a 3-stage mbarrier
-// pipeline; one thread issues tcgen05.mma (M=128, N=128, K=16 per
-// instruction); the epilogue reads TMEM and writes the result through
-// separable index tables either as complex FP32 or directly as the split
-// BF16 operand of the next GEMM.
+// The kernel is persistent (one CTA per SM walks the 128 x 128 output tiles
+// of all items) and warp-specialised: warp 0 fetches operands by TMA
+// (128-byte swizzle) through a 4-stage mbarrier pipeline, warp 1 issues
+// tcgen05.mma (M=128, N=128, K=16 per instruction) into one of two TMEM
+// accumulators, and warps 2-9 drain the other accumulator: TMEM -> shared
+// staging -> global stores through separable index tables, either as complex
+// FP32 or directly as the split BF16 operand of the next GEMM.  The epilogue
+// of one tile thus overlaps the loads and MMAs of the next.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -28,13 +31,14 @@
 namespace ntu {
 
 namespace {
-constexpr int TBM = 128, TBN = 128, TBK = 64, TSTAGES = 3;
+constexpr int TBM = 128, TBN = 128, TBK = 64, TSTAGES = 4;
 constexpr int TILE_A = TBM * TBK * 2, TILE_B = TBN * TBK * 2;
+constexpr int EPI_WARPS = 8, TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 1ll << 28;
 constexpr int SM_STAGE = TBN + 1;                 // staging pitch (floats)
-constexpr size_t TC_SMEM = (size_t)TSTAGES * (TILE_A + TILE_B) + 1024 + 256;
-static_assert((size_t)TBM * SM_STAGE * 4 <= (size_t)TSTAGES * (TILE_A + TILE_B),
-              "epilogue staging must fit in the pipeline buffers");
+constexpr size_t STAGING = (size_t)TBM * SM_STAGE * 4;
+constexpr size_t TC_SMEM = (size_t)TSTAGES * (TILE_A + TILE_B) + STAGING + 1024 + 256;
+static_assert(TC_SMEM <= 227 * 1024, "shared memory budget");
 }  // namespace
 
 // MODE 0: complex FP32 output at out[rowC[m] + colC[n]].
@@ -43,104 +47,151 @@ static_assert((size_t)TBM * SM_STAGE * 4 <= (size_t)TSTAGES * (TILE_A + TILE_B),
 // MODE 2: split doubled A operand: as MODE 1 but complex row r goes to the
 //         real rows (r/64)*128 + r%64 (Re part) and +64 (Im part).
 template <int MODE>
-__global__ void __launch_bounds__(128) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                 const __grid_constant__ CUtensorMap tmB,
-                                                 TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB,
+                                                          TcArgs a, int items) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
   unsigned char* sB = smem + TSTAGES * TILE_A;
-  uint64_t* full = (uint64_t*)(sB + TSTAGES * TILE_B);
+  float* stage = (float*)(sB + TSTAGES * TILE_B);          // [128][SM_STAGE]
+  uint64_t* full = (uint64_t*)((unsigned char*)stage + STAGING);
   uint64_t* empty = full + TSTAGES;
-  uint64_t* accf = empty + TSTAGES;
-  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  uint64_t* accf = empty + TSTAGES;                        // [2] accumulator ready
+  uint64_t* acce = accf + 2;                               // [2] accumulator drained
+  uint64_t* done = acce + 2;                               // all MMAs retired
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.x * TBN, mt = blockIdx.y, z = blockIdx.z;
+  const int ntN = (a.N + TBN - 1) / TBN;
+  const int per_item = ntN * a.mtiles;
+  const long long total = (long long)per_item * items;
   if (tid == 0) {
     for (int s = 0; s < TSTAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-    tc::mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) { tc::mbar_init(&accf[b], 1); tc::mbar_init(&acce[b], EPI_WARPS); }
+    tc::mbar_init(done, 1);
     tc::fence_barrier_init();
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, TBN);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 2 * TBN);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const int total = 3 * a.kTiles;
-  int issued = 0;                       // TMA stages armed by the producer
-  if (warp == 0 && lane == 0) {
-    for (int it = 0; it < total; ++it) {
-      const int s = it % TSTAGES, u = it / TSTAGES;
-      if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, WAIT_LIMIT)) {
-        raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
-        break;
+  const int steps = 3 * a.kTiles;                          // hi*hi, hi*lo, lo*hi
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer
+      long long g = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int z = (int)(t / per_item), rem = (int)(t % per_item);
+        const int mt = rem / ntN, n0 = (rem % ntN) * TBN;
+        for (int it = 0; it < steps; ++it, ++g) {
+          const int s = (int)(g % TSTAGES);
+          const long long u = g / TSTAGES;
+          if (u > 0 && !tc::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), WAIT_LIMIT)) {
+            raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+            ok = false;
+            break;
+          }
+          const int p = it / a.kTiles, kt = it % a.kTiles;
+          const int xa = (p == 2 ? a.krp : 0) + kt * TBK, xb = (p == 1 ? a.krp : 0) + kt * TBK;
+          tc::mbar_expect_tx(&full[s], TILE_A + TILE_B);
+          tc::tma_load_3d(sA + s * TILE_A, &tmA, &full[s], xa, mt * TBM, z);
+          tc::tma_load_3d(sB + s * TILE_B, &tmB, &full[s], xb, n0, z);
+        }
       }
-      const int p = it / a.kTiles, kt = it % a.kTiles;
-      const int xa = (p == 2 ? a.krp : 0) + kt * TBK, xb = (p == 1 ? a.krp : 0) + kt * TBK;
-      tc::mbar_expect_tx(&full[s], TILE_A + TILE_B);
-      tc::tma_load_3d(sA + s * TILE_A, &tmA, &full[s], xa, mt * TBM, z);
-      tc::tma_load_3d(sB + s * TILE_B, &tmB, &full[s], xb, n0, z);
-      issued = it + 1;
+      // no TMA copy may still be landing in shared memory when the CTA exits
+      for (long long q = g - TSTAGES < 0 ? 0 : g - TSTAGES; q < g; ++q)
+        if (!tc::mbar_wait(&full[q % TSTAGES], (uint32_t)((q / TSTAGES) & 1), WAIT_LIMIT))
+          raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = tc::idesc_bf16_f32(TBM, TBN);
-    for (int it = 0; it < total; ++it) {
-      const int s = it % TSTAGES, u = it / TSTAGES;
-      if (!tc::mbar_wait(&full[s], u & 1, WAIT_LIMIT)) {
-        raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t idesc = tc::idesc_bf16_f32(TBM, TBN);
+      long long g = 0;
+      int i = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+        const int b = i & 1, ub = i >> 1;
+        if (ub > 0 && !tc::mbar_wait(&acce[b], (uint32_t)((ub - 1) & 1), WAIT_LIMIT)) {
+          raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(b * TBN);
+        for (int it = 0; it < steps; ++it, ++g) {
+          const int s = (int)(g % TSTAGES);
+          if (!tc::mbar_wait(&full[s], (uint32_t)((g / TSTAGES) & 1), WAIT_LIMIT)) {
+            raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint64_t ad = tc::sdesc_k128(tc::smem_u32(sA + s * TILE_A));
+          const uint64_t bd = tc::sdesc_k128(tc::smem_u32(sB + s * TILE_B));
+#pragma unroll
+          for (int kk = 0; kk < TBK / 16; ++kk)
+            tc::mma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (it | kk) != 0);
+          tc::mma_commit(&empty[s]);
+        }
+        if (ok) tc::mma_commit(&accf[b]);
+      }
+      // every MMA issued has retired before TMEM is released
+      tc::mma_commit(done);
+      if (!tc::mbar_wait(done, 0, WAIT_LIMIT)) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns
+    // half * 64 .. +63 of the accumulator
+    const int et = tid - 64, quarter = warp & 3, half = (warp - 2) >> 2;
+    const int row = quarter * 32 + lane;
+    const int ethreads = 32 * EPI_WARPS;
+    int i = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int b = i & 1, ub = i >> 1;
+      const bool got = tc::mbar_wait(&accf[b], (uint32_t)(ub & 1), WAIT_LIMIT);
+      if (!tc::bar_and(1, ethreads, got)) {
+        if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
         break;
       }
       tc::fence_after_sync();
-      const uint64_t ad = tc::sdesc_k128(tc::smem_u32(sA + s * TILE_A));
-      const uint64_t bd = tc::sdesc_k128(tc::smem_u32(sB + s * TILE_B));
-#pragma unroll
-      for (int kk = 0; kk < TBK / 16; ++kk)
-        tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (it | kk) != 0);
-      tc::mma_commit(&empty[s]);
-    }
-    tc::mma_commit(accf);
-  }
-  __syncwarp();
-  bool ok = tc::mbar_wait(accf, 0, WAIT_LIMIT);
-  ok = __all_sync(0xffffffffu, ok);
-  if (!ok && lane == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
-  if (warp == 0 && lane == 0 && issued > 0) {
-    // make sure no TMA copy is still landing in shared memory before reuse
-    for (int it = issued - TSTAGES < 0 ? 0 : issued - TSTAGES; it < issued; ++it)
-      if (!tc::mbar_wait(&full[it % TSTAGES], (it / TSTAGES) & 1, WAIT_LIMIT))
-        raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
-  }
-  tc::fence_after_sync();
-  __syncthreads();
-  float* stage = (float*)smem;         // [128][SM_STAGE], reuses the pipeline buffers
-  if (ok) {
-    const int row = warp * 32 + lane;
 #pragma unroll 1
-    for (int c = 0; c < TBN; c += 16) {
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+      for (int c = half * 64; c < half * 64 + 64; c += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TBN + c), v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) stage[row * SM_STAGE + c + i] = v[i];
+        for (int q = 0; q < 16; ++q) stage[row * SM_STAGE + c + q] = v[q];
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[b]);          // accumulator b may be reused
+      tc::bar_sync(1, ethreads);                         // staging complete
+      const int z = (int)(t / per_item), rem = (int)(t % per_item);
+      const int mt = rem / ntN, n0 = (rem % ntN) * TBN;
+      for (int idx = et; idx < 64 * TBN; idx += ethreads) {
+        const int j = idx / TBN, nn = idx % TBN;
+        const int m = mt * 64 + j, n = n0 + nn;
+        if (m >= a.Mc || n >= a.N) continue;
+        const float re = stage[j * SM_STAGE + nn], im = stage[(64 + j) * SM_STAGE + nn];
+        if (MODE == 0) {
+          float2* o = (float2*)a.out + (long long)z * a.sOut;
+          o[(long long)a.rowC[m] + a.colC[n]] = make_float2(re, im);
+        } else {
+          __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
+          store_split(o, (long long)a.rowC[m] + a.colC[n], (long long)a.rowK[m] + a.colK[n],
+                      a.pitch, a.krp_out, re, im, MODE == 2);
+        }
+      }
+      tc::bar_sync(1, ethreads);                         // staging free again
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, TBN);
-  if (!ok) return;
-  for (int idx = tid; idx < 64 * TBN; idx += 128) {
-    const int j = idx / TBN, nn = idx % TBN;
-    const int m = mt * 64 + j, n = n0 + nn;
-    if (m >= a.Mc || n >= a.N) continue;
-    const float re = stage[j * SM_STAGE + nn], im = stage[(64 + j) * SM_STAGE + nn];
-    if (MODE == 0) {
-      float2* o = (float2*)a.out + (long long)z * a.sOut;
-      o[(long long)a.rowC[m] + a.colC[n]] = make_float2(re, im);
-    } else {
-      __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
-      store_split(o, (long long)a.rowC[m] + a.colC[n], (long long)a.rowK[m] + a.colK[n],
-                  a.pitch, a.krp_out, re, im, MODE == 2);
-    }
-  }
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * TBN);
 }
 
 // --------------------------------------------------------------- host side
@@ -180,17 +231,27 @@ cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out) {
   a.colK = op.colK >= 0 ? t + op.colK : nullptr;
   a.out = out;
   a.err = c->d_status;
-  dim3 grid((a.N + TBN - 1) / TBN, op.mtiles, n);
+  a.mtiles = op.mtiles;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const long long tiles = (long long)((a.N + TBN - 1) / TBN) * op.mtiles * n;
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  if (grid <= 0) return cudaSuccess;
   static bool attr[3] = {false, false, false};
   if (op.mode == 0) {
     if (!attr[0]) { cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[0] = true; }
-    k_tc_gemm<0><<<grid, 128, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a);
+    k_tc_gemm<0><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   } else if (op.mode == 1) {
     if (!attr[1]) { cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[1] = true; }
-    k_tc_gemm<1><<<grid, 128, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a);
+    k_tc_gemm<1><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   } else {
     if (!attr[2]) { cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[2] = true; }
-    k_tc_gemm<2><<<grid, 128, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a);
+    k_tc_gemm<2><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   }
   return after_launch(c, "k_tc_gemm");
 }

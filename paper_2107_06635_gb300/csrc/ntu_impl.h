@@ -32,6 +32,7 @@ struct TcArgs {
   int kTiles;            // 64-wide K tiles per split pass
   int krp;               // padded real K of one half ([hi | lo] rows are 2 krp wide)
   int Mc, N;             // valid complex rows, valid columns
+  int mtiles;            // 128-row tiles of the doubled A operand
   const int *rowC, *colC, *rowK, *colK;
   void* out;
   long long sOut;        // per-item stride of the output (elements)
