@@ -31,14 +31,21 @@
 namespace ntu {
 
 namespace {
-constexpr int TBM = 128, TBN = 128, TBK = 64, TSTAGES = 4;
+constexpr int TBM = 128, TBN = 128, TBK = 64;
 constexpr int TILE_A = TBM * TBK * 2, TILE_B = TBN * TBK * 2;
 constexpr int EPI_WARPS = 8, TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 1ll << 28;
 constexpr int SM_STAGE = TBN + 1;                 // staging pitch (floats)
-constexpr size_t STAGING = (size_t)TBM * SM_STAGE * 4;
-constexpr size_t TC_SMEM = (size_t)TSTAGES * (TILE_A + TILE_B) + STAGING + 1024 + 256;
-static_assert(TC_SMEM <= 227 * 1024, "shared memory budget");
+// The split-BF16 outputs (modes 1, 2) are written through a shared staging
+// tile so that the 2-byte stores run along output rows; the FP32 output of
+// the long-K join (mode 0) is written straight from registers and spends
+// the space on two more pipeline stages instead.
+template <int MODE> struct TcCfg {
+  static constexpr int STAGES = MODE == 0 ? 6 : 4;
+  static constexpr size_t STAGING = MODE == 0 ? 0 : (size_t)TBM * SM_STAGE * 4;
+  static constexpr size_t SMEM = (size_t)STAGES * (TILE_A + TILE_B) + STAGING + 1024 + 256;
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+};
 }  // namespace
 
 // MODE 0: complex FP32 output at out[rowC[m] + colC[n]].
@@ -50,12 +57,13 @@ template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB,
                                                           TcArgs a, int items) {
+  constexpr int TSTAGES = TcCfg<MODE>::STAGES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
   unsigned char* sB = smem + TSTAGES * TILE_A;
-  float* stage = (float*)(sB + TSTAGES * TILE_B);          // [128][SM_STAGE]
-  uint64_t* full = (uint64_t*)((unsigned char*)stage + STAGING);
+  float* stage = (float*)(sB + TSTAGES * TILE_B);          // [128][SM_STAGE] (modes 1, 2)
+  uint64_t* full = (uint64_t*)((unsigned char*)stage + TcCfg<MODE>::STAGING);
   uint64_t* empty = full + TSTAGES;
   uint64_t* accf = empty + TSTAGES;                        // [2] accumulator ready
   uint64_t* acce = accf + 2;                               // [2] accumulator drained
@@ -76,7 +84,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const int steps = 3 * a.kTiles;                          // hi*hi, hi*lo, lo*hi
+  // Per 64-wide K tile two stages: the hi halves of A and B, then the lo
+  // halves; the three products hi*hi, hi*lo, lo*hi are issued once both
+  // have landed, so every operand tile is fetched once.
+  const int steps = 2 * a.kTiles;
   if (warp == 0) {
     if (lane == 0) {
       // ---- producer
@@ -93,11 +104,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             ok = false;
             break;
           }
-          const int p = it / a.kTiles, kt = it % a.kTiles;
-          const int xa = (p == 2 ? a.krp : 0) + kt * TBK, xb = (p == 1 ? a.krp : 0) + kt * TBK;
+          const int x = (it & 1) * a.krp + (it >> 1) * TBK;
           tc::mbar_expect_tx(&full[s], TILE_A + TILE_B);
-          tc::tma_load_3d(sA + s * TILE_A, &tmA, &full[s], xa, mt * TBM, z);
-          tc::tma_load_3d(sB + s * TILE_B, &tmB, &full[s], xb, n0, z);
+          tc::tma_load_3d(sA + s * TILE_A, &tmA, &full[s], x, mt * TBM, z);
+          tc::tma_load_3d(sB + s * TILE_B, &tmB, &full[s], x, n0, z);
         }
       }
       // no TMA copy may still be landing in shared memory when the CTA exits
@@ -121,20 +131,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         }
         tc::fence_after_sync();
         const uint32_t acc = tmem + (uint32_t)(b * TBN);
-        for (int it = 0; it < steps; ++it, ++g) {
-          const int s = (int)(g % TSTAGES);
-          if (!tc::mbar_wait(&full[s], (uint32_t)((g / TSTAGES) & 1), WAIT_LIMIT)) {
+        for (int it = 0; it < steps; it += 2, g += 2) {
+          const int sh = (int)(g % TSTAGES), sl = (int)((g + 1) % TSTAGES);
+          if (!tc::mbar_wait(&full[sh], (uint32_t)((g / TSTAGES) & 1), WAIT_LIMIT) ||
+              !tc::mbar_wait(&full[sl], (uint32_t)(((g + 1) / TSTAGES) & 1), WAIT_LIMIT)) {
             raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          const uint64_t ad = tc::sdesc_k128(tc::smem_u32(sA + s * TILE_A));
-          const uint64_t bd = tc::sdesc_k128(tc::smem_u32(sB + s * TILE_B));
+          const uint64_t ah = tc::sdesc_k128(tc::smem_u32(sA + sh * TILE_A));
+          const uint64_t bh = tc::sdesc_k128(tc::smem_u32(sB + sh * TILE_B));
+          const uint64_t al = tc::sdesc_k128(tc::smem_u32(sA + sl * TILE_A));
+          const uint64_t bl = tc::sdesc_k128(tc::smem_u32(sB + sl * TILE_B));
 #pragma unroll
-          for (int kk = 0; kk < TBK / 16; ++kk)
-            tc::mma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (it | kk) != 0);
-          tc::mma_commit(&empty[s]);
+          for (int kk = 0; kk < TBK / 16; ++kk) {
+            tc::mma_bf16(acc, ah + 2 * kk, bh + 2 * kk, idesc, (it | kk) != 0);
+            tc::mma_bf16(acc, ah + 2 * kk, bl + 2 * kk, idesc, 1);
+            tc::mma_bf16(acc, al + 2 * kk, bh + 2 * kk, idesc, 1);
+          }
+          tc::mma_commit(&empty[sh]);
+          tc::mma_commit(&empty[sl]);
         }
         if (ok) tc::mma_commit(&accf[b]);
       }
@@ -158,6 +175,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         break;
       }
       tc::fence_after_sync();
+      const int z = (int)(t / per_item), rem = (int)(t % per_item);
+      const int mt = rem / ntN, n0 = (rem % ntN) * TBN;
+      if (MODE == 0) {
+        // lane row < 64 holds Re, row >= 64 Im of complex row mt*64 + row % 64
+        const int m = mt * 64 + (row & 63);
+        float* o = (float*)a.out + 2 * (long long)z * a.sOut + (row >> 6);
+#pragma unroll 1
+        for (int c = half * 64; c < half * 64 + 64; c += 16) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TBN + c), v);
+          if (m < a.Mc) {
+            const long long rb = a.rowC[m];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (n0 + c + q < a.N) o[2 * (rb + a.colC[n0 + c + q])] = v[q];
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acce[b]);
+        continue;
+      }
 #pragma unroll 1
       for (int c = half * 64; c < half * 64 + 64; c += 16) {
         float v[16];
@@ -169,21 +208,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acce[b]);          // accumulator b may be reused
       tc::bar_sync(1, ethreads);                         // staging complete
-      const int z = (int)(t / per_item), rem = (int)(t % per_item);
-      const int mt = rem / ntN, n0 = (rem % ntN) * TBN;
       for (int idx = et; idx < 64 * TBN; idx += ethreads) {
         const int j = idx / TBN, nn = idx % TBN;
         const int m = mt * 64 + j, n = n0 + nn;
         if (m >= a.Mc || n >= a.N) continue;
         const float re = stage[j * SM_STAGE + nn], im = stage[(64 + j) * SM_STAGE + nn];
-        if (MODE == 0) {
-          float2* o = (float2*)a.out + (long long)z * a.sOut;
-          o[(long long)a.rowC[m] + a.colC[n]] = make_float2(re, im);
-        } else {
-          __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
-          store_split(o, (long long)a.rowC[m] + a.colC[n], (long long)a.rowK[m] + a.colK[n],
-                      a.pitch, a.krp_out, re, im, MODE == 2);
-        }
+        __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
+        store_split(o, (long long)a.rowC[m] + a.colC[n], (long long)a.rowK[m] + a.colK[n],
+                    a.pitch, a.krp_out, re, im, MODE == 2);
       }
       tc::bar_sync(1, ethreads);                         // staging free again
     }
@@ -244,14 +276,14 @@ cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out) {
   if (grid <= 0) return cudaSuccess;
   static bool attr[3] = {false, false, false};
   if (op.mode == 0) {
-    if (!attr[0]) { cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[0] = true; }
-    k_tc_gemm<0><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
+    if (!attr[0]) { cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<0>::SMEM); attr[0] = true; }
+    k_tc_gemm<0><<<grid, TC_THREADS, TcCfg<0>::SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   } else if (op.mode == 1) {
-    if (!attr[1]) { cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[1] = true; }
-    k_tc_gemm<1><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
+    if (!attr[1]) { cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<1>::SMEM); attr[1] = true; }
+    k_tc_gemm<1><<<grid, TC_THREADS, TcCfg<1>::SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   } else {
-    if (!attr[2]) { cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); attr[2] = true; }
-    k_tc_gemm<2><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
+    if (!attr[2]) { cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<2>::SMEM); attr[2] = true; }
+    k_tc_gemm<2><<<grid, TC_THREADS, TcCfg<2>::SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   }
   return after_launch(c, "k_tc_gemm");
 }
