@@ -112,6 +112,8 @@ void carve(ntu_ctx* c, Carver& cv) {
     W.T2s = cv.take<char>(n * bT);
     W.HLd = cv.take<char>(n * (size_t)P.rowsHL * 2 * P.krpJ * 2);
     W.HRs = cv.take<char>(n * (size_t)P.rowsHR * 2 * P.krpJ * 2);
+    W.Ys = cv.take<char>(n * (size_t)P.rowsY * 2 * P.krpY * 2);
+    W.Qs = cv.take<char>(n * (size_t)P.rowsQ * 2 * P.krpY * 2);
   }
   W.graw = cv.take<double2>(n * P.szG);
   W.g = cv.take<double2>(n * P.szG);

@@ -320,6 +320,28 @@ int plan_build(ntu_ctx* c) {
     P.t1s.rowK = T.add({{D, D}, {D, 0}, {K, 0}});
     P.t1s.colK = T.add({{D, 0}, {K, 0}, {D, 1}});
     P.t1s.mode = 1; P.t1s.sC = P.rowsT * pE; P.t1s.pitch = pE; P.t1s.krp_out = (int)P.krpE;
+    // tcgen05 t1: Y as the doubled A operand (complex row (u,n,k), complex
+    // column (p,e')) written by the y product, conj(Q) as the B operand (row
+    // (n',k',u'), column (p,e')); the output tables are those of t1s
+    P.krpY = up(2LL * dp * D, 64);
+    P.rowsY = 128 * ((D2K + 63) / 64);
+    P.rowsQ = up(D2K, 128);
+    const int pY = (int)(2 * P.krpY);
+    P.y2 = P.y;
+    P.y2.rowC = T.add({{dp, 0}, {D, DK}, {D, K}, {K, 1}});
+    P.y2.colC = T.add({{D, 0}});
+    P.y2.rowK = T.add({{dp, D}, {D, 0}, {D, 0}, {K, 0}});
+    P.y2.colK = T.add({{D, 1}});
+    P.y2.mode = 2; P.y2.sC = P.rowsY * pY; P.y2.pitch = pY; P.y2.krp_out = (int)P.krpY;
+    TcOp t1;
+    memset(&t1, 0, sizeof(t1));
+    t1.rowC = P.t1s.rowC; t1.colC = P.t1s.colC; t1.rowK = P.t1s.rowK; t1.colK = P.t1s.colK;
+    t1.mode = 1;
+    t1.mtiles = (int)(P.rowsY / 128);
+    t1.args.kTiles = (int)(P.krpY / 64); t1.args.krp = (int)P.krpY;
+    t1.args.Mc = (int)D2K; t1.args.N = (int)D2K;
+    t1.args.pitch = pE; t1.args.krp_out = (int)P.krpE; t1.args.sOut = P.rowsT * pE;
+    P.tc_t1 = t1;
     // t2: C[(ht,ht'),(k,k',n,n')] -> B operand of h: row (k,k',ht,ht'), column (n,n')
     TcOp t2;
     memset(&t2, 0, sizeof(t2));
@@ -439,6 +461,37 @@ static cudaError_t env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, 
 
 // Tensor maps of the split operands (the work space is fixed at init, so
 // the maps are encoded once).
+// conj(Q) as the split B operand of tc_t1: Q[p,e,u,n,k] goes to row
+// (n*K + k)*D + u, complex column p*D + e.
+__global__ void k_q_split(long long total, int D, int K, const float2* __restrict__ Q,
+                          __nv_bfloat16* __restrict__ Qs, long long szQ, long long sOut,
+                          int pitch, int krp) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long item = i / szQ, j = i % szQ;
+    const int k = (int)(j % K);
+    long long r = j / K;
+    const int n = (int)(r % D); r /= D;
+    const int u = (int)(r % D); r /= D;
+    const int e = (int)(r % D);
+    const int p = (int)(r / D);
+    const float2 v = Q[i];
+    store_split(Qs + item * sOut, ((long long)n * K + k) * D + u, (long long)p * D + e, pitch,
+                krp, v.x, -v.y, 0);
+  }
+}
+
+cudaError_t launch_q_split(ntu_ctx* c, int n, const float2* Q, void* Qs) {
+  const Plan& P = c->plan;
+  const long long total = (long long)n * P.szQ;
+  if (total == 0) return cudaSuccess;
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  k_q_split<<<blocks, 256, 0, c->stream>>>(total, P.D, P.K, Q, (__nv_bfloat16*)Qs, P.szQ,
+                                           P.rowsQ * 2 * P.krpY, (int)(2 * P.krpY),
+                                           (int)P.krpY);
+  return after_launch(c, "k_q_split");
+}
+
 int tc_plan_maps(ntu_ctx* c) {
   Plan& P = c->plan;
   Work& W = c->w;
@@ -447,6 +500,8 @@ int tc_plan_maps(ntu_ctx* c) {
   auto mk = [&](CUtensorMap* m, void* base, long long cols, long long rows) {
     if (st == NTU_OK) st = tc_make_map(m, base, cols, rows, cap);
   };
+  mk(&P.tc_t1.mapA, W.Ys, 2 * P.krpY, P.rowsY);
+  mk(&P.tc_t1.mapB, W.Qs, 2 * P.krpY, P.rowsQ);
   mk(&P.tc_t2L.mapA, W.ETLd, pE, P.rowsE);
   mk(&P.tc_t2R.mapA, W.ETRd, pE, P.rowsE);
   mk(&P.tc_t2L.mapB, W.T1s, pE, P.rowsT);
@@ -474,12 +529,14 @@ static cudaError_t env_chain_bf16x3(ntu_ctx* c, int n, const void* Ta, const voi
   RG(run_gemm<float2>(c, P.e2BL, n, Tb, Tb, W.EBLd));
   RG(run_gemm<float2>(c, P.e2TR, n, Ta, Ta, W.ETRd));
   RG(run_gemm<float2>(c, P.e2BR, n, Ta, Ta, W.EBRd));
-  RG(run_gemm<float2>(c, P.y, n, QA, W.EL, W.Y));
-  RG(run_gemm<float2>(c, P.t1s, n, W.Y, QA, W.T1s));
+  RG(run_gemm<float2>(c, P.y2, n, QA, W.EL, W.Ys));
+  RG(launch_q_split(c, n, (const float2*)QA, W.Qs));
+  RG(launch_tc_gemm(c, P.tc_t1, n, W.T1s));
   RG(launch_tc_gemm(c, P.tc_t2L, n, W.T2s));
   RG(launch_tc_gemm(c, P.tc_hL, n, W.HLd));
-  RG(run_gemm<float2>(c, P.y, n, QB, W.ER, W.Y));
-  RG(run_gemm<float2>(c, P.t1s, n, W.Y, QB, W.T1s));
+  RG(run_gemm<float2>(c, P.y2, n, QB, W.ER, W.Ys));
+  RG(launch_q_split(c, n, (const float2*)QB, W.Qs));
+  RG(launch_tc_gemm(c, P.tc_t1, n, W.T1s));
   RG(launch_tc_gemm(c, P.tc_t2R, n, W.T2s));
   RG(launch_tc_gemm(c, P.tc_hR, n, W.HRs));
   RG(launch_tc_gemm(c, P.tc_join, n, graw));

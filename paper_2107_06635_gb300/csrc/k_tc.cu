@@ -34,6 +34,7 @@ namespace {
 constexpr int TBM = 128, TBN = 128, TBK = 64;
 constexpr int TILE_A = TBM * TBK * 2, TILE_B = TBN * TBK * 2;
 constexpr int EPI_WARPS = 8, TC_THREADS = 64 + 32 * EPI_WARPS;
+static_assert((32 * EPI_WARPS) % TBN == 0, "epilogue threads per output column");
 constexpr long long WAIT_LIMIT = 1ll << 28;
 constexpr int SM_STAGE = TBN + 1;                 // staging pitch (floats)
 // The split-BF16 outputs (modes 1, 2) are written through a shared staging
@@ -43,7 +44,7 @@ constexpr int SM_STAGE = TBN + 1;                 // staging pitch (floats)
 template <int MODE> struct TcCfg {
   static constexpr int STAGES = MODE == 0 ? 6 : 4;
   static constexpr size_t STAGING = MODE == 0 ? 0 : (size_t)TBM * SM_STAGE * 4;
-  static constexpr size_t SMEM = (size_t)STAGES * (TILE_A + TILE_B) + STAGING + 1024 + 256;
+  static constexpr size_t SMEM = (size_t)STAGES * (TILE_A + TILE_B) + STAGING + 1024 + 1024;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 }  // namespace
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
   uint64_t* acce = accf + 2;                               // [2] accumulator drained
   uint64_t* done = acce + 2;                               // all MMAs retired
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* srow = (int*)(tmem_slot + 4);                      // [2][64] row offsets of a tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntN = (a.N + TBN - 1) / TBN;
   const int per_item = ntN * a.mtiles;
@@ -207,15 +209,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acce[b]);          // accumulator b may be reused
+      if (et < 64) {
+        const int m = mt * 64 + et;
+        srow[et] = m < a.Mc ? a.rowC[m] : 0;
+        srow[64 + et] = m < a.Mc ? a.rowK[m] : 0;
+      }
       tc::bar_sync(1, ethreads);                         // staging complete
-      for (int idx = et; idx < 64 * TBN; idx += ethreads) {
-        const int j = idx / TBN, nn = idx % TBN;
-        const int m = mt * 64 + j, n = n0 + nn;
-        if (m >= a.Mc || n >= a.N) continue;
-        const float re = stage[j * SM_STAGE + nn], im = stage[(64 + j) * SM_STAGE + nn];
-        __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
-        store_split(o, (long long)a.rowC[m] + a.colC[n], (long long)a.rowK[m] + a.colK[n],
-                    a.pitch, a.krp_out, re, im, MODE == 2);
+      {
+        // each thread keeps one output column; rows advance by ethreads / TBN
+        const int nn = et % TBN, n = n0 + nn;
+        if (n < a.N) {
+          const long long cC = a.colC[n], cK = a.colK[n];
+          __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
+          for (int j = et / TBN; j < 64 && mt * 64 + j < a.Mc; j += ethreads / TBN) {
+            const float re = stage[j * SM_STAGE + nn], im = stage[(64 + j) * SM_STAGE + nn];
+            store_split(o, srow[j] + cC, srow[64 + j] + cK, a.pitch, a.krp_out, re, im,
+                        MODE == 2);
+          }
+        }
       }
       tc::bar_sync(1, ethreads);                         // staging free again
     }

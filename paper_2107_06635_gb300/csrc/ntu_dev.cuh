@@ -67,19 +67,23 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 __device__ __forceinline__ void store_split(__nv_bfloat16* base, long long r, long long kc,
                                             int pitch, int krp, float re, float im,
                                             int doubled) {
+  // pitch and krp are even, so every (re, im) pair is a 4-byte aligned word
   __nv_bfloat16 h0, l0, h1, l1;
   split_bf16(re, h0, l0);
   split_bf16(im, h1, l1);
   if (!doubled) {
-    __nv_bfloat16* p = base + r * pitch + 2 * kc;
-    p[0] = h0; p[1] = h1; p[krp] = l0; p[krp + 1] = l1;
+    __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(base + r * pitch + 2 * kc);
+    p[0] = __halves2bfloat162(h0, h1);
+    p[krp / 2] = __halves2bfloat162(l0, l1);
   } else {
-    __nv_bfloat16 hm, lm;
-    split_bf16(-im, hm, lm);
-    __nv_bfloat16* pr = base + ((r / 64) * 128 + (r % 64)) * pitch + 2 * kc;
-    __nv_bfloat16* pi = pr + 64LL * pitch;
-    pr[0] = h0; pr[1] = hm; pr[krp] = l0; pr[krp + 1] = lm;
-    pi[0] = h1; pi[1] = h0; pi[krp] = l1; pi[krp + 1] = l0;
+    // -im splits into (-hi, -lo) exactly
+    __nv_bfloat162* pr =
+        reinterpret_cast<__nv_bfloat162*>(base + ((r / 64) * 128 + (r % 64)) * pitch + 2 * kc);
+    __nv_bfloat162* pi = pr + 32LL * pitch;
+    pr[0] = __halves2bfloat162(h0, __hneg(h1));
+    pr[krp / 2] = __halves2bfloat162(l0, __hneg(l1));
+    pi[0] = __halves2bfloat162(h1, h0);
+    pi[krp / 2] = __halves2bfloat162(l1, l0);
   }
 }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
