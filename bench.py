@@ -16,6 +16,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -34,6 +35,11 @@ from paper_2107_06635_gb300 import inputs as I  # noqa: E402
 METRIC = "NTU bond updates/s"
 FP64_PEAK = 1.25e12          # nominal GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
 FP32_SIMT_PEAK = 152 * 128 * 2 * 2.07e9   # nominal FP32 FMA pipes
+# The mixed contexts build the ALS reduced metric in double-FP32 arithmetic:
+# one complex multiply-add (8 flops of the FP64 algorithm) costs 48 FP32
+# lane operations, so that part of the work peaks at the FP32 lane rate x 8/48.
+DF_OPS_PER_CMAC = 48
+DF_PEAK = 152 * 128 * 2.07e9 * 8 / DF_OPS_PER_CMAC
 
 
 def measured_peaks():
@@ -52,17 +58,53 @@ def env_flops(D, r, d_p=2):
     return 8.0 * mac
 
 
-def als_flops(D, r, sweeps):
-    """Algorithmic real FP64 flops of the ALS stage of one bond update (Fig. 5):
-    per half sweep the Hermitian reduced metric g_A, K^4 D + K^3 D^2 complex
-    multiply-adds of which the lower triangle needs half, and the residual
-    J - g_A m of the solve (one n_A x n_A product, n_A = K D); plus g x0 and
-    the final error (8 n_g^2 each).  The K x D SVDs of the tilts are not
-    counted."""
+def als_flops_parts(D, r, sweeps):
+    """Algorithmic real flops of the ALS stage of one bond update (Fig. 5),
+    as (reduced-metric builds, rest): per half sweep the Hermitian reduced
+    metric g_A, K^4 D + K^3 D^2 complex multiply-adds of which the lower
+    triangle needs half, and the residual J - g_A m of the solve (one
+    n_A x n_A product, n_A = K D); plus g x0 and the final error (8 n_g^2
+    each).  The K x D SVDs of the tilts are not counted."""
     K = D * r
     nA, ng = K * D, K * K
-    half = 8.0 * (K ** 4 * D + K ** 3 * D * D) / 2 + 8.0 * nA * nA
-    return sweeps * 2 * half + 2 * 8.0 * ng * ng
+    build = sweeps * 2 * 8.0 * (K ** 4 * D + K ** 3 * D * D) / 2
+    rest = sweeps * 2 * 8.0 * nA * nA + 2 * 8.0 * ng * ng
+    return build, rest
+
+
+def als_flops(D, r, sweeps):
+    return sum(als_flops_parts(D, r, sweeps))
+
+
+def als_peak(precision, D, r, sweeps):
+    """Peak of k_als for its own mix of pipes: FP64 throughout on the FP64
+    context; on the mixed contexts the builds at DF_PEAK and the rest at the
+    FP64 peak, i.e. the time a kernel needs that runs every part at its
+    pipe's peak, converted back to a rate."""
+    if precision == "fp64":
+        return FP64_PEAK, "nominal FP64 (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)"
+    build, rest = als_flops_parts(D, r, sweeps)
+    t = build / DF_PEAK + rest / FP64_PEAK
+    return (build + rest) / t, ("pipe-weighted: reduced-metric builds at the double-FP32 rate "
+                                "(FP32 lanes 152x128x2.07 GHz x 8/48), the rest at nominal FP64")
+
+
+def als_traffic(precision, D, r, sweeps, items):
+    """DRAM bytes of one k_als launch from the ncu capture recorded in
+    profiles/traffic.json, scaled by items (every item's data is private);
+    None when the kernel sources changed since the capture or the workload
+    differs."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_als"]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if (h.hexdigest() != rec["sources_sha256"] or rec["precision"] != precision
+                or (rec["D"], rec["r"], rec["sweeps"]) != (D, r, sweeps)):
+            return None
+        return rec["dram_bytes_per_item"] * items
+    except Exception:
+        return None
 
 
 def env_roof(precision, achieved, peaks):
@@ -321,6 +363,7 @@ def run_ours(args):
 
     als_ms = float(st_mixed[3])
     achieved = B * als_flops(D, r, S) / (als_ms / 1e3)
+    als_pk, als_pk_src = als_peak(args.precision, D, r, S)
     env_achieved = B * env_flops(D, r) / (float(st_mixed[1]) / 1e3)
     cpu = None
     if not args.no_cpu_baseline:
@@ -341,9 +384,10 @@ def run_ours(args):
             "fp32": "mixed: FP32 environment, FP64 solvers",
             "fp64": "FP64 throughout"}[args.precision]),
         "roofline": {"kernel": "k_als (ALS truncation, Fig. 5)", "bound": "alu",
-                     "achieved": achieved / 1e12, "peak": FP64_PEAK / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK, "traffic": None,
-                     "peak_source": "nominal FP64 derived from unit counts and clocks"},
+                     "achieved": achieved / 1e12, "peak": als_pk / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / als_pk,
+                     "traffic": als_traffic(args.precision, D, r, S, B),
+                     "peak_source": als_pk_src},
         "env_roofline": env_roof(args.precision, env_achieved, peaks),
         "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
                              [round(float(x), 3) for x in st_mixed])),
