@@ -180,15 +180,17 @@ int ntu_set_profiling(ntu_ctx* ctx, int on);
 int ntu_stage_times(ntu_ctx* ctx, double* ms_out);
 
 /* Which solver path the device took, counted since the previous call (then
- * reset), into counts[6]: counts[0] ALS solves whose tolerance selection
+ * reset), into counts[8]: counts[0] ALS solves whose tolerance selection
  * (Eq. 4) was decided by Gershgorin discs (every candidate tolerance keeps
  * every eigenpair of g_A) and solved by conjugate gradients, counts[1] ALS
  * solves decided by a shifted Cholesky factorisation and solved by
  * iterative refinement, counts[2] ALS solves through the eigendecomposition
  * and the full selection, counts[3] metrics certified positive definite by
  * Gershgorin discs, counts[4] by Cholesky, counts[5] metrics repaired
- * through the eigendecomposition (Sec. II).  Synchronises the context's
- * stream. */
+ * through the eigendecomposition (Sec. II), counts[6] QRs of gated matrices
+ * (Fig. 2(b)) by double-FP32 CholeskyQR2 (mixed contexts), counts[7] by
+ * Householder (FP64 contexts, and matrices too ill-conditioned for
+ * CholeskyQR2).  Synchronises the context's stream. */
 int ntu_solver_paths(ntu_ctx* ctx, int* counts);
 
 /* ---- a stage for callers that cannot allocate device memory ----------- */

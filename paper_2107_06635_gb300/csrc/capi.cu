@@ -115,6 +115,7 @@ void carve(ntu_ctx* c, Carver& cv) {
     W.Ys = cv.take<char>(n * (size_t)P.rowsY * 2 * P.krpY * 2);
     W.Qs = cv.take<char>(n * (size_t)P.rowsQ * 2 * P.krpY * 2);
   }
+  W.qrflag = cv.take<int>(n * 2);
   W.graw = cv.take<double2>(n * P.szG);
   W.g = cv.take<double2>(n * P.szG);
   W.gscr = cv.take<double2>(n * P.szG);
@@ -278,8 +279,8 @@ extern "C" int ntu_last_launch_count(const ntu_ctx* c) { return c ? c->launches 
 extern "C" int ntu_solver_paths(ntu_ctx* c, int* counts) {
   if (!c || !counts) return fail(c, NTU_EINVAL, "ntu_solver_paths: NULL argument");
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");
-  CK(cudaMemcpy(counts, c->d_paths, 6 * sizeof(int), cudaMemcpyDeviceToHost), "read counters");
-  CK(cudaMemset(c->d_paths, 0, 6 * sizeof(int)), "reset counters");
+  CK(cudaMemcpy(counts, c->d_paths, 8 * sizeof(int), cudaMemcpyDeviceToHost), "read counters");
+  CK(cudaMemset(c->d_paths, 0, 8 * sizeof(int)), "reset counters");
   return NTU_OK;
 }
 

@@ -85,18 +85,160 @@ __global__ void __launch_bounds__(NTU_CTA) k_gated(int d, int danc, int D, int r
   }
 }
 
+// ------------------------------------------- CholeskyQR2, double-FP32
+// Thin QR of the column-major m x K gated matrix for the mixed contexts
+// (Fig. 2(b)): G1 = M^H M = L1 L1^H, Q1 = M L1^{-H}; G2 = Q1^H Q1 = L2 L2^H,
+// Q = Q1 L2^{-H}, R = L2^H L1^H.  Both Cholesky factors have a real positive
+// diagonal, so R has one too and (Q, R) is the unique QR with that
+// convention.  The m-long products (Gram matrices and Q) run in double-FP32
+// arithmetic (FP32 issues at 64x the FP64 rate), the K x K factorisations and
+// inverses in FP64.  The second pass restores orthogonality to working
+// precision when kappa(M)^2 * 2^-48 << 1; the kernel flags the matrix for the
+// Householder kernel instead when a factorisation fails or when
+// min/max diag(L1) <= 1e-5.
+struct QrDfSmem {
+  double2 G[32 * 32];      // Gram matrix, then its Cholesky factor (column-major)
+  double2 R1[32 * 32];     // L1^H (row-major, upper)
+  double2 Ri[32 * 32];     // an upper-triangular inverse (row-major, FP64)
+  float4 Rid[32 * 32];     // the same in double-FP32
+  double red[2 * NTU_WARPS];
+  int flag;
+};
+
+// G = X^H X (lower triangle, column-major, leading dimension K) from the
+// column-major double-FP32 X (m x K); one warp per entry.
+__device__ void qrdf_gram(const float4* __restrict__ X, int m, int K, double2* G) {
+  const int wid = threadIdx.x >> 5, lid = threadIdx.x & 31;
+  const int npair = K * (K + 1) / 2;
+  for (int t = wid; t < npair; t += NTU_WARPS) {
+    int c = 0, rem = t;                 // pair t -> (r >= c)
+    while (rem >= K - c) { rem -= K - c; ++c; }
+    const int r = c + rem;
+    const float4* xr = X + (size_t)r * m;
+    const float4* xc = X + (size_t)c * m;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = lid; i < m; i += 32) df_cmac<true>(acc, xr[i], xc[i]);
+    acc = df_warp_sum(acc);
+    if (lid == 0) G[(size_t)c * K + r] = df_join(acc);
+  }
+  __syncthreads();
+}
+
+// From the Cholesky factor L (column-major lower) of G: U = L^H into Ru
+// (row-major), its inverse into Ri (FP64) and Rid (double-FP32).
+__device__ void qrdf_factor_inverse(const double2* L, int K, double2* Ru, double2* Ri,
+                                    float4* Rid) {
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < K * K; idx += NTU_CTA) {
+    const int i = idx / K, j = idx % K;
+    Ru[idx] = j >= i ? cconj(L[(size_t)i * K + j]) : cz();
+  }
+  __syncthreads();
+  // column j of the inverse of the upper-triangular Ru, by back substitution
+  for (int j = tid; j < K; j += NTU_CTA) {
+    for (int i = K - 1; i >= 0; --i) {
+      double2 v = cz();
+      if (i <= j) {
+        v = i == j ? make_double2(1.0, 0.0) : cz();
+        for (int l = i + 1; l <= j; ++l) v = cfms(Ru[i * K + l], Ri[l * K + j], v);
+        v = cscale(v, 1.0 / Ru[i * K + i].x);
+      }
+      Ri[i * K + j] = v;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < K * K; idx += NTU_CTA) Rid[idx] = df_split(Ri[idx]);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NTU_CTA) k_qr_df(int m, int K, const double2* __restrict__ Mg,
+                                                   float4* __restrict__ Xg,
+                                                   double2* __restrict__ QA, double2* __restrict__ RA,
+                                                   double2* __restrict__ QB, double2* __restrict__ RB,
+                                                   int* __restrict__ fallback, int* paths) {
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  QrDfSmem& S = *reinterpret_cast<QrDfSmem*>(qr_smem);
+  const int item = blockIdx.x, side = blockIdx.y, tid = threadIdx.x;
+  const size_t mk = (size_t)m * K;
+  const double2* M = Mg + ((size_t)item * 2 + side) * mk;
+  float4* X = Xg + ((size_t)item * 2 + side) * mk;
+  for (size_t idx = tid; idx < mk; idx += NTU_CTA) X[idx] = df_split(M[idx]);
+  __syncthreads();
+  // pass 1: G1 = M^H M = L1 L1^H, R1 = L1^H, Q1 = M R1^{-1} (in place)
+  qrdf_gram(X, m, K, S.G);
+  int ok = cta_cholesky(S.G, K, 0.0, &S.flag);
+  if (ok) {
+    double dmin = INFINITY, dmax = 0.0;
+    for (int i = 0; i < K; ++i) {
+      dmin = fmin(dmin, S.G[(size_t)i * K + i].x);
+      dmax = fmax(dmax, S.G[(size_t)i * K + i].x);
+    }
+    ok = dmin > 1e-5 * dmax;
+  }
+  if (ok) {
+    qrdf_factor_inverse(S.G, K, S.R1, S.Ri, S.Rid);
+    // row i: q_j = sum_{l <= j} x_l Ri[l][j], descending j so that the
+    // update can overwrite x in place
+    for (int i = tid; i < m; i += NTU_CTA) {
+      for (int j = K - 1; j >= 0; --j) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int l = 0; l <= j; ++l) df_cmac<false>(acc, X[(size_t)l * m + i], S.Rid[l * K + j]);
+        X[(size_t)j * m + i] = acc;
+      }
+    }
+    __syncthreads();
+    // pass 2: G2 = Q1^H Q1 = L2 L2^H, R2 = L2^H, Q = Q1 R2^{-1}, R = R2 R1
+    qrdf_gram(X, m, K, S.G);
+    ok = cta_cholesky(S.G, K, 0.0, &S.flag);
+  }
+  if (ok) {
+    // R = L2^H R1 (upper) into S.Ri, written out before S.Ri is reused for
+    // the inverse of L2^H
+    double2* R2 = S.Ri;
+    for (int idx = tid; idx < K * K; idx += NTU_CTA) {
+      const int i = idx / K, j = idx % K;
+      double2 acc = cz();
+      for (int l = i; l <= j; ++l) acc = cfma(cconj(S.G[(size_t)i * K + l]), S.R1[l * K + j], acc);
+      R2[idx] = acc;                     // (L2^H R1)[i][j], upper
+    }
+    __syncthreads();
+    double2* Ro = (side ? RB : RA) + (size_t)item * K * K;
+    for (int idx = tid; idx < K * K; idx += NTU_CTA) Ro[idx] = (idx % K) >= (idx / K) ? R2[idx] : cz();
+    __syncthreads();
+    qrdf_factor_inverse(S.G, K, S.R1, S.Ri, S.Rid);    // R1 <- L2^H, Ri / Rid <- its inverse
+    double2* Qo = (side ? QB : QA) + (size_t)item * mk;
+    for (int i = tid; i < m; i += NTU_CTA) {
+      for (int j = 0; j < K; ++j) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int l = 0; l <= j; ++l) df_cmac<false>(acc, X[(size_t)l * m + i], S.Rid[l * K + j]);
+        Qo[(size_t)i * K + j] = df_join(acc);
+      }
+    }
+  }
+  if (tid == 0) {
+    fallback[item * 2 + side] = ok ? 0 : 1;
+    if (ok && paths) atomicAdd(paths + 6, 1);
+  }
+}
+
+size_t qr_df_smem_bytes() { return sizeof(QrDfSmem); }
+
 // ------------------------------------------------------- Householder QR
 // Thin QR of the column-major m x K gated matrix with R's diagonal made real
 // non-negative (Fig. 2(b)).  Q is written row-major (m x K), R row-major
-// (K x K).  One CTA per (item, side).
+// (K x K).  One CTA per (item, side); with `only` set, only the matrices it
+// flags (those the double-FP32 kernel left to this one).
 __global__ void __launch_bounds__(NTU_CTA) k_qr(int m, int K, double2* __restrict__ Mg,
                                                 double2* __restrict__ Qcm,
                                                 double2* __restrict__ QA, double2* __restrict__ RA,
-                                                double2* __restrict__ QB, double2* __restrict__ RB) {
+                                                double2* __restrict__ QB, double2* __restrict__ RB,
+                                                const int* __restrict__ only, int* paths) {
   __shared__ double2 taus[32];
   __shared__ double betas[32];
   __shared__ double sred[2 * NTU_WARPS];
   const int item = blockIdx.x, side = blockIdx.y, tid = threadIdx.x;
+  if (only && !only[item * 2 + side]) return;
+  if (tid == 0 && paths) atomicAdd(paths + 7, 1);
   const int wid = tid >> 5, lid = tid & 31;
   double2* M = Mg + ((size_t)item * 2 + side) * m * K;
   double2* Qc = Qcm + ((size_t)item * 2 + side) * m * K;
@@ -349,7 +491,24 @@ cudaError_t launch_gate_qr(ntu_ctx* c, int n, const double2* Ta, const double2* 
                                                          W.GB, W.Mg);
   e = after_launch(c, "k_gated");
   if (e != cudaSuccess) return e;
-  k_qr<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.m, P.K, W.Mg, W.Qcm, QA, RA, QB, RB);
+  if (c->cfg.precision != NTU_FP64) {
+    const size_t sq = qr_df_smem_bytes();
+    static bool attr_df = false;
+    if (!attr_df) {
+      cudaFuncSetAttribute(k_qr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq);
+      attr_df = true;
+    }
+    k_qr_df<<<dim3(n, 2), NTU_CTA, sq, c->stream>>>(P.m, P.K, W.Mg, (float4*)W.Qcm, QA, RA, QB,
+                                                   RB, W.qrflag, c->d_paths);
+    e = after_launch(c, "k_qr_df");
+    if (e != cudaSuccess) return e;
+    // Householder for the matrices the double-FP32 kernel handed back
+    k_qr<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.m, P.K, W.Mg, W.Qcm, QA, RA, QB, RB, W.qrflag,
+                                                 c->d_paths);
+    return after_launch(c, "k_qr");
+  }
+  k_qr<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.m, P.K, W.Mg, W.Qcm, QA, RA, QB, RB, nullptr,
+                                               c->d_paths);
   return after_launch(c, "k_qr");
 }
 

@@ -315,47 +315,6 @@ __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
   return 1;
 }
 
-// ------------------------------------------- double-FP32 arithmetic
-// A real number x is carried as an unevaluated sum hi + lo of two FP32
-// values (hi = fl32(x), lo = fl32(x - hi)), good to about 2^-48 relative; a
-// complex number as float4 (re_hi, im_hi, re_lo, im_lo).  Products use the
-// exact FMA residual of hi * hi plus the two cross terms (lo * lo is below
-// the format's precision); sums keep the rounding error of the high part
-// exactly (two-sum) and add all low-order terms in FP32.  The explicitly
-// rounded intrinsics keep the compiler from contracting the error terms.
-// On this GPU FP32 issues at 64x the FP64 rate, so the ~12 FP32 operations
-// of a real multiply-add cost less than a sixth of one FP64 FMA.
-__device__ __forceinline__ float4 df_split(double2 v) {
-  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-  return make_float4(rh, ih, __double2float_rn(v.x - (double)rh),
-                     __double2float_rn(v.y - (double)ih));
-}
-__device__ __forceinline__ double2 df_join(float4 a) {
-  return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
-}
-// (sh, sl) += (xh + xl) (yh + yl)
-__device__ __forceinline__ void df_mac1(float& sh, float& sl, float xh, float xl, float yh,
-                                        float yl) {
-  const float p = __fmul_rn(xh, yh);
-  float e = fmaf(xh, yh, -p);
-  e = fmaf(xh, yl, e);
-  e = fmaf(xl, yh, e);
-  const float t = __fadd_rn(sh, p);
-  const float z = __fsub_rn(t, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
-  sh = t;
-  sl = __fadd_rn(sl, __fadd_rn(err, e));
-}
-// acc += a * b, or conj(a) * b with CONJ
-template <bool CONJ>
-__device__ __forceinline__ void df_cmac(float4& acc, float4 a, float4 b) {
-  const float s = CONJ ? -1.0f : 1.0f;
-  df_mac1(acc.x, acc.z, a.x, a.z, b.x, b.z);                  // re += ar br
-  df_mac1(acc.x, acc.z, -s * a.y, -s * a.w, b.y, b.w);        // re -+= ai bi
-  df_mac1(acc.y, acc.w, a.x, a.z, b.y, b.w);                  // im += ar bi
-  df_mac1(acc.y, acc.w, s * a.y, s * a.w, b.x, b.z);          // im +-= ai br
-}
-
 // g (FP64) -> gdf = g 2^-e in FP32 pairs, with 2^e the power of two nearest
 // above max |Re|, |Im| (an exact scaling that keeps every entry in FP32
 // range).  Returns e.

@@ -25,7 +25,7 @@ __global__ void k_gate_split(int d, int r, int swap_sites, const double2* G, dou
 __global__ void k_gated(int d, int danc, int D, int r, const double2* Ta, const double2* Tb,
                         const double2* GA, const double2* GB, double2* Mg);
 __global__ void k_qr(int m, int K, double2* Mg, double2* Qcm, double2* QA, double2* RA,
-                     double2* QB, double2* RB);
+                     double2* QB, double2* RB, const int* only, int* paths);
 }  // namespace ntu
 
 // 4 MiB of scratch, held by every GPU that loads the library until the
@@ -104,7 +104,7 @@ extern "C" int ntu_gate_qr_noalloc(int D, int d_phys, int d_anc, int r, const do
   }
   if (e == cudaSuccess) {
     k_qr<<<dim3(1, 2), NTU_CTA, 0, s>>>((int)m, (int)K, Mg, Qcm, (double2*)QA, (double2*)RA,
-                                        (double2*)QB, (double2*)RB);
+                                        (double2*)QB, (double2*)RB, nullptr, nullptr);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess)

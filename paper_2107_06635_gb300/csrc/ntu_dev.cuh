@@ -218,6 +218,68 @@ __device__ inline Reflector cta_reflector(const double2* v, int len, double* sre
   return r;
 }
 
+// ------------------------------------------- double-FP32 arithmetic
+// A real number x is carried as an unevaluated sum hi + lo of two FP32
+// values (hi = fl32(x), lo = fl32(x - hi)), good to about 2^-48 relative; a
+// complex number as float4 (re_hi, im_hi, re_lo, im_lo).  Products use the
+// exact FMA residual of hi * hi plus the two cross terms (lo * lo is below
+// the format's precision); sums keep the rounding error of the high part
+// exactly (two-sum) and add all low-order terms in FP32.  The explicitly
+// rounded intrinsics keep the compiler from contracting the error terms.
+// On this GPU FP32 issues at 64x the FP64 rate, so the ~12 FP32 operations
+// of a real multiply-add cost less than a sixth of one FP64 FMA.
+__device__ __forceinline__ float4 df_split(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, ih, __double2float_rn(v.x - (double)rh),
+                     __double2float_rn(v.y - (double)ih));
+}
+__device__ __forceinline__ double2 df_join(float4 a) {
+  return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+}
+// (sh, sl) += (xh + xl) (yh + yl)
+__device__ __forceinline__ void df_mac1(float& sh, float& sl, float xh, float xl, float yh,
+                                        float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float t = __fadd_rn(sh, p);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+// acc += a * b, or conj(a) * b with CONJ
+template <bool CONJ>
+__device__ __forceinline__ void df_cmac(float4& acc, float4 a, float4 b) {
+  const float s = CONJ ? -1.0f : 1.0f;
+  df_mac1(acc.x, acc.z, a.x, a.z, b.x, b.z);                  // re += ar br
+  df_mac1(acc.x, acc.z, -s * a.y, -s * a.w, b.y, b.w);        // re -+= ai bi
+  df_mac1(acc.y, acc.w, a.x, a.z, b.y, b.w);                  // im += ar bi
+  df_mac1(acc.y, acc.w, s * a.y, s * a.w, b.x, b.z);          // im +-= ai br
+}
+
+// (sh, sl) += (bh + bl)
+__device__ __forceinline__ void df_add1(float& sh, float& sl, float bh, float bl) {
+  const float t = __fadd_rn(sh, bh);
+  const float z = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(bh, z));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, bl));
+}
+// Sum of a double-FP32 complex value over the 32 lanes of a warp (all lanes
+// receive it).
+__device__ __forceinline__ float4 df_warp_sum(float4 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float4 w = make_float4(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o),
+                                 __shfl_xor_sync(0xffffffffu, v.z, o), __shfl_xor_sync(0xffffffffu, v.w, o));
+    df_add1(v.x, v.z, w.x, w.z);
+    df_add1(v.y, v.w, w.y, w.w);
+  }
+  return v;
+}
+
 // -------------------------------------------------- one-sided Jacobi SVD
 // SVD of an m x n complex matrix (m, n <= 32) held column-major in shared
 // memory with leading dimension 32: A V = U diag(s).  On exit A's first n

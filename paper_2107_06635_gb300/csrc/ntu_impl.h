@@ -79,6 +79,7 @@ struct Work {
   void *Tac, *Tbc, *QAc, *QBc, *EL, *ER, *ETL, *EBL, *ETR, *EBR, *Y, *T1, *T2, *HL, *HR, *graw;
   // split-BF16 operands of the tensor-core environment
   void *ETLd, *EBLd, *ETRd, *EBRd, *T1s, *T2s, *HLd, *HRs, *Ys, *Qs;
+  int* qrflag;           // 2 per item: QR left to the Householder kernel
   double2 *g, *gscr, *gw;     // metric, Cholesky / eigen scratch, eigenvectors
   double *gz, *geig;          // explicit Z (ng*ng) and d,e (2*ng) for the repair fallback
   double2 *gtau, *gp;         // reflector factors, vector scratch (ng each)
@@ -118,7 +119,8 @@ struct ntu_ctx {
   int profiling;
   cudaEvent_t ev[6];
   int* d_paths;       // [ALS Gershgorin+CG, ALS shifted Cholesky, ALS eigen,
-                      //  repair Gershgorin, repair Cholesky, repair eigen]
+                      //  repair Gershgorin, repair Cholesky, repair eigen,
+                      //  QR CholeskyQR2, QR Householder]
   int debug_sync;     // synchronise and check after every launch (NTU_DEBUG_SYNC=1)
 };
 

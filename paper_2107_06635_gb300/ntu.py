@@ -255,9 +255,11 @@ class Context:
         """Counts since the last call: ALS solves certified by Gershgorin
         discs (CG solve), by shifted Cholesky (refinement solve), ALS eigen
         solves; metrics certified PD by Gershgorin discs, by Cholesky, and
-        metrics eigen-repaired."""
-        c = np.zeros(6, dtype=np.int32)
+        metrics eigen-repaired; QRs by double-FP32 CholeskyQR2 and by
+        Householder."""
+        c = np.zeros(8, dtype=np.int32)
         self._ck(self.lib.ntu_solver_paths(self.h, _ptr(c)))
         return {"als_gershgorin": int(c[0]), "als_cholesky": int(c[1]), "als_eigen": int(c[2]),
                 "repair_gershgorin": int(c[3]), "repair_cholesky": int(c[4]),
-                "repair_eigen": int(c[5])}
+                "repair_eigen": int(c[5]), "qr_cholesky2": int(c[6]),
+                "qr_householder": int(c[7])}

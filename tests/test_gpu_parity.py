@@ -73,6 +73,56 @@ def test_gate_qr_matches_oracle(D, r, d_anc):
         assert _rel(QB[i].cpu().numpy(), qb) < 1e-12
 
 
+@pytest.mark.parametrize("D,r,precision", [(3, 2, 1), (5, 2, 2), (8, 2, 2), (4, 4, 1)])
+def test_gate_qr_cholesky_qr2_mixed_context(D, r, precision):
+    """Mixed contexts factor the gated matrices by CholeskyQR2 in double-FP32
+    arithmetic; the QR with positive real diag(R) is unique, so Q and R meet
+    the oracle's Householder QR to near FP64 precision."""
+    n = 3
+    Ta, Tb, G = _items(120 + D, n, 2, D)
+    ctx = _ctx(D, r, precision=precision, max_batch=n, kmax=8)
+    m, K = 2 * D ** 3, D * r
+    QA, RA, QB, RB = _empty((n, m, K)), _empty((n, K, K)), _empty((n, m, K)), _empty((n, K, K))
+    ctx.solver_paths()
+    ctx.batch_gate_qr_dev(n, _dev(Ta), _dev(Tb), _dev(G), QA, RA, QB, RB)
+    ctx.sync()
+    paths = ctx.solver_paths()
+    assert paths["qr_cholesky2"] == 2 * n and paths["qr_householder"] == 0
+    cfg = O.Config(D=D, r=r)
+    for i in range(n):
+        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+        assert _rel(RA[i].cpu().numpy(), ra) < 1e-11
+        assert _rel(RB[i].cpu().numpy(), rb) < 1e-11
+        assert _rel(QA[i].cpu().numpy(), qa) < 1e-11
+        assert _rel(QB[i].cpu().numpy(), qb) < 1e-11
+        q = QA[i].cpu().numpy()
+        assert np.abs(q.conj().T @ q - np.eye(K)).max() < 1e-12
+
+
+def test_gate_qr_rank_deficient_falls_back_to_householder():
+    """A zero-padded product state makes the gated matrices rank deficient:
+    the Cholesky factorisation of M^H M fails and the mixed context hands the
+    matrices to the Householder kernel, whose output is then bit-identical to
+    the FP64 context's."""
+    D, r, n = 3, 2, 2
+    Ta = np.stack([I.plus_x_state(D), I.plus_z_state(D)])
+    Tb = np.stack([I.plus_z_state(D), I.plus_x_state(D)])
+    G = np.stack([I.zz_gate(0.3), I.zz_gate(0.7)])
+    m, K = 2 * D ** 3, D * r
+    outs = []
+    for precision in (0, 2):
+        ctx = _ctx(D, r, precision=precision, max_batch=n, kmax=8 if precision else 15)
+        QA, RA, QB, RB = _empty((n, m, K)), _empty((n, K, K)), _empty((n, m, K)), _empty((n, K, K))
+        ctx.solver_paths()
+        ctx.batch_gate_qr_dev(n, _dev(Ta), _dev(Tb), _dev(G), QA, RA, QB, RB)
+        ctx.sync()
+        paths = ctx.solver_paths()
+        assert paths["qr_householder"] == 2 * n and paths["qr_cholesky2"] == 0
+        outs.append([x.cpu().numpy() for x in (QA, RA, QB, RB)])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
 # --------------------------------------------------------- environment
 @pytest.mark.parametrize("D,r", [(2, 2), (3, 2), (4, 2), (5, 2), (3, 4)])
 def test_env_matches_oracle_fp64(D, r):
