@@ -187,6 +187,8 @@ struct AlsShared {
   double2 ap[256];
   double2 ph[32];
   float4 Fdf[32 * 8];
+  float4 pdf[256];             // CG direction split into FP32 pairs
+  int ge;                      // scale exponent of the double-FP32 copy of g
   int cumX[257];               // item offsets of the row blocks of the double-FP32 build
   double red[2 * NTU_WARPS];
   double eps0, tau_sel;
@@ -315,16 +317,17 @@ __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
   return 1;
 }
 
-// g (FP64) -> gdf = g 2^-e in FP32 pairs, with 2^e the power of two nearest
-// above max |Re|, |Im| (an exact scaling that keeps every entry in FP32
-// range).  Returns e.
+// g (FP64) -> gdf = g 2^-e in FP32 pairs.  e = 0 while max |Re|, |Im| lies
+// in [2^-60, 2^60] (products and sums of the build then stay far inside the
+// FP32 range); otherwise 2^e is the power of two just above the maximum, an
+// exact scaling.  Returns e.
 __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng) {
   const int tid = threadIdx.x;
   const size_t nn = (size_t)ng * ng;
   double mx = 0.0;
   for (size_t i = tid; i < nn; i += NTU_CTA) mx = fmax(mx, fmax(fabs(g[i].x), fabs(g[i].y)));
   mx = block_max(mx, sm.red);
-  const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
+  const int e = (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ilogb(mx) + 1 : 0;
   for (size_t i = tid; i < nn; i += NTU_CTA) {
     double2 v = g[i];
     gdf[i] = df_split(make_double2(scalbn(v.x, -e), scalbn(v.y, -e)));
@@ -335,10 +338,11 @@ __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng)
 
 // als_reduced in double-FP32 arithmetic: same contractions and the same
 // block lower triangle, each thread holding four q columns in registers;
-// gX comes out in FP64 (scaled back by 2^e).  F (the isometric factor) is
-// split into sm.Fdf.
+// gX comes out in FP64 (scaled back by 2^e) and, for the matrix products of
+// the conjugate-gradient solve, in double-FP32 (gXdf, scaled by 2^-e).  F
+// (the isometric factor) is split into sm.Fdf.
 __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gdf, int e,
-                               int side, float4* Tmdf, double2* gX) {
+                               int side, float4* Tmdf, double2* gX, float4* gXdf) {
   const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
   const double2* F = side == 0 ? sm.MB : sm.MA;
   const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
@@ -359,6 +363,7 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
     const float4* gr = gdf + (size_t)r * ng + f * sf;
     const int q0 = qb * 4;
     float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+#pragma unroll 4
     for (int c = 0; c < K; ++c) {
       const float4 gv = gr[c * sc];
       const float4* Fc = sm.Fdf + c * D + q0;
@@ -388,6 +393,7 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
     const int q0 = qb * 4, row0 = f1 * D + q0;
     const int nr = min(4, D - q0);
     float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+#pragma unroll 4
     for (int c = 0; c < K; ++c) {
       const float4 tv = Tmdf[(size_t)(f1 * sf + c * sc) * nA + col];
       const float4* Fc = sm.Fdf + c * D + q0;
@@ -397,13 +403,23 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
       if (nr > 3) df_cmac<true>(acc3, Fc[3], tv);
     }
     double2* outc = gX + (size_t)col * nA;
+    float4* outd = gXdf + (size_t)col * nA;
     const float4 accs[4] = {acc0, acc1, acc2, acc3};
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (t < nr && row0 + t >= col) {
+    for (int t = 0; t < 4; ++t) {
+      const int row = row0 + t;
+      if (t < nr && row >= col) {
         double2 v = df_join(accs[t]);
-        outc[row0 + t] = make_double2(scalbn(v.x, e), scalbn(v.y, e));
+        if (e != 0) v = make_double2(scalbn(v.x, e), scalbn(v.y, e));
+        outc[row] = v;
+        outd[row] = accs[t];
+        if (row != col) {                                // upper triangle
+          gX[(size_t)row * nA + col] = cconj(v);
+          gXdf[(size_t)row * nA + col] =
+              make_float4(accs[t].x, -accs[t].y, accs[t].z, -accs[t].w);
+        }
       }
+    }
   }
   __syncthreads();
 }
@@ -427,8 +443,8 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
     Tm[idx] = acc;
   }
   __syncthreads();
-  // gX[(f',q'),(f,q)] = sum_c' conj(F[c'][q']) Tm[f'*sf + c'*sc][(f,q)], lower
-  // triangle only (gX is Hermitian; als_mirror fills the rest when needed)
+  // gX[(f',q'),(f,q)] = sum_c' conj(F[c'][q']) Tm[f'*sf + c'*sc][(f,q)] from
+  // the lower triangle, mirrored into the upper one
   for (int idx = tid; idx < nA * nA; idx += NTU_CTA) {
     int col = idx / nA, row = idx % nA, f1 = row / D, q1 = row % D;
     if (row < col) continue;
@@ -436,6 +452,7 @@ __device__ void als_reduced(AlsShared& sm, const AlsArgs& a, const double2* g, i
     for (int c = 0; c < K; ++c)
       acc = cfmac(F[c * D + q1], Tm[(size_t)(f1 * sf + c * sc) * nA + col], acc);
     gX[idx] = acc;
+    if (row != col) gX[(size_t)row * nA + col] = cconj(acc);
   }
   __syncthreads();
 }
@@ -470,27 +487,107 @@ __device__ void als_source(AlsShared& sm, const AlsArgs& a, int side, double2* j
 // proof holds or an iteration stalls; the caller then takes the eigen path.
 __device__ void als_mirror(double2* gX, int nA);
 
+// Upper triangle of the double-FP32 copy from its lower triangle.
+__device__ void als_mirror_df(float4* A, int nA) {
+  for (int idx = threadIdx.x; idx < nA * nA; idx += NTU_CTA) {
+    const int col = idx / nA, row = idx % nA;
+    if (row < col) {
+      const float4 v = A[(size_t)row * nA + col];
+      A[idx] = make_float4(v.x, -v.y, v.z, -v.w);
+    }
+  }
+  __syncthreads();
+}
+
+// out = g_A v (g_A full, column-major), in FP64 or, with df, in double-FP32
+// on the copy scaled by 2^-ge (v is split into sm.pdf first).  Two threads
+// per row take the two halves of the sum, each with two independent
+// accumulators, so that the dependent chains are a quarter of n_A long.
+__device__ void als_matvec(AlsShared& sm, const double2* A, const float4* Adf, const double2* v,
+                           double2* out, int nA, bool df) {
+  const int tid = threadIdx.x, h = tid & 1;
+  const int half = (nA + 1) >> 1;
+  const int j0 = h ? half : 0, j1 = h ? nA : half;
+  if (df) {
+    for (int i = tid; i < nA; i += NTU_CTA) sm.pdf[i] = df_split(v[i]);
+    __syncthreads();
+  }
+  for (int base = 0; base < nA; base += NTU_CTA / 2) {
+    const int i = base + (tid >> 1);
+    const bool on = i < nA;
+    if (df) {
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+      if (on) {
+        int j = j0;
+#pragma unroll 4
+        for (; j + 1 < j1; j += 2) {
+          df_cmac<false>(a0, Adf[(size_t)j * nA + i], sm.pdf[j]);
+          df_cmac<false>(a1, Adf[(size_t)(j + 1) * nA + i], sm.pdf[j + 1]);
+        }
+        if (j < j1) df_cmac<false>(a0, Adf[(size_t)j * nA + i], sm.pdf[j]);
+      }
+      df_add1(a0.x, a0.z, a1.x, a1.z);
+      df_add1(a0.y, a0.w, a1.y, a1.w);
+      const float4 o = make_float4(__shfl_xor_sync(0xffffffffu, a0.x, 1), __shfl_xor_sync(0xffffffffu, a0.y, 1),
+                                   __shfl_xor_sync(0xffffffffu, a0.z, 1), __shfl_xor_sync(0xffffffffu, a0.w, 1));
+      df_add1(a0.x, a0.z, o.x, o.z);
+      df_add1(a0.y, a0.w, o.y, o.w);
+      if (on && h == 0) {
+        double2 r = df_join(a0);
+        if (sm.ge != 0) r = make_double2(scalbn(r.x, sm.ge), scalbn(r.y, sm.ge));
+        out[i] = r;
+      }
+    } else {
+      double2 a0 = cz(), a1 = cz();
+      if (on) {
+        int j = j0;
+#pragma unroll 4
+        for (; j + 1 < j1; j += 2) {
+          a0 = cfma(A[(size_t)j * nA + i], v[j], a0);
+          a1 = cfma(A[(size_t)(j + 1) * nA + i], v[j + 1], a1);
+        }
+        if (j < j1) a0 = cfma(A[(size_t)j * nA + i], v[j], a0);
+      }
+      a0 = cadd(a0, a1);
+      a0.x += __shfl_xor_sync(0xffffffffu, a0.x, 1);
+      a0.y += __shfl_xor_sync(0xffffffffu, a0.y, 1);
+      if (on && h == 0) out[i] = a0;
+    }
+  }
+  __syncthreads();
+}
+
 __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2* gX,
                               double2* gC, const double2* jv, double tau_max) {
   const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31, nA = a.nA;
-  // Gershgorin discs from the lower triangle: d_i = Re gX[i][i] and
-  // s_i = sum_{j != i} (|Re| + |Im|) of row i >= sum_{j != i} |gX[i][j]|, so
-  // every eigenvalue lies in [min(d - s), max(d + s)].
+  // Gershgorin discs: d_i = Re gX[i][i] and s_i = sum_{j != i} (|Re| +
+  // |Im|) >= sum_{j != i} |gX[i][j]|, so every eigenvalue lies in
+  // [min(d - s), max(d + s)].  gX is full and Hermitian, so row i's sum is
+  // column i's (contiguous).  On the mixed contexts s_i is summed in FP32
+  // from the high parts of the double-FP32 copy (scaled by 2^-ge); that
+  // rounding (< 1e-5 relative for n_A <= 256) is covered by inflating s_i by
+  // 1e-4.
   double glo = INFINITY, ghi = -INFINITY;
   for (int i = wid; i < nA; i += NTU_WARPS) {
-    double s = 0.0;
-    for (int j = i + 1 + lid; j < nA; j += 32) {           // column i below the diagonal
-      double2 v = gX[(size_t)i * nA + j];
-      s += fabs(v.x) + fabs(v.y);
+    double sgi;
+    if (a.df) {
+      const float4* col = reinterpret_cast<const float4*>(gC) + (size_t)i * nA;
+      float sf = 0.f;
+      for (int j = lid; j < nA; j += 32)
+        if (j != i) { const float4 v = col[j]; sf += fabsf(v.x) + fabsf(v.y); }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
+      sgi = scalbn((double)sf, sm.ge) * (1.0 + 1e-4);
+    } else {
+      const double2* col = gX + (size_t)i * nA;
+      double sd = 0.0;
+      for (int j = lid; j < nA; j += 32)
+        if (j != i) { const double2 v = col[j]; sd += fabs(v.x) + fabs(v.y); }
+      sgi = warp_sum(sd);
     }
-    for (int j = lid; j < i; j += 32) {                     // row i left of the diagonal
-      double2 v = gX[(size_t)j * nA + i];
-      s += fabs(v.x) + fabs(v.y);
-    }
-    s = warp_sum(s);
     const double d = gX[(size_t)i * nA + i].x;
-    glo = fmin(glo, d - s);
-    ghi = fmax(ghi, d + s);
+    glo = fmin(glo, d - sgi);
+    ghi = fmax(ghi, d + sgi);
   }
   glo = block_min(glo, sm.red);
   const double bmax = block_max(ghi, sm.red);               // >= lambda_max
@@ -500,29 +597,49 @@ __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2
     // Tier 1: the discs alone prove lambda_min > tau_max lambda_max; solve
     // gX v = J by conjugate gradients on the full matrix, started from the
     // current factor (the tilt left it in the gauge of the fixed side, so
-    // near convergence of the sweeps it already solves the system).
-    als_mirror(gX, nA);
+    // near convergence of the sweeps it already solves the system).  On the
+    // mixed contexts the products g_A p run in double-FP32 on the copy the
+    // build left in gC, and a candidate is accepted only once its residual,
+    // recomputed in FP64, is <= 1e-13 |J| (at most three restarts from that
+    // residual); the FP64 context iterates in FP64 down to 1e-15 |J|.
+    const bool df = a.df != 0;
+    const float4* gXdf = reinterpret_cast<const float4*>(gC);
     const double2* M0 = side == 0 ? sm.MA : sm.MB;
+    for (int i = tid; i < nA; i += NTU_CTA) sm.y[i] = M0[i];
+    __syncthreads();
+    als_matvec(sm, gX, gXdf, sm.y, sm.ap, nA, df);          // ap = g_A x
     double js = 0.0, rs = 0.0;
     for (int i = tid; i < nA; i += NTU_CTA) {
-      double2 r = jv[i];
-      for (int j = 0; j < nA; ++j) r = cfms(gX[(size_t)j * nA + i], M0[j], r);
-      sm.y[i] = M0[i]; sm.y2[i] = r; sm.p[i] = r;
+      const double2 r = csub(jv[i], sm.ap[i]);
+      sm.y2[i] = r; sm.p[i] = r;
       js += cabs2(jv[i]);
       rs += cabs2(r);
     }
     js = block_sum(js, sm.red);
     rs = block_sum(rs, sm.red);
-    const double stop = 1e-30 * js;                          // |r| <= 1e-15 |J|
-    const double floor2 = 1e-26 * js;                        // |r| <= 1e-13 |J|
-    int conv = rs <= stop;
+    const double stop = (df ? 1e-28 : 1e-30) * js;          // |r| <= 1e-14 (1e-15) |J|
+    const double floor2 = (df ? 1e-24 : 1e-26) * js;        // rounding floor of the recursion
+    const double accept = 1e-26 * js;                       // FP64 residual <= 1e-13 |J|
+    int conv = 0, checks = 0;
+    bool small = rs <= stop;
     double prev = rs;
     for (int it = 0; it < 80 && !conv; ++it) {
-      for (int i = tid; i < nA; i += NTU_CTA) {
-        double2 acc = cz();
-        for (int j = 0; j < nA; ++j) acc = cfma(gX[(size_t)j * nA + i], sm.p[j], acc);
-        sm.ap[i] = acc;
+      if (small) {
+        if (!df) { conv = 1; break; }
+        als_matvec(sm, gX, gXdf, sm.y, sm.ap, nA, false);     // FP64 residual
+        double r64 = 0.0;
+        for (int i = tid; i < nA; i += NTU_CTA) {
+          const double2 r = csub(jv[i], sm.ap[i]);
+          sm.y2[i] = r; sm.p[i] = r;
+          r64 += cabs2(r);
+        }
+        r64 = block_sum(r64, sm.red);
+        if (r64 <= accept) { conv = 1; break; }
+        if (++checks > 3) break;
+        rs = r64; prev = r64; small = false;
+        continue;
       }
+      als_matvec(sm, gX, gXdf, sm.p, sm.ap, nA, df);
       double pap = 0.0;
       for (int i = tid; i < nA; i += NTU_CTA) pap += cmulc(sm.p[i], sm.ap[i]).x;
       pap = block_sum(pap, sm.red);
@@ -538,7 +655,7 @@ __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2
       }
       rn = block_sum(rn, sm.red);
       // converged, or stalled at the rounding floor of the recursion
-      if (rn <= stop || (it >= 2 && rn > 0.25 * prev && rn <= floor2)) { conv = 1; break; }
+      small = rn <= stop || (it >= 2 && rn > 0.25 * prev && rn <= floor2);
       prev = rn;
       const double beta = rn / rs;
       rs = rn;
@@ -547,6 +664,7 @@ __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2
         sm.p[i] = make_double2(fma(beta, p.x, r.x), fma(beta, p.y, r.y));
       }
       __syncthreads();
+      if (small && !df) { conv = 1; break; }
     }
     if (conv) {
       double2* M = side == 0 ? sm.MA : sm.MB;
@@ -686,7 +804,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   log.count = 0;
   double2* gC = a.gC + item * (long long)nA * nA;
   const double tau_max = als_tau(a.kmin < 0 ? 0 : a.kmin);
-  if (tid == 0) { sm.err = 0; sm.n_cg = 0; sm.n_fast = 0; sm.n_eig = 0; }
+  if (tid == 0) { sm.err = 0; sm.n_cg = 0; sm.n_fast = 0; sm.n_eig = 0; sm.ge = 0; }
   // X0 = R_A R_B^T, x0 = vec(X0) with kA slow
   for (int idx = tid; idx < K * K; idx += NTU_CTA) {
     int i = idx / K, j = idx % K;
@@ -725,6 +843,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
     }
     __syncthreads();
     ge = als_split_g(sm, g, a.gdf + item * (long long)ng * ng, ng);
+    if (tid == 0) sm.ge = ge;
     gdf = a.gdf + item * (long long)ng * ng;
   }
   // SVDU start (Fig. 2(c,d)).  X0 = U S V^H gives the balanced start
@@ -734,7 +853,9 @@ __global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
   for (int s = 0; s < a.sweeps; ++s) {
     for (int side = 0; side < 2; ++side) {
       if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
-      if (a.df) als_reduced_df(sm, a, gdf, ge, side, reinterpret_cast<float4*>(Tm), gX);
+      if (a.df)
+        als_reduced_df(sm, a, gdf, ge, side, reinterpret_cast<float4*>(Tm), gX,
+                       reinterpret_cast<float4*>(gC));
       else als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
       als_source(sm, a, side, jv, gx0);
       if (!als_solve_chol(sm, a, side, gX, gC, jv, tau_max)) {
