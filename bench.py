@@ -414,7 +414,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=8)
     ap.add_argument("--r", type=int, default=2)
-    ap.add_argument("--batch", type=int, default=304)
+    ap.add_argument("--batch", type=int, default=456)
     ap.add_argument("--sweeps", type=int, default=10)
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)

@@ -186,8 +186,6 @@ struct AlsShared {
   double2 p[256];
   double2 ap[256];
   double2 ph[32];
-  float4 Fdf[32 * 8];
-  float4 pdf[256];             // CG direction split into FP32 pairs
   int ge;                      // scale exponent of the double-FP32 copy of g
   int cumX[257];               // item offsets of the row blocks of the double-FP32 build
   double red[2 * NTU_WARPS];
@@ -196,6 +194,13 @@ struct AlsShared {
   int flag;
   int n_cg, n_fast, n_eig;
 };
+
+// The double-FP32 split of the isometric factor (during a build) and of the
+// CG direction (during a solve) live in the SVD work array W, which only the
+// tilts use; this keeps the per-CTA footprint low enough for three CTAs per
+// SM.
+__device__ __forceinline__ float4* als_fdf(AlsShared& sm) { return reinterpret_cast<float4*>(sm.S.W); }
+__device__ __forceinline__ float4* als_pdf(AlsShared& sm) { return reinterpret_cast<float4*>(sm.S.W) + 256; }
 
 struct AlsArgs {
   int D, K, ng, nA, sweeps, kmin, kmax;
@@ -340,14 +345,14 @@ __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng)
 // block lower triangle, each thread holding four q columns in registers;
 // gX comes out in FP64 (scaled back by 2^e) and, for the matrix products of
 // the conjugate-gradient solve, in double-FP32 (gXdf, scaled by 2^-e).  F
-// (the isometric factor) is split into sm.Fdf.
+// (the isometric factor) is split into als_fdf(sm).
 __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gdf, int e,
                                int side, float4* Tmdf, double2* gX, float4* gXdf) {
   const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
   const double2* F = side == 0 ? sm.MB : sm.MA;
   const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
   const int nq = (D + 3) >> 2;
-  for (int i = tid; i < K * D; i += NTU_CTA) sm.Fdf[i] = df_split(F[i]);
+  for (int i = tid; i < K * D; i += NTU_CTA) als_fdf(sm)[i] = df_split(F[i]);
   __syncthreads();
   // Tm[r][(f,q)] = sum_c g[r][f*sf + c*sc] F[c][q] for free(r) = fp >= f.
   // Work items (pair t = (fp, f), c', q block) are enumerated densely, so
@@ -366,7 +371,7 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
 #pragma unroll 4
     for (int c = 0; c < K; ++c) {
       const float4 gv = gr[c * sc];
-      const float4* Fc = sm.Fdf + c * D + q0;
+      const float4* Fc = als_fdf(sm) + c * D + q0;
       df_cmac<false>(acc0, gv, Fc[0]);
       if (q0 + 1 < D) df_cmac<false>(acc1, gv, Fc[1]);
       if (q0 + 2 < D) df_cmac<false>(acc2, gv, Fc[2]);
@@ -396,7 +401,7 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
 #pragma unroll 4
     for (int c = 0; c < K; ++c) {
       const float4 tv = Tmdf[(size_t)(f1 * sf + c * sc) * nA + col];
-      const float4* Fc = sm.Fdf + c * D + q0;
+      const float4* Fc = als_fdf(sm) + c * D + q0;
       df_cmac<true>(acc0, Fc[0], tv);
       if (nr > 1) df_cmac<true>(acc1, Fc[1], tv);
       if (nr > 2) df_cmac<true>(acc2, Fc[2], tv);
@@ -500,7 +505,7 @@ __device__ void als_mirror_df(float4* A, int nA) {
 }
 
 // out = g_A v (g_A full, column-major), in FP64 or, with df, in double-FP32
-// on the copy scaled by 2^-ge (v is split into sm.pdf first).  Two threads
+// on the copy scaled by 2^-ge (v is split into als_pdf(sm) first).  Two threads
 // per row take the two halves of the sum, each with two independent
 // accumulators, so that the dependent chains are a quarter of n_A long.
 __device__ void als_matvec(AlsShared& sm, const double2* A, const float4* Adf, const double2* v,
@@ -509,7 +514,7 @@ __device__ void als_matvec(AlsShared& sm, const double2* A, const float4* Adf, c
   const int half = (nA + 1) >> 1;
   const int j0 = h ? half : 0, j1 = h ? nA : half;
   if (df) {
-    for (int i = tid; i < nA; i += NTU_CTA) sm.pdf[i] = df_split(v[i]);
+    for (int i = tid; i < nA; i += NTU_CTA) als_pdf(sm)[i] = df_split(v[i]);
     __syncthreads();
   }
   for (int base = 0; base < nA; base += NTU_CTA / 2) {
@@ -521,10 +526,10 @@ __device__ void als_matvec(AlsShared& sm, const double2* A, const float4* Adf, c
         int j = j0;
 #pragma unroll 4
         for (; j + 1 < j1; j += 2) {
-          df_cmac<false>(a0, Adf[(size_t)j * nA + i], sm.pdf[j]);
-          df_cmac<false>(a1, Adf[(size_t)(j + 1) * nA + i], sm.pdf[j + 1]);
+          df_cmac<false>(a0, Adf[(size_t)j * nA + i], als_pdf(sm)[j]);
+          df_cmac<false>(a1, Adf[(size_t)(j + 1) * nA + i], als_pdf(sm)[j + 1]);
         }
-        if (j < j1) df_cmac<false>(a0, Adf[(size_t)j * nA + i], sm.pdf[j]);
+        if (j < j1) df_cmac<false>(a0, Adf[(size_t)j * nA + i], als_pdf(sm)[j]);
       }
       df_add1(a0.x, a0.z, a1.x, a1.z);
       df_add1(a0.y, a0.w, a1.y, a1.w);
@@ -573,16 +578,22 @@ __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, double2
     if (a.df) {
       const float4* col = reinterpret_cast<const float4*>(gC) + (size_t)i * nA;
       float sf = 0.f;
-      for (int j = lid; j < nA; j += 32)
-        if (j != i) { const float4 v = col[j]; sf += fabsf(v.x) + fabsf(v.y); }
+#pragma unroll 4
+      for (int j = lid; j < nA; j += 32) {
+        const float4 v = col[j];
+        sf += j != i ? fabsf(v.x) + fabsf(v.y) : 0.f;
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
       sgi = scalbn((double)sf, sm.ge) * (1.0 + 1e-4);
     } else {
       const double2* col = gX + (size_t)i * nA;
       double sd = 0.0;
-      for (int j = lid; j < nA; j += 32)
-        if (j != i) { const double2 v = col[j]; sd += fabs(v.x) + fabs(v.y); }
+#pragma unroll 4
+      for (int j = lid; j < nA; j += 32) {
+        const double2 v = col[j];
+        sd += j != i ? fabs(v.x) + fabs(v.y) : 0.0;
+      }
       sgi = warp_sum(sd);
     }
     const double d = gX[(size_t)i * nA + i].x;
@@ -778,7 +789,10 @@ __device__ void als_solve(AlsShared& sm, const AlsArgs& a, int side, double2* gX
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NTU_CTA) k_als(AlsArgs a) {
+// MINB: CTAs per SM the register budget is sized for (2: 128 registers, no
+// spills; 3: 80 registers, for batches of more than two items per SM).
+template <int MINB>
+__global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AlsShared& sm = *reinterpret_cast<AlsShared*>(smem_raw);
   const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
@@ -940,8 +954,24 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   a.df = c->cfg.precision != NTU_FP64;
   a.gdf = reinterpret_cast<float4*>(W.gscr);
   size_t sm = sizeof(AlsShared);
-  cudaFuncSetAttribute(k_als, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_als<<<n, NTU_CTA, sm, c->stream>>>(a);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  if (n > 2 * sms) {
+    cudaFuncSetAttribute(k_als<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_als<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    k_als<3><<<n, NTU_CTA, sm, c->stream>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_als<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_als<2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    k_als<2><<<n, NTU_CTA, sm, c->stream>>>(a);
+  }
   return after_launch(c, "k_als");
 }
 
