@@ -14,7 +14,7 @@
 // of all items) and warp-specialised: warp 0 fetches operands by TMA
 // (128-byte swizzle) through a 4-stage mbarrier pipeline, warp 1 issues
 // tcgen05.mma (M=128, N=128, K=16 per instruction) into one of two TMEM
-// accumulators, and warps 2-9 drain the other accumulator: TMEM -> shared
+// accumulators, and warps 2-17 drain the other accumulator: TMEM -> shared
 // staging -> global stores through separable index tables, either as complex
 // FP32 or directly as the split BF16 operand of the next GEMM.  The epilogue
 // of one tile thus overlaps the loads and MMAs of the next.
@@ -33,7 +33,8 @@ namespace ntu {
 namespace {
 constexpr int TBM = 128, TBN = 128, TBK = 64;
 constexpr int TILE_A = TBM * TBK * 2, TILE_B = TBN * TBK * 2;
-constexpr int EPI_WARPS = 8, TC_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int EPI_WARPS = 16, TC_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int EPI_SLICES = EPI_WARPS / 4, SLICE_COLS = TBN / EPI_SLICES;  // column slices per TMEM quarter
 static_assert((32 * EPI_WARPS) % TBN == 0, "epilogue threads per output column");
 constexpr long long WAIT_LIMIT = 1ll << 28;
 constexpr int SM_STAGE = TBN + 1;                 // staging pitch (floats)
@@ -164,8 +165,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     __syncwarp();
   } else {
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns
-    // half * 64 .. +63 of the accumulator
-    const int et = tid - 64, quarter = warp & 3, half = (warp - 2) >> 2;
+    // slice * SLICE_COLS .. + SLICE_COLS - 1 of the accumulator
+    const int et = tid - 64, quarter = warp & 3, slice = (warp - 2) >> 2;
     const int row = quarter * 32 + lane;
     const int ethreads = 32 * EPI_WARPS;
     int i = 0;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         const int m = mt * 64 + (row & 63);
         float* o = (float*)a.out + 2 * (long long)z * a.sOut + (row >> 6);
 #pragma unroll 1
-        for (int c = half * 64; c < half * 64 + 64; c += 16) {
+        for (int c = slice * SLICE_COLS; c < (slice + 1) * SLICE_COLS; c += 16) {
           float v[16];
           tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TBN + c), v);
           if (m < a.Mc) {
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         continue;
       }
 #pragma unroll 1
-      for (int c = half * 64; c < half * 64 + 64; c += 16) {
+      for (int c = slice * SLICE_COLS; c < (slice + 1) * SLICE_COLS; c += 16) {
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TBN + c), v);
 #pragma unroll
