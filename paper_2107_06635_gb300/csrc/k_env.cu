@@ -385,6 +385,24 @@ int plan_build(ntu_ctx* c) {
     jn.args.sOut = P.szG;
     P.tc_join = jn;
   }
+  // Epilogue vectorisation of the split outputs: every aligned group of four
+  // columns must land in one output row at four consecutive complex columns
+  // starting at a multiple of four, for every row.
+  auto vec4_ok = [&](const TcOp& o) {
+    const std::vector<int>& t = T.tab;
+    const int N = o.args.N, Mc = o.args.Mc;
+    if (o.mode == 0 || N % 4 != 0) return 0;
+    for (int m = 0; m < Mc; ++m)
+      if (t[o.rowK + m] % 4 != 0) return 0;
+    for (int n = 0; n < N; n += 4) {
+      if (t[o.colK + n] % 4 != 0) return 0;
+      for (int q = 1; q < 4; ++q)
+        if (t[o.colC + n + q] != t[o.colC + n] || t[o.colK + n + q] != t[o.colK + n] + q) return 0;
+    }
+    return 1;
+  };
+  for (TcOp* o : {&P.tc_t1, &P.tc_t2L, &P.tc_t2R, &P.tc_hL, &P.tc_hR, &P.tc_join})
+    o->args.vec4 = vec4_ok(*o);
   P.n_tab = (int)T.tab.size();
   if (cudaMalloc(&P.d_tab, sizeof(int) * P.n_tab) != cudaSuccess) return NTU_ENOMEM;
   if (cudaMemcpy(P.d_tab, T.tab.data(), sizeof(int) * P.n_tab, cudaMemcpyHostToDevice) !=

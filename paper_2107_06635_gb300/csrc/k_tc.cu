@@ -37,7 +37,7 @@ constexpr int EPI_WARPS = 16, TC_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int EPI_SLICES = EPI_WARPS / 4, SLICE_COLS = TBN / EPI_SLICES;  // column slices per TMEM quarter
 static_assert((32 * EPI_WARPS) % TBN == 0, "epilogue threads per output column");
 constexpr long long WAIT_LIMIT = 1ll << 28;
-constexpr int SM_STAGE = TBN + 1;                 // staging pitch (floats)
+constexpr int SM_STAGE = TBN + 4;                 // staging pitch (floats), 16-byte rows
 // The split-BF16 outputs (modes 1, 2) are written through a shared staging
 // tile so that the 2-byte stores run along output rows; the FP32 output of
 // the long-K join (mode 0) is written straight from registers and spends
@@ -204,8 +204,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
       for (int c = slice * SLICE_COLS; c < (slice + 1) * SLICE_COLS; c += 16) {
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TBN + c), v);
+        float4* dst = reinterpret_cast<float4*>(stage + row * SM_STAGE + c);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) stage[row * SM_STAGE + c + q] = v[q];
+        for (int q = 0; q < 4; ++q)
+          dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
       tc::fence_before_sync();
       __syncwarp();
@@ -216,7 +218,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         srow[64 + et] = m < a.Mc ? a.rowK[m] : 0;
       }
       tc::bar_sync(1, ethreads);                         // staging complete
-      {
+      if (a.vec4) {
+        // four consecutive columns per item: their (re, im) pairs are
+        // consecutive in one output row (checked on the host), so hi and lo
+        // each go out as one 16-byte store
+        __nv_bfloat16* o = (__nv_bfloat16*)a.out + (long long)z * a.sOut;
+        const int g4 = et % (TBN / 4);
+        const int n = n0 + 4 * g4;
+        if (n < a.N) {
+          const long long cC = a.colC[n], cK = a.colK[n];
+          for (int j = et / (TBN / 4); j < 64 && mt * 64 + j < a.Mc; j += ethreads / (TBN / 4)) {
+            const float4 re = *reinterpret_cast<const float4*>(stage + j * SM_STAGE + 4 * g4);
+            const float4 im = *reinterpret_cast<const float4*>(stage + (64 + j) * SM_STAGE + 4 * g4);
+            store_split4(o, srow[j] + cC, srow[64 + j] + cK, a.pitch, a.krp_out, re, im,
+                         MODE == 2);
+          }
+        }
+      } else {
         // each thread keeps one output column; rows advance by ethreads / TBN
         const int nn = et % TBN, n = n0 + nn;
         if (n < a.N) {

@@ -86,6 +86,42 @@ __device__ __forceinline__ void store_split(__nv_bfloat16* base, long long r, lo
     pi[krp / 2] = __halves2bfloat162(l1, l0);
   }
 }
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  __nv_bfloat162 t = __halves2bfloat162(a, b);
+  return *reinterpret_cast<uint32_t*>(&t);
+}
+// Four consecutive complex columns kc .. kc+3 (kc a multiple of 4) of complex
+// row r in the layout of store_split: the hi halves go out as one 16-byte
+// store and the lo halves as another (two each for a doubled operand).
+__device__ __forceinline__ void store_split4(__nv_bfloat16* base, long long r, long long kc,
+                                             int pitch, int krp, float4 re, float4 im,
+                                             int doubled) {
+  const float rv[4] = {re.x, re.y, re.z, re.w}, iv[4] = {im.x, im.y, im.z, im.w};
+  __nv_bfloat16 rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { split_bf16(rv[q], rh[q], rl[q]); split_bf16(iv[q], ih[q], il[q]); }
+  if (!doubled) {
+    __nv_bfloat16* p = base + r * pitch + 2 * kc;
+    *reinterpret_cast<uint4*>(p) = make_uint4(pack_bf16(rh[0], ih[0]), pack_bf16(rh[1], ih[1]),
+                                              pack_bf16(rh[2], ih[2]), pack_bf16(rh[3], ih[3]));
+    *reinterpret_cast<uint4*>(p + krp) = make_uint4(pack_bf16(rl[0], il[0]), pack_bf16(rl[1], il[1]),
+                                                    pack_bf16(rl[2], il[2]), pack_bf16(rl[3], il[3]));
+  } else {
+    __nv_bfloat16* pr = base + ((r / 64) * 128 + (r % 64)) * pitch + 2 * kc;
+    __nv_bfloat16* pi = pr + 64LL * pitch;
+    *reinterpret_cast<uint4*>(pr) =
+        make_uint4(pack_bf16(rh[0], __hneg(ih[0])), pack_bf16(rh[1], __hneg(ih[1])),
+                   pack_bf16(rh[2], __hneg(ih[2])), pack_bf16(rh[3], __hneg(ih[3])));
+    *reinterpret_cast<uint4*>(pr + krp) =
+        make_uint4(pack_bf16(rl[0], __hneg(il[0])), pack_bf16(rl[1], __hneg(il[1])),
+                   pack_bf16(rl[2], __hneg(il[2])), pack_bf16(rl[3], __hneg(il[3])));
+    *reinterpret_cast<uint4*>(pi) = make_uint4(pack_bf16(ih[0], rh[0]), pack_bf16(ih[1], rh[1]),
+                                               pack_bf16(ih[2], rh[2]), pack_bf16(ih[3], rh[3]));
+    *reinterpret_cast<uint4*>(pi + krp) =
+        make_uint4(pack_bf16(il[0], rl[0]), pack_bf16(il[1], rl[1]), pack_bf16(il[2], rl[2]),
+                   pack_bf16(il[3], rl[3]));
+  }
+}
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
 // a / b by Smith's method (no squares of b, so no underflow or overflow for

@@ -37,6 +37,7 @@ struct TcArgs {
   void* out;
   long long sOut;        // per-item stride of the output (elements)
   int pitch, krp_out;    // split outputs: row pitch and lo offset (BF16 elements)
+  int vec4;              // split outputs: groups of four columns are consecutive in one row
   int* err;
 };
 
