@@ -303,17 +303,44 @@ __global__ void __launch_bounds__(NTU_CTA) k_recompose(int dp, int D, int K,
                                                        const double2* __restrict__ MA,
                                                        const double2* __restrict__ MB,
                                                        double2* __restrict__ TaO,
-                                                       double2* __restrict__ TbO) {
+                                                       double2* __restrict__ TbO, int df) {
   __shared__ double2 Ms[32 * 8];
+  __shared__ float4 Mdf[32 * 8];
   __shared__ double sred[2 * NTU_WARPS];
   const int item = blockIdx.x, side = blockIdx.y, tid = threadIdx.x;
   const int D2 = D * D, D3 = D2 * D, D4 = D3 * D, m = dp * D3;
   const double2* Q = (side ? QB : QA) + (size_t)item * m * K;
   const double2* Mx = (side ? MB : MA) + (size_t)item * K * D;
   double2* out = (side ? TbO : TaO) + (size_t)item * dp * D4;
-  for (int i = tid; i < K * D; i += NTU_CTA) Ms[i] = Mx[i];
+  for (int i = tid; i < K * D; i += NTU_CTA) { Ms[i] = Mx[i]; Mdf[i] = df_split(Mx[i]); }
   __syncthreads();
   double nrm2 = 0.0;
+  if (df) {
+    // mixed contexts: one row of Q per thread, split into FP32 pairs once and
+    // multiplied in double-FP32 by all D columns of M (D <= 8)
+    for (int row = tid; row < m; row += NTU_CTA) {
+      float4 acc[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < K; ++k) {
+        const float4 q = df_split(Q[(size_t)row * K + k]);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a < D) df_cmac<false>(acc[a], q, Mdf[k * D + a]);
+      }
+      int n_ = row % D, t = row / D;
+      int u = t % D; t /= D;
+      int e = t % D; int p = t / D;
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        if (a < D) {
+          const double2 v = df_join(acc[a]);
+          const int l = side ? a : e, rr = side ? e : a;
+          out[(size_t)p * D4 + l * D3 + u * D2 + rr * D + n_] = v;
+          nrm2 += cabs2(v);
+        }
+    }
+  } else
   for (int idx = tid; idx < m * D; idx += NTU_CTA) {
     int row = idx / D, a = idx % D;
     double2 acc = cz();
@@ -517,7 +544,7 @@ cudaError_t launch_recompose(ntu_ctx* c, int n, const double2* QA, const double2
                              double2* Tb_out) {
   const Plan& P = c->plan;
   k_recompose<<<dim3(n, 2), NTU_CTA, 0, c->stream>>>(P.dp, P.D, P.K, QA, QB, MA, MB, Ta_out,
-                                                     Tb_out);
+                                                     Tb_out, c->cfg.precision != NTU_FP64);
   return after_launch(c, "k_recompose");
 }
 
