@@ -108,7 +108,6 @@ void carve(ntu_ctx* c, Carver& cv) {
     W.EBLd = cv.take<char>(n * bE);
     W.ETRd = cv.take<char>(n * bE);
     W.EBRd = cv.take<char>(n * bE);
-    W.T1s = cv.take<char>(n * bT);
     W.T2s = cv.take<char>(n * bT);
     W.HLd = cv.take<char>(n * (size_t)P.rowsHL * 2 * P.krpJ * 2);
     W.HRs = cv.take<char>(n * (size_t)P.rowsHR * 2 * P.krpJ * 2);

@@ -310,52 +310,21 @@ int plan_build(ntu_ctx* c) {
     // The composite column indices below are ordered so that each producer's
     // fastest column index is the consumer's K index: the split stores then
     // run along rows (coalesced) instead of across them.
-    const long long KD2 = K * D2;
-    // T1[(u,n,k),(u',n',k')] as the B operand of t2, with the GEMM's columns
-    // ordered (n',k',u'): row (k,k',n,n'), column (u,u')
-    P.t1s = P.t1;
-    P.t1s.colB = T.add({{D, K}, {K, 1}, {D, DK}});
-    P.t1s.rowC = T.add({{D, 0}, {D, D}, {K, KD2}});
-    P.t1s.colC = T.add({{D, 1}, {K, D2}, {D, 0}});
-    P.t1s.rowK = T.add({{D, D}, {D, 0}, {K, 0}});
-    P.t1s.colK = T.add({{D, 0}, {K, 0}, {D, 1}});
-    P.t1s.mode = 1; P.t1s.sC = P.rowsT * pE; P.t1s.pitch = pE; P.t1s.krp_out = (int)P.krpE;
-    // tcgen05 t1: Y as the doubled A operand (complex row (u,n,k), complex
-    // column (p,e')) written by the y product, conj(Q) as the B operand (row
-    // (n',k',u'), column (p,e')); the output tables are those of t1s
+    // Fused t1-t2 (k_t12.cu): Y as the doubled A operand with complex row
+    // k*64 + u*D + n (64 rows per k, padding rows zero) and complex column
+    // (p,e'); conj(Q) as the B operand with row k'*64 + u'*D + n' and column
+    // (p,e') (written by k_q_split); the result goes to T2s, the B operand of
+    // h: row (k,k',ht,ht'), complex column (n,n').
     P.krpY = up(2LL * dp * D, 64);
-    P.rowsY = 128 * ((D2K + 63) / 64);
-    P.rowsQ = up(D2K, 128);
+    P.rowsY = 128LL * K;
+    P.rowsQ = 64LL * K;
     const int pY = (int)(2 * P.krpY);
     P.y2 = P.y;
-    P.y2.rowC = T.add({{dp, 0}, {D, DK}, {D, K}, {K, 1}});
+    P.y2.rowC = T.add({{dp, 0}, {D, D}, {D, 1}, {K, 64}});
     P.y2.colC = T.add({{D, 0}});
     P.y2.rowK = T.add({{dp, D}, {D, 0}, {D, 0}, {K, 0}});
     P.y2.colK = T.add({{D, 1}});
     P.y2.mode = 2; P.y2.sC = P.rowsY * pY; P.y2.pitch = pY; P.y2.krp_out = (int)P.krpY;
-    TcOp t1;
-    memset(&t1, 0, sizeof(t1));
-    t1.rowC = P.t1s.rowC; t1.colC = P.t1s.colC; t1.rowK = P.t1s.rowK; t1.colK = P.t1s.colK;
-    t1.mode = 1;
-    t1.mtiles = (int)(P.rowsY / 128);
-    t1.args.kTiles = (int)(P.krpY / 64); t1.args.krp = (int)P.krpY;
-    t1.args.Mc = (int)D2K; t1.args.N = (int)D2K;
-    t1.args.pitch = pE; t1.args.krp_out = (int)P.krpE; t1.args.sOut = P.rowsT * pE;
-    P.tc_t1 = t1;
-    // t2: C[(ht,ht'),(k,k',n,n')] -> B operand of h: row (k,k',ht,ht'), column (n,n')
-    TcOp t2;
-    memset(&t2, 0, sizeof(t2));
-    t2.rowC = T.add({{D, D}, {D, 1}});
-    t2.colC = T.add({{K, KD2}, {K, D2}, {D, 0}, {D, 0}});
-    t2.rowK = T.add({{D, 0}, {D, 0}});
-    t2.colK = T.add({{K, 0}, {K, 0}, {D, D}, {D, 1}});
-    t2.mode = 1;
-    t2.mtiles = (int)(P.rowsE / 128);
-    t2.args.kTiles = (int)(P.krpE / 64); t2.args.krp = (int)P.krpE;
-    t2.args.Mc = (int)D2; t2.args.N = (int)D2K2;
-    t2.args.pitch = pE; t2.args.krp_out = (int)P.krpE; t2.args.sOut = P.rowsT * pE;
-    P.tc_t2L = t2;
-    P.tc_t2R = t2;
     // h: C[(hb,hb'),(k,k',ht,ht')] -> join operand: complex column
     // h = (hb,hb',ht,ht'); H_L doubled (A) with complex row (k,k'), H_R plain
     // (B) with row (k',k) so that the join writes g along its rows
@@ -401,7 +370,7 @@ int plan_build(ntu_ctx* c) {
     }
     return 1;
   };
-  for (TcOp* o : {&P.tc_t1, &P.tc_t2L, &P.tc_t2R, &P.tc_hL, &P.tc_hR, &P.tc_join})
+  for (TcOp* o : {&P.tc_hL, &P.tc_hR, &P.tc_join})
     o->args.vec4 = vec4_ok(*o);
   P.n_tab = (int)T.tab.size();
   if (cudaMalloc(&P.d_tab, sizeof(int) * P.n_tab) != cudaSuccess) return NTU_ENOMEM;
@@ -479,8 +448,8 @@ static cudaError_t env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, 
 
 // Tensor maps of the split operands (the work space is fixed at init, so
 // the maps are encoded once).
-// conj(Q) as the split B operand of tc_t1: Q[p,e,u,n,k] goes to row
-// (n*K + k)*D + u, complex column p*D + e.
+// conj(Q) as the split B operand of the fused t1-t2: Q[p,e,u,n,k] goes to
+// row k*64 + u*D + n, complex column p*D + e.
 __global__ void k_q_split(long long total, int D, int K, const float2* __restrict__ Q,
                           __nv_bfloat16* __restrict__ Qs, long long szQ, long long sOut,
                           int pitch, int krp) {
@@ -494,7 +463,7 @@ __global__ void k_q_split(long long total, int D, int K, const float2* __restric
     const int e = (int)(r % D);
     const int p = (int)(r / D);
     const float2 v = Q[i];
-    store_split(Qs + item * sOut, ((long long)n * K + k) * D + u, (long long)p * D + e, pitch,
+    store_split(Qs + item * sOut, (long long)k * 64 + u * D + n, (long long)p * D + e, pitch,
                 krp, v.x, -v.y, 0);
   }
 }
@@ -518,12 +487,10 @@ int tc_plan_maps(ntu_ctx* c) {
   auto mk = [&](CUtensorMap* m, void* base, long long cols, long long rows) {
     if (st == NTU_OK) st = tc_make_map(m, base, cols, rows, cap);
   };
-  mk(&P.tc_t1.mapA, W.Ys, 2 * P.krpY, P.rowsY);
-  mk(&P.tc_t1.mapB, W.Qs, 2 * P.krpY, P.rowsQ);
-  mk(&P.tc_t2L.mapA, W.ETLd, pE, P.rowsE);
-  mk(&P.tc_t2R.mapA, W.ETRd, pE, P.rowsE);
-  mk(&P.tc_t2L.mapB, W.T1s, pE, P.rowsT);
-  P.tc_t2R.mapB = P.tc_t2L.mapB;
+  mk(&P.mapYs, W.Ys, 2 * P.krpY, P.rowsY);
+  if (st == NTU_OK) st = tc_make_map(&P.mapQs, W.Qs, 2 * P.krpY, P.rowsQ, cap, 64);
+  mk(&P.mapEtopL, W.ETLd, pE, P.rowsE);
+  mk(&P.mapEtopR, W.ETRd, pE, P.rowsE);
   mk(&P.tc_hL.mapA, W.EBLd, pE, P.rowsE);
   mk(&P.tc_hR.mapA, W.EBRd, pE, P.rowsE);
   mk(&P.tc_hL.mapB, W.T2s, pE, P.rowsT);
@@ -549,13 +516,11 @@ static cudaError_t env_chain_bf16x3(ntu_ctx* c, int n, const void* Ta, const voi
   RG(run_gemm<float2>(c, P.e2BR, n, Ta, Ta, W.EBRd));
   RG(run_gemm<float2>(c, P.y2, n, QA, W.EL, W.Ys));
   RG(launch_q_split(c, n, (const float2*)QA, W.Qs));
-  RG(launch_tc_gemm(c, P.tc_t1, n, W.T1s));
-  RG(launch_tc_gemm(c, P.tc_t2L, n, W.T2s));
+  RG(launch_t12(c, n, P.mapEtopL, W.T2s));
   RG(launch_tc_gemm(c, P.tc_hL, n, W.HLd));
   RG(run_gemm<float2>(c, P.y2, n, QB, W.ER, W.Ys));
   RG(launch_q_split(c, n, (const float2*)QB, W.Qs));
-  RG(launch_tc_gemm(c, P.tc_t1, n, W.T1s));
-  RG(launch_tc_gemm(c, P.tc_t2R, n, W.T2s));
+  RG(launch_t12(c, n, P.mapEtopR, W.T2s));
   RG(launch_tc_gemm(c, P.tc_hR, n, W.HRs));
   RG(launch_tc_gemm(c, P.tc_join, n, graw));
   return cudaSuccess;

@@ -1,0 +1,437 @@
+// Fused t1 -> t2 of the half environment (Fig. 4(c,d)) on tcgen05 for the
+// NTU_MIXED_BF16X3 precision.
+//
+// For one item and one bond-index pair (k, k') the double isometry block
+//   T1[(u,n),(u',n')] = sum_{p,e'} Y[p,e',u,n,k] conj(Q[p,e',u',n',k'])
+// and the top-edge contraction
+//   T2[(ht,ht'),(n,n')] = sum_{u,u'} E_top[ht,u,ht',u'] T1[(u,n),(u',n')]
+// are two chained GEMMs.  The first runs on the tensor cores into TMEM, its
+// result is split into BF16 hi/lo and written by the epilogue warps straight
+// into shared memory as the (128-byte swizzled, K-major) B operand of the
+// second, so T1 never leaves the SM; only T2 goes to HBM, as the split B
+// operand of h (rows (k,k',ht,ht'), complex columns (n,n')).
+//
+// Complex products are real GEMMs as in k_tc.cu: A doubled (Re / Im rows 64
+// apart in a 128-row tile), B interleaved (re, im) along K, three split
+// products hi*hi + hi*lo + lo*hi accumulated in FP32.
+//
+// One persistent CTA per SM takes a contiguous range of (item, k, k') units.
+// Warp 0 issues TMA (E_top once per item, the Y block once per k, the
+// conj(Q) block per unit, double-buffered), warp 1 issues the MMAs (GEMM1 of
+// unit i, then GEMM2 of unit i-1), warps 2-9 turn accumulator 1 into the B
+// operand of GEMM2 (two buffers), warps 10-17 turn accumulator 2 into output
+// rows through a shared staging block.  Every wait is bounded; every role
+// leaves its loop on a timeout and the epilogue groups leave together.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "ntu_dev.cuh"
+#include "ntu_impl.h"
+#include "tc_sm103.cuh"
+
+namespace ntu {
+
+namespace {
+constexpr int EPI = 256;                       // threads of each epilogue group
+static_assert(EPI % 128 == 0 && EPI % 64 == 0, "copy-out: krpE (64 or 128) must divide EPI");
+constexpr int T12_THREADS = 64 + 2 * EPI;
+constexpr long long T12_WAIT = 1ll << 28;
+constexpr int T12_SLEEP_POLLS = 1 << 17;       // x <= 20 us: about 2.6 s
+constexpr int A_TILE = 128 * 128;            // 128 rows x 64 BF16
+constexpr int B_TILE = 64 * 128;             // 64 rows x 64 BF16
+constexpr int OFF_A2 = 0;                     // 4 A tiles: E_top hi0, hi1, lo0, lo1
+constexpr int OFF_A1 = OFF_A2 + 4 * A_TILE;   // 2 A tiles: Y hi, lo
+constexpr int OFF_B1 = OFF_A1 + 2 * A_TILE;   // 2 buffers x 2 B tiles: conj(Q) hi, lo
+constexpr int OFF_B2 = OFF_B1 + 4 * B_TILE;   // 2 buffers x 4 B tiles: T1 hi0, hi1, lo0, lo1
+constexpr int OFF_OUT = OFF_B2 + 8 * B_TILE;  // output staging, 64 rows x (256 + 2) BF16
+constexpr int OUT_PITCH = 256 + 2;            // odd word count: conflict-free column stores
+constexpr int OUT_BYTES = 64 * OUT_PITCH * 2 + 16 * 16;
+constexpr int OFF_BAR = OFF_OUT + OUT_BYTES;
+constexpr size_t T12_SMEM = (size_t)OFF_BAR + 512 + 1024;
+static_assert(T12_SMEM <= 227 * 1024, "shared memory budget");
+
+// Byte offset of BF16 element w (0..63) of row r in a K-major tile with
+// 128-byte rows written with the 128-byte swizzle (what TMA writes and the
+// MMA descriptor of tc::sdesc_k128 expects): the 16-byte chunk index is
+// XORed with the row index modulo 8.
+__device__ __forceinline__ uint32_t swz(int r, int w) {
+  return (uint32_t)(r * 128 + ((((w >> 3) ^ (r & 7))) << 4) + ((w & 7) << 1));
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+}  // namespace
+
+struct T12Args {
+  int D, K;
+  int nchunk;           // 64-wide K chunks of GEMM2 (krpE / 64)
+  int krpY, krpE;
+  long long units;      // items * K * K
+  __nv_bfloat16* out;   // T2 split operand, items x rowsT x 2 krpE
+  long long sOut;       // per-item stride (elements)
+  int* err;
+};
+
+// DT = 8: bond dimension fixed at compile time (every index of the epilogues
+// folds into constants); DT = 0: any D <= 8 at run time.
+template <int DT>
+__global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ CUtensorMap mA2,
+                                                      const __grid_constant__ CUtensorMap mA1,
+                                                      const __grid_constant__ CUtensorMap mB1,
+                                                      T12Args a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = (uint64_t*)(sm + OFF_BAR);
+  uint64_t *a2_full = bar, *a2_empty = bar + 1, *a1_full = bar + 2, *a1_empty = bar + 3;
+  uint64_t *q_full = bar + 4, *q_empty = bar + 6;             // [2]
+  uint64_t *c1_full = bar + 8, *c1_empty = bar + 10;          // accumulator 1 [2]
+  uint64_t *b2_full = bar + 12, *b2_empty = bar + 14;         // GEMM2 B operand [2]
+  uint64_t *c2_full = bar + 16, *c2_empty = bar + 18;         // accumulator 2 [2]
+  uint64_t* done = bar + 20;
+  uint32_t* tmem_slot = (uint32_t*)(bar + 21);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = DT ? DT : a.D, K = a.K, D2 = D * D, KK = K * K;
+  // contiguous range of units for this CTA
+  const long long u0 = a.units * blockIdx.x / gridDim.x;
+  const long long u1 = a.units * (blockIdx.x + 1) / gridDim.x;
+  // padding of the generated operand and of the staging block must read as
+  // zero: clear both once (generic stores, then a proxy fence)
+  for (int i = tid; i < (8 * B_TILE + OUT_BYTES) / 16; i += T12_THREADS)
+    reinterpret_cast<uint4*>(sm + OFF_B2)[i] = make_uint4(0u, 0u, 0u, 0u);
+  fence_proxy_async();
+  if (tid == 0) {
+    tc::mbar_init(a2_full, 1); tc::mbar_init(a2_empty, 1);
+    tc::mbar_init(a1_full, 1); tc::mbar_init(a1_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&q_full[b], 1); tc::mbar_init(&q_empty[b], 1);
+      tc::mbar_init(&c1_full[b], 1); tc::mbar_init(&c1_empty[b], EPI / 32);
+      tc::mbar_init(&b2_full[b], 1); tc::mbar_init(&b2_empty[b], 1);
+      tc::mbar_init(&c2_full[b], 1); tc::mbar_init(&c2_empty[b], EPI / 32);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 256);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: per unit the Y block if (item, k) changed, the
+      // conj(Q) block, then E_top if the item changed (this order lets the
+      // MMA warp issue GEMM1 of the new unit before it releases E_top)
+      int a1z = -1, a1k = -1, a2z = -1;
+      long long a1n = 0, a2n = 0, qn = 0, i = 0;
+      for (long long u = u0; u < u1; ++u, ++i) {
+        const int z = (int)(u / KK), kk = (int)(u % KK), k = kk / K, kp = kk % K;
+        if (z != a1z || k != a1k) {
+          if (a1n > 0 && !tc::mbar_wait(a1_empty, (uint32_t)((a1n - 1) & 1), T12_WAIT)) {
+            raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+            break;
+          }
+          tc::mbar_expect_tx(a1_full, 2 * A_TILE);
+          tc::tma_load_3d(sm + OFF_A1, &mA1, a1_full, 0, k * 128, z);
+          tc::tma_load_3d(sm + OFF_A1 + A_TILE, &mA1, a1_full, a.krpY, k * 128, z);
+          ++a1n; a1z = z; a1k = k;
+        }
+        const int qb = (int)(i & 1);
+        const long long qu = i >> 1;
+        if (qu > 0 && !tc::mbar_wait(&q_empty[qb], (uint32_t)((qu - 1) & 1), T12_WAIT)) {
+          raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+          break;
+        }
+        unsigned char* qd = sm + OFF_B1 + qb * 2 * B_TILE;
+        tc::mbar_expect_tx(&q_full[qb], 2 * B_TILE);
+        tc::tma_load_3d(qd, &mB1, &q_full[qb], 0, kp * 64, z);
+        tc::tma_load_3d(qd + B_TILE, &mB1, &q_full[qb], a.krpY, kp * 64, z);
+        ++qn;
+        if (z != a2z) {
+          if (a2n > 0 && !tc::mbar_wait(a2_empty, (uint32_t)((a2n - 1) & 1), T12_WAIT)) {
+            raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+            break;
+          }
+          tc::mbar_expect_tx(a2_full, 2 * a.nchunk * A_TILE);
+          for (int c = 0; c < a.nchunk; ++c) {
+            tc::tma_load_3d(sm + OFF_A2 + c * A_TILE, &mA2, a2_full, c * 64, 0, z);
+            tc::tma_load_3d(sm + OFF_A2 + (2 + c) * A_TILE, &mA2, a2_full, a.krpE + c * 64, 0, z);
+          }
+          ++a2n; a2z = z;
+        }
+      }
+      // no TMA copy may still be landing in shared memory when the CTA exits
+      bool dr = true;
+      if (a1n > 0) dr &= tc::mbar_wait(a1_full, (uint32_t)((a1n - 1) & 1), T12_WAIT);
+      if (a2n > 0) dr &= tc::mbar_wait(a2_full, (uint32_t)((a2n - 1) & 1), T12_WAIT);
+      for (long long q = qn - 2 < 0 ? 0 : qn - 2; q < qn; ++q)
+        dr &= tc::mbar_wait(&q_full[q & 1], (uint32_t)((q >> 1) & 1), T12_WAIT);
+      if (!dr) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: GEMM1 of unit i, then GEMM2 of unit i - 1
+      const uint32_t id = tc::idesc_bf16_f32(128, 64);
+      int a1z = -1, a1k = -1, a2z = -1;
+      long long a1n = 0, a2n = 0, i = 0;
+      bool ok = true;
+      for (long long u = u0; u <= u1 && ok; ++u, ++i) {
+        if (u < u1) {
+          const int z = (int)(u / KK), kk = (int)(u % KK), k = kk / K;
+          if (z != a1z || k != a1k) {
+            if (!tc::mbar_wait(a1_full, (uint32_t)(a1n & 1), T12_WAIT)) { ok = false; break; }
+            ++a1n; a1z = z; a1k = k;
+          }
+          const int b = (int)(i & 1);
+          const long long ub = i >> 1;
+          if (ub > 0 && !tc::mbar_wait(&c1_empty[b], (uint32_t)((ub - 1) & 1), T12_WAIT)) { ok = false; break; }
+          if (!tc::mbar_wait(&q_full[b], (uint32_t)(ub & 1), T12_WAIT)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t acc = tmem + (uint32_t)(b * 64);
+          const uint64_t ah = tc::sdesc_k128(tc::smem_u32(sm + OFF_A1));
+          const uint64_t al = tc::sdesc_k128(tc::smem_u32(sm + OFF_A1 + A_TILE));
+          const uint64_t bh = tc::sdesc_k128(tc::smem_u32(sm + OFF_B1 + b * 2 * B_TILE));
+          const uint64_t bl = tc::sdesc_k128(tc::smem_u32(sm + OFF_B1 + b * 2 * B_TILE + B_TILE));
+#pragma unroll
+          for (int kk4 = 0; kk4 < 4; ++kk4) {
+            tc::mma_bf16(acc, ah + 2 * kk4, bh + 2 * kk4, id, kk4 != 0);
+            tc::mma_bf16(acc, ah + 2 * kk4, bl + 2 * kk4, id, 1);
+            tc::mma_bf16(acc, al + 2 * kk4, bh + 2 * kk4, id, 1);
+          }
+          tc::mma_commit(&q_empty[b]);
+          tc::mma_commit(&c1_full[b]);
+          // the Y block is released after the last unit that reads it
+          bool last_k = u + 1 >= u1;
+          if (!last_k) {
+            const int zn = (int)((u + 1) / KK), kn = (int)((u + 1) % KK) / K;
+            last_k = zn != z || kn != k;
+          }
+          if (last_k) tc::mma_commit(a1_empty);
+        }
+        if (u > u0) {
+          // GEMM2 of unit j = u - 1
+          const long long j = i - 1;
+          const int zj = (int)((u - 1) / KK);
+          const int b = (int)(j & 1);
+          const long long ub = j >> 1;
+          if (zj != a2z) {
+            if (!tc::mbar_wait(a2_full, (uint32_t)(a2n & 1), T12_WAIT)) { ok = false; break; }
+            ++a2n; a2z = zj;
+          }
+          if (!tc::mbar_wait(&b2_full[b], (uint32_t)(ub & 1), T12_WAIT)) { ok = false; break; }
+          if (ub > 0 && !tc::mbar_wait(&c2_empty[b], (uint32_t)((ub - 1) & 1), T12_WAIT)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t acc = tmem + 128u + (uint32_t)(b * 64);
+          for (int c = 0; c < a.nchunk; ++c) {
+            const uint64_t ah = tc::sdesc_k128(tc::smem_u32(sm + OFF_A2 + c * A_TILE));
+            const uint64_t al = tc::sdesc_k128(tc::smem_u32(sm + OFF_A2 + (2 + c) * A_TILE));
+            const uint64_t bh = tc::sdesc_k128(tc::smem_u32(sm + OFF_B2 + (b * 4 + c) * B_TILE));
+            const uint64_t bl = tc::sdesc_k128(tc::smem_u32(sm + OFF_B2 + (b * 4 + 2 + c) * B_TILE));
+#pragma unroll
+            for (int kk4 = 0; kk4 < 4; ++kk4) {
+              tc::mma_bf16(acc, ah + 2 * kk4, bh + 2 * kk4, id, (c | kk4) != 0);
+              tc::mma_bf16(acc, ah + 2 * kk4, bl + 2 * kk4, id, 1);
+              tc::mma_bf16(acc, al + 2 * kk4, bh + 2 * kk4, id, 1);
+            }
+          }
+          tc::mma_commit(&b2_empty[b]);
+          tc::mma_commit(&c2_full[b]);
+          if (u == u1 || (int)(u / KK) != zj) tc::mma_commit(a2_empty);
+        }
+      }
+      if (!ok) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+      // every MMA issued has retired before TMEM is released
+      tc::mma_commit(done);
+      if (!tc::mbar_wait(done, 0, T12_WAIT)) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+    }
+    __syncwarp();
+  } else if (warp < 2 + EPI / 32) {
+    // ---- epilogue 1: accumulator 1 (rows (u,n) Re / Im, columns (u',n'))
+    // -> split B operand of GEMM2 in shared memory, row n' * D + n (this
+    // order spreads a warp's stores over the swizzle chunks; epilogue 2 maps
+    // GEMM2's columns back), K (u,u')
+    // warp w reads TMEM lanes 32 (w % 4) .. +31, columns slice * 32 .. +31
+    const int et = tid - 64, quarter = warp & 3, row = quarter * 32 + lane;
+    const int cs = ((warp - 2) >> 2) * 32;
+    const int r = row & 63, im = row >> 6;
+    const bool rv = r < D2;
+    const int uu = rv ? r / D : 0, nn = rv ? r % D : 0;
+    long long i = 0;
+    for (long long u = u0; u < u1; ++u, ++i) {
+      const int b = (int)(i & 1);
+      const long long ub = i >> 1;
+      // one thread waits (suspended in hardware), the group meets at a
+      // named barrier that also carries the outcome
+      bool got = true;
+      if (et == 0) {
+        got = tc::mbar_wait_sleep(&c1_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
+        if (got && ub > 0) got = tc::mbar_wait_sleep(&b2_empty[b], (uint32_t)((ub - 1) & 1), T12_SLEEP_POLLS);
+      }
+      if (!tc::bar_and(1, EPI, got)) {
+        if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+        break;
+      }
+      tc::fence_after_sync();
+      unsigned char* B2 = sm + OFF_B2 + b * 4 * B_TILE;
+      if (DT == 8) {
+        // row n' * 8 + n, so (row & 7) = n; K = 16 u + 2 u' + im lies in
+        // chunk u >> 2, 16-byte slot (2u + (u' >> 2)) ^ n, byte 4 (u' & 3) + 2 im
+        unsigned char* bh = B2 + (uu >> 2) * B_TILE + nn * 128 + (im << 1);
+        unsigned char* s0 = bh + (((((2 * uu) & 7) ^ nn)) << 4);
+        unsigned char* s1 = bh + (((((2 * uu + 1) & 7) ^ nn)) << 4);
+#pragma unroll
+        for (int c0 = cs; c0 < cs + 32; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 64 + c0), v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int c = c0 + q, up = c >> 3, np = c & 7;
+            unsigned char* dst = (up >> 2 ? s1 : s0) + np * 1024 + ((up & 3) << 2);
+            __nv_bfloat16 h, l;
+            split_bf16(v[q], h, l);
+            *reinterpret_cast<__nv_bfloat16*>(dst) = h;
+            *reinterpret_cast<__nv_bfloat16*>(dst + 2 * B_TILE) = l;
+          }
+        }
+      } else
+#pragma unroll 1
+      for (int c0 = cs; c0 < cs + 32; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 64 + c0), v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int c = c0 + q;
+          if (rv && c < D2) {
+            const int up = c / D, np = c % D;
+            const int brow = np * D + nn, kre = 2 * (uu * D + up) + im;
+            const uint32_t off = swz(brow, kre & 63);
+            __nv_bfloat16 h, l;
+            split_bf16(v[q], h, l);
+            *reinterpret_cast<__nv_bfloat16*>(B2 + (kre >> 6) * B_TILE + off) = h;
+            *reinterpret_cast<__nv_bfloat16*>(B2 + (2 + (kre >> 6)) * B_TILE + off) = l;
+          }
+        }
+      }
+      fence_proxy_async();                       // generic writes -> tensor-core reads
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&c1_empty[b]);
+      tc::bar_sync(1, EPI);
+      if (et == 0) tc::mbar_arrive(&b2_full[b]);
+    }
+  } else {
+    // ---- epilogue 2: accumulator 2 (rows (ht,ht') Re / Im, columns j =
+    // n' * D + n) -> staging rows of the split T2 operand (complex column
+    // n * D + n') -> contiguous HBM rows
+    const int et = tid - 64 - EPI, quarter = warp & 3, row = quarter * 32 + lane;
+    const int cs = ((warp - 2 - EPI / 32) >> 2) * 32;
+    const int r = row & 63, im = row >> 6;
+    const bool rv = r < D2;
+    const int pitch = 2 * a.krpE;             // output row (BF16)
+    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(sm + OFF_OUT);
+    long long i = 0;
+    for (long long u = u0; u < u1; ++u, ++i) {
+      const int z = (int)(u / KK), kk = (int)(u % KK);
+      const int b = (int)(i & 1);
+      const long long ub = i >> 1;
+      const bool got =
+          et != 0 || tc::mbar_wait_sleep(&c2_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
+      if (!tc::bar_and(2, EPI, got)) {
+        if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+        break;
+      }
+      tc::fence_after_sync();
+      if (DT == 8) {
+        // column j = n' * 8 + n -> complex column n * 8 + n'; krpE = 128
+        __nv_bfloat16* sr = stg + r * OUT_PITCH + im;
+#pragma unroll
+        for (int c0 = cs; c0 < cs + 32; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(128 + b * 64 + c0), v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int c = c0 + q, col = (c & 7) * 8 + (c >> 3);
+            __nv_bfloat16 h, l;
+            split_bf16(v[q], h, l);
+            sr[2 * col] = h;
+            sr[128 + 2 * col] = l;
+          }
+        }
+      } else
+#pragma unroll 1
+      for (int c0 = cs; c0 < cs + 32; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(128 + b * 64 + c0), v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int c = c0 + q;
+          if (rv && c < D2) {
+            const int col = (c % D) * D + c / D;
+            __nv_bfloat16 h, l;
+            split_bf16(v[q], h, l);
+            stg[r * OUT_PITCH + 2 * col + im] = h;
+            stg[r * OUT_PITCH + a.krpE + 2 * col + im] = l;
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&c2_empty[b]);
+      tc::bar_sync(2, EPI);
+      // rows (k,k',ht,ht') of this unit are contiguous in the output
+      // staging rows are OUT_PITCH BF16 (an odd number of words) apart,
+      // output rows pitch apart: word-wide copies, consecutive threads on
+      // consecutive words (conflict-free reads, coalesced writes)
+      const int wpr = pitch / 2;                // 4-byte words per row
+      uint32_t* dst = reinterpret_cast<uint32_t*>(
+          a.out + (long long)z * a.sOut + (long long)kk * D2 * pitch);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(sm + OFF_OUT);
+      const int w = et % wpr, rstep = EPI / wpr;    // wpr = krpE divides EPI
+      for (int rr = et / wpr; rr < D2; rr += rstep)
+        dst[(size_t)rr * wpr + w] = src[rr * (OUT_PITCH / 2) + w];
+      tc::bar_sync(2, EPI);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+size_t t12_smem_bytes() { return T12_SMEM; }
+
+cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE, void* out) {
+  const Plan& P = c->plan;
+  T12Args a;
+  a.D = P.D; a.K = P.K;
+  a.nchunk = (int)(P.krpE / 64);
+  a.krpY = (int)P.krpY; a.krpE = (int)P.krpE;
+  a.units = (long long)n * P.K * P.K;
+  a.out = (__nv_bfloat16*)out;
+  a.sOut = P.rowsT * 2 * P.krpE;
+  a.err = c->d_status;
+  if (a.units == 0) return cudaSuccess;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int grid = (int)(a.units < sms ? a.units : sms);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_t12<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T12_SMEM);
+    cudaFuncSetAttribute(k_t12<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T12_SMEM);
+    attr = true;
+  }
+  if (P.D == 8)
+    k_t12<8><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, a);
+  else
+    k_t12<0><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, a);
+  return after_launch(c, "k_t12");
+}
+
+}  // namespace ntu

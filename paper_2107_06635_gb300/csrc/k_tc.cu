@@ -273,12 +273,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 3-D map of a [items][rows][cols] BF16 array with 64 x 128 boxes and the
 // 128-byte swizzle.  cols must be a multiple of 64 (so every row pitch and
 // every box start are 16-byte aligned).
-int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items) {
+int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items,
+                int box_rows) {
   auto enc = tensor_map_encoder();
   if (!enc) return NTU_EUNSUPPORTED;
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)items};
   cuuint64_t strides[2] = {(cuuint64_t)cols * 2, (cuuint64_t)cols * rows * 2};
-  cuuint32_t box[3] = {TBK, TBM, 1}, es[3] = {1, 1, 1};
+  cuuint32_t box[3] = {TBK, (cuuint32_t)box_rows, 1}, es[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

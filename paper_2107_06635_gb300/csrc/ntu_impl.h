@@ -59,10 +59,10 @@ struct Plan {
   GemmOp join;                          // join of the two halves (Fig. 4(d,e))
   // split-BF16 tensor-core variant (NTU_MIXED_BF16X3)
   GemmOp e2TL, e2BL, e2TR, e2BR;        // edge tensors written as doubled A operands
-  GemmOp t1s;                           // T1 written as the B operand of t2 (FP32 pipes)
-  GemmOp y2;                            // Y written as the doubled A operand of tc_t1
-  TcOp tc_t1, tc_t2L, tc_t2R, tc_hL, tc_hR, tc_join;
-  long long krpY, rowsY, rowsQ;         // split operands of tc_t1: Y (doubled A), conj(Q) (B)
+  GemmOp y2;                            // Y written as the doubled A operand of the fused t1-t2
+  TcOp tc_hL, tc_hR, tc_join;
+  long long krpY, rowsY, rowsQ;         // split operands of the fused t1-t2: Y (doubled A), conj(Q) (B)
+  CUtensorMap mapYs, mapQs, mapEtopL, mapEtopR;   // TMA maps of the fused t1-t2 (k_t12.cu)
   long long krpE, krpJ;                 // padded real K of the t2/h and join GEMMs
   long long rowsE, rowsT, rowsHL, rowsHR;  // allocated rows of the split operands
   int* d_tab;                           // device index tables
@@ -79,7 +79,7 @@ struct Work {
   // environment (element type: double2 for FP64, float2 for the mixed paths)
   void *Tac, *Tbc, *QAc, *QBc, *EL, *ER, *ETL, *EBL, *ETR, *EBR, *Y, *T1, *T2, *HL, *HR, *graw;
   // split-BF16 operands of the tensor-core environment
-  void *ETLd, *EBLd, *ETRd, *EBRd, *T1s, *T2s, *HLd, *HRs, *Ys, *Qs;
+  void *ETLd, *EBLd, *ETRd, *EBRd, *T2s, *HLd, *HRs, *Ys, *Qs;
   int* qrflag;           // 2 per item: QR left to the Householder kernel
   double2 *g, *gscr, *gw;     // metric, Cholesky / eigen scratch, eigenvectors
   double *gz, *geig;          // explicit Z (ng*ng) and d,e (2*ng) for the repair fallback
@@ -161,7 +161,9 @@ cudaError_t launch_copy_raw(ntu_ctx* c, int n, const void* graw, double2* g);
 size_t als_smem_bytes();
 
 // tensor-core environment (k_tc.cu, k_env.cu)
-int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items);
+int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items,
+                int box_rows = 128);
+cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE, void* out);
 int tc_plan_maps(ntu_ctx* c);
 cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out);
 
