@@ -148,6 +148,41 @@ int ntu_batch_update_host(ntu_ctx* ctx, int n, const double* Ta, const double* T
                           const double* gates, double* Ta_out, double* Tb_out,
                           double* info);
 
+/* ---- uneven batches ------------------------------------------------------
+ * Independent bond updates whose bond dimension D and gate rank r differ from
+ * item to item (the batch form of the step driver, Sec. II, run over many
+ * independent bonds).  An ntu_uneven holds one context per kind (D, r) --
+ * each with its own plan and work space, all on one stream -- and pinned
+ * host staging.
+ *
+ * ntu_uneven_init: n_kinds distinct kinds (D[k], r[k]), at most max_items[k]
+ *   items of kind k per call; d_phys, d_anc, als_sweeps, precision, tau_kmin,
+ *   tau_kmax as in ntu_config (shared by every kind); stream NULL creates a
+ *   private stream.  Errors: NTU_EINVAL (repeated kind, bad sizes), and the
+ *   errors of ntu_init for any kind.
+ * ntu_uneven_update_host: n items (host pointers); item i is of kind
+ *   kind[i]; Ta, Tb, Ta_out, Tb_out are the items' site tensors concatenated
+ *   in item order (item i takes d_p * D^4 complex of its kind); gates n x
+ *   d_phys^4 complex; info n x 4 ([eps, delta, eps0, tau] as in
+ *   ntu_batch_update_dev).  The items of each kind go through that kind's
+ *   batched update; with use_graph = 1 the device part of the call (copies
+ *   in, every kind's update, copies out) is captured as one CUDA graph the
+ *   first time a given set of per-kind counts is seen, and replayed by later
+ *   calls with the same counts.  Synchronises before return.  Errors:
+ *   NTU_EINVAL (unknown kind, more items of a kind than max_items), device
+ *   status of any kind as in ntu_sync.
+ * ntu_uneven_last_error: description of the last failure (uneven == NULL:
+ *   of the last failed ntu_uneven_init). */
+typedef struct ntu_uneven ntu_uneven;
+int ntu_uneven_init(int d_phys, int d_anc, int als_sweeps, int precision, int tau_kmin,
+                    int tau_kmax, int n_kinds, const int* D, const int* r, const int* max_items,
+                    void* stream, ntu_uneven** out);
+int ntu_uneven_update_host(ntu_uneven* uneven, int n, const int* kind, const double* Ta,
+                           const double* Tb, const double* gates, double* Ta_out,
+                           double* Tb_out, double* info, int use_graph);
+int ntu_uneven_destroy(ntu_uneven* uneven);
+const char* ntu_uneven_last_error(const ntu_uneven* uneven);
+
 /* Stage calls (device pointers), for testing and for callers that chain
  * their own pipeline.
  *   gate_qr : Fig. 2(a,b)   -> QA, QB ((d_p D^3) x K), RA, RB (K x K)

@@ -38,7 +38,7 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 _DP = ctypes.POINTER(ctypes.c_double)
 
-# name -> argument types; every function returns int except ntu_last_error
+# name -> argument types; every function returns int except the *_last_error ones
 _SIGS = {
     "ntu_init": [ctypes.POINTER(Config), _P, ctypes.POINTER(_P)],
     "ntu_destroy": [_P],
@@ -63,6 +63,10 @@ _SIGS = {
     "ntu_stage_times": [_P, _P],
     "ntu_solver_paths": [_P, _P],
     "ntu_gate_qr_noalloc": [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P],
+    "ntu_uneven_init": [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_P)],
+    "ntu_uneven_update_host": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I],
+    "ntu_uneven_destroy": [_P],
+    "ntu_uneven_last_error": [_P],
 }
 
 
@@ -87,7 +91,7 @@ def load(build: bool = True):
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "ntu_last_error" else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name.endswith("last_error") else ctypes.c_int
     _LIB = lib
     return lib
 
@@ -263,3 +267,59 @@ class Context:
                 "repair_gershgorin": int(c[3]), "repair_cholesky": int(c[4]),
                 "repair_eigen": int(c[5]), "qr_cholesky2": int(c[6]),
                 "qr_householder": int(c[7])}
+
+
+class UnevenBatch:
+    """Independent bond updates of different (D, r) in one call: one context
+    per kind on a shared stream; optionally replayed as one CUDA graph."""
+
+    def __init__(self, kinds, max_items, d: int = 2, d_anc: int = 1, sweeps: int = 10,
+                 precision: int = NTU_FP64, tau_kmin: int = 4, tau_kmax: int = 15, stream=None):
+        self.lib = load()
+        self.kinds = [tuple(k) for k in kinds]
+        self.d, self.d_anc = d, d_anc
+        n = len(self.kinds)
+        Ds = (ctypes.c_int * n)(*[k[0] for k in self.kinds])
+        rs = (ctypes.c_int * n)(*[k[1] for k in self.kinds])
+        caps = (ctypes.c_int * n)(*[int(m) for m in max_items])
+        h = _P()
+        st = self.lib.ntu_uneven_init(d, d_anc, sweeps, precision, tau_kmin, tau_kmax, n,
+                                      ctypes.cast(Ds, _P), ctypes.cast(rs, _P),
+                                      ctypes.cast(caps, _P), stream, ctypes.byref(h))
+        if st != 0:
+            raise NTUError(st, self.lib.ntu_uneven_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ntu_uneven_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, items, use_graph: bool = False):
+        """items: list of (D, r, Ta, Tb, G) with complex128 arrays.  Returns
+        (list of Ta', list of Tb', info n x 4)."""
+        n = len(items)
+        index = {k: i for i, k in enumerate(self.kinds)}
+        kind = np.array([index[(it[0], it[1])] for it in items], dtype=np.int32)
+        ta = np.ascontiguousarray(np.concatenate([np.asarray(it[2], np.complex128).ravel() for it in items]))
+        tb = np.ascontiguousarray(np.concatenate([np.asarray(it[3], np.complex128).ravel() for it in items]))
+        gg = np.ascontiguousarray(np.stack([np.asarray(it[4], np.complex128) for it in items]))
+        oa, ob = np.empty_like(ta), np.empty_like(tb)
+        info = np.empty((n, 4))
+        st = self.lib.ntu_uneven_update_host(self.h, n, _ptr(kind), _ptr(ta), _ptr(tb), _ptr(gg),
+                                             _ptr(oa), _ptr(ob), _ptr(info), 1 if use_graph else 0)
+        if st != 0:
+            raise NTUError(st, self.lib.ntu_uneven_last_error(self.h).decode())
+        outs_a, outs_b, o = [], [], 0
+        for it in items:
+            sz = np.asarray(it[2]).size
+            outs_a.append(oa[o:o + sz].reshape(np.asarray(it[2]).shape))
+            outs_b.append(ob[o:o + sz].reshape(np.asarray(it[3]).shape))
+            o += sz
+        return outs_a, outs_b, info

@@ -54,3 +54,17 @@ def test_null_arguments(lib):
     assert lib.ntu_init(None, None, None) == 1
     assert lib.ntu_destroy(None) == 0
     assert lib.ntu_sync(None) == 1
+
+
+def test_uneven_init_rejects_bad_kinds(lib):
+    import ctypes as C
+    D = (C.c_int * 2)(4, 4)
+    r = (C.c_int * 2)(2, 2)
+    cap = (C.c_int * 2)(1, 1)
+    h = C.c_void_p()
+    st = lib.ntu_uneven_init(2, 1, 10, 0, 4, 15, 2, C.cast(D, C.c_void_p), C.cast(r, C.c_void_p),
+                             C.cast(cap, C.c_void_p), None, C.byref(h))
+    assert st == 1 and h.value is None
+    assert b"repeats" in lib.ntu_uneven_last_error(None)
+    assert lib.ntu_uneven_init(2, 1, 10, 0, 4, 15, 0, None, None, None, None, C.byref(h)) == 1
+    assert lib.ntu_uneven_destroy(None) == 0
