@@ -204,6 +204,34 @@ print(json.dumps({{"n": n, "seconds": dt}}))
     return res["n"] / res["seconds"], res["n"], res["seconds"], cores
 
 
+def _oracle_rate_uneven(sweeps, seconds, seed, n_items):
+    """Bond updates/s of the CPU oracle on the first items of the uneven
+    workload (fresh child process, all host cores available to BLAS)."""
+    cores = len(os.sched_getaffinity(0))
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+from oracle import ntu_oracle as O
+from paper_2107_06635_gb300 import inputs as I
+items = I.uneven_batch({seed}, {n_items})
+run = lambda it: O.bond_update(it[2], it[3], it[4], O.Config(D=it[0], r=it[1], sweeps={sweeps}))
+run(items[0])
+t0 = time.perf_counter(); n = 0
+while n < len(items) and (n < 2 or time.perf_counter() - t0 < {seconds}):
+    run(items[n]); n += 1
+print(json.dumps({{"n": n, "seconds": time.perf_counter() - t0}}))
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    return res["n"] / res["seconds"], res["n"], res["seconds"], cores
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -211,9 +239,13 @@ def run_reference(args):
     D, r, sweeps = args.D, args.r, args.sweeps
     times, items = [], 0
     cores = len(os.sched_getaffinity(0))
+    uneven = args.workload == "uneven"
     # one step = a bounded sample of the workload on the host cores
     for i in range(args.warmup + args.steps):
-        rate, n, sec, cores = _oracle_rate(D, r, sweeps, args.ref_seconds, 5 + i, max_items=8)
+        if uneven:
+            rate, n, sec, cores = _oracle_rate_uneven(args.sweeps, args.ref_seconds, 5 + i, 8)
+        else:
+            rate, n, sec, cores = _oracle_rate(D, r, sweeps, args.ref_seconds, 5 + i, max_items=8)
         if i >= args.warmup:
             times.append(sec)
             items += n
@@ -223,10 +255,12 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": workload_config(args, "fp64 oracle (CPU)"),
+        "config": (uneven_config(args, "fp64 oracle (CPU)") if uneven
+                   else workload_config(args, "fp64 oracle (CPU)")),
         "cpu_baseline": {"value": value, "unit": "bond updates/s", "cores": cores,
                          "kind": "oracle",
-                         "sample": f"{items} D={D} bond updates over {args.steps} steps"},
+                         "sample": (f"{items} bond updates of the uneven workload" if uneven else
+                                    f"{items} D={D} bond updates") + f" over {args.steps} steps"},
         "e2e": {"value": value, "unit": "bond updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -239,6 +273,151 @@ def workload_config(args, precision):
             "D": args.D, "d": 2, "r": args.r, "batch_per_gpu": args.batch,
             "sweeps": args.sweeps, "precision": precision, "seed": 5,
             "l2": "flushed (256 MB write) before every timed step"}
+
+
+def uneven_config(args, precision):
+    return {"workload": f"uneven batch: {args.batch} independent NTU bond updates, D uniform in "
+                        f"3..8, r in {{2, 4}} (exp(-i 0.01 ZZ) / exp(-i 0.01 (XX+YY+ZZ))), "
+                        f"complex64 draws, {args.sweeps} ALS sweeps",
+            "batch_per_gpu": args.batch, "sweeps": args.sweeps, "precision": precision,
+            "seed": 5, "l2": "flushed (256 MB write) before every timed step"}
+
+
+def run_uneven(args):
+    """The uneven workload: items grouped by kind (D, r), the kinds' batched
+    updates forked onto one stream per kind and replayed as one CUDA graph;
+    compared with the same grouped enqueue without the graph and with one
+    launch sequence per bond."""
+    import torch
+    from paper_2107_06635_gb300 import ntu
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    B, S = args.batch, args.sweeps
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    items = I.uneven_batch(5 + 1000 * rank, B)
+    kinds = sorted({(it[0], it[1]) for it in items})
+    caps = [sum(1 for it in items if (it[0], it[1]) == k) for k in kinds]
+    prec = {"bf16x3": ntu.NTU_MIXED_BF16X3, "fp32": ntu.NTU_MIXED_FP32,
+            "fp64": ntu.NTU_FP64}[args.precision]
+
+    def timed(ub, mode, steps, warmup):
+        ts, launches = [], 0
+        for i in range(warmup + steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ub.run(mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            if i >= warmup:
+                ts.append(e0.elapsed_time(e1))
+                launches += ub.last_launch_count()
+        ub.sync()
+        return max_over_ranks(statistics.mean(ts)), launches
+
+    def make(p):
+        ub = ntu.UnevenBatch(kinds, caps, sweeps=S, precision=p,
+                             tau_kmax=15 if p == ntu.NTU_FP64 else 8, stream=stream.cuda_stream)
+        ub.stage(items)
+        return ub
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ub = make(prec)
+    ms_graph, launches = timed(ub, ub.GRAPH, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_grouped, _ = timed(ub, ub.GROUPED, args.steps, 1)
+    ms_item, _ = timed(ub, ub.PER_ITEM, max(1, min(args.steps, 2)), 1)
+    _, _, info = ub.fetch(items)
+
+    # end to end through the host call (graph replay, copies in and out)
+    t_e2e = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ub.update(items, use_graph=True)
+        dt = time.perf_counter() - t0
+        barrier()
+        if i >= args.warmup:
+            t_e2e.append(dt)
+    e2e_s = max_over_ranks(statistics.mean(t_e2e))
+    ub.close()
+
+    fp64 = None
+    if not args.no_fp64 and prec != ntu.NTU_FP64:
+        u64 = make(ntu.NTU_FP64)
+        ms64, _ = timed(u64, u64.GRAPH, args.fp64_steps, 1)
+        u64.close()
+        fp64 = {"value": world * B / (ms64 / 1e3), "unit": "bond updates/s", "ms_per_step": ms64}
+    if rank != 0:
+        return
+    value = world * B / (ms_graph / 1e3)
+    env_total = sum(env_flops(it[0], it[1]) for it in items)
+    peaks = measured_peaks()
+    roof = env_roof(args.precision, env_total / (ms_graph / 1e3), peaks)
+    roof["kernel"] = ("whole step: environment flops of every item over the step time "
+                      "(a lower bound on the tensor-core kernels' own rate)")
+    roof["traffic"] = None
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, n, sec, cores = _oracle_rate_uneven(S, args.cpu_seconds, 5, 64)
+        cpu = {"value": rate, "unit": "bond updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"the first {n} bond updates of the uneven workload in {sec:.1f} s "
+                         f"(numpy/BLAS, {cores} threads)"}
+    in_b = sum(it[2].size + it[3].size + it[4].size for it in items) * 16
+    out_b = sum(it[2].size + it[3].size for it in items) * 16 + B * 4 * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": "bond updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "split-bf16 env (fp32 acc) + c128 solvers",
+                  "fp32": "c64 env + c128 solvers", "fp64": "c128"}[args.precision],
+        "data": "synthetic",
+        "config": uneven_config(args, args.precision),
+        "kinds": {f"D{k[0]}r{k[1]}": c for k, c in zip(kinds, caps)},
+        "roofline": roof,
+        "grouped_no_graph": {"value": world * B / (ms_grouped / 1e3), "ms_per_step": ms_grouped},
+        "per_bond_launches": {"value": world * B / (ms_item / 1e3), "ms_per_step": ms_item},
+        "speedup_vs_per_bond": ms_item / ms_graph,
+        "fp64_path": fp64,
+        "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+        "delta_median": float(np.median(info[:, 1])),
+        "e2e": {"value": world * B / e2e_s, "unit": "bond updates/s",
+                "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 # --------------------------------------------------------------- GPU leg
@@ -414,17 +593,26 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=8)
     ap.add_argument("--r", type=int, default=2)
-    ap.add_argument("--batch", type=int, default=456)
-    ap.add_argument("--sweeps", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=None, help="default 456 (uniform), 512 (uneven)")
+    ap.add_argument("--sweeps", type=int, default=None, help="default 10 (uniform), 8 (uneven)")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven"],
+                    help="uniform: the D=8 batch (default); uneven: D in 3..8, r in {2, 4}")
     args = ap.parse_args()
+    uneven = args.workload == "uneven"
+    if args.batch is None:
+        args.batch = 512 if uneven else 456
+    if args.sweeps is None:
+        args.sweeps = 8 if uneven else 10
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -152,8 +152,9 @@ int ntu_batch_update_host(ntu_ctx* ctx, int n, const double* Ta, const double* T
  * Independent bond updates whose bond dimension D and gate rank r differ from
  * item to item (the batch form of the step driver, Sec. II, run over many
  * independent bonds).  An ntu_uneven holds one context per kind (D, r) --
- * each with its own plan and work space, all on one stream -- and pinned
- * host staging.
+ * each with its own plan, work space and stream -- and pinned host staging.
+ * Every call forks the kinds' work from the uneven's stream onto the kind
+ * streams and joins it back, so the kinds run concurrently on the GPU.
  *
  * ntu_uneven_init: n_kinds distinct kinds (D[k], r[k]), at most max_items[k]
  *   items of kind k per call; d_phys, d_anc, als_sweeps, precision, tau_kmin,
@@ -168,18 +169,42 @@ int ntu_batch_update_host(ntu_ctx* ctx, int n, const double* Ta, const double* T
  *   batched update; with use_graph = 1 the device part of the call (copies
  *   in, every kind's update, copies out) is captured as one CUDA graph the
  *   first time a given set of per-kind counts is seen, and replayed by later
- *   calls with the same counts.  Synchronises before return.  Errors:
- *   NTU_EINVAL (unknown kind, more items of a kind than max_items), device
- *   status of any kind as in ntu_sync.
+ *   calls with the same counts.  Synchronises before return; afterwards the
+ *   items count as staged (below).  Errors: NTU_EINVAL (unknown kind, more
+ *   items of a kind than max_items), device status of any kind as in
+ *   ntu_sync.
+ * ntu_uneven_stage: copy n items (same layout) to the device and keep them
+ *   there as the staged items; synchronises.
+ * ntu_uneven_run: enqueue the update of the staged items on the uneven's
+ *   stream and return without synchronising; results stay on the device.
+ *   mode NTU_UNEVEN_GROUPED: one batched update per kind; NTU_UNEVEN_GRAPH:
+ *   the same captured as a CUDA graph on first use for the staged per-kind
+ *   counts and replayed afterwards; NTU_UNEVEN_PER_ITEM: one update launch
+ *   sequence per item (the per-bond form, for comparison).  All modes give
+ *   the same results.  Errors: NTU_EINVAL (mode).
+ * ntu_uneven_sync: wait for the uneven's stream; device status of every kind
+ *   with staged items, as in ntu_sync.
+ * ntu_uneven_fetch: copy the results of the staged items back (kind[] must
+ *   give the staged per-kind counts, else NTU_ESTATE); synchronises.
+ * ntu_uneven_last_launch_count: kernels launched by the last update or run
+ *   (for a graph replay: the kernels of the graph).
  * ntu_uneven_last_error: description of the last failure (uneven == NULL:
  *   of the last failed ntu_uneven_init). */
 typedef struct ntu_uneven ntu_uneven;
+enum { NTU_UNEVEN_GROUPED = 0, NTU_UNEVEN_GRAPH = 1, NTU_UNEVEN_PER_ITEM = 2 };
 int ntu_uneven_init(int d_phys, int d_anc, int als_sweeps, int precision, int tau_kmin,
                     int tau_kmax, int n_kinds, const int* D, const int* r, const int* max_items,
                     void* stream, ntu_uneven** out);
 int ntu_uneven_update_host(ntu_uneven* uneven, int n, const int* kind, const double* Ta,
                            const double* Tb, const double* gates, double* Ta_out,
                            double* Tb_out, double* info, int use_graph);
+int ntu_uneven_stage(ntu_uneven* uneven, int n, const int* kind, const double* Ta,
+                     const double* Tb, const double* gates);
+int ntu_uneven_run(ntu_uneven* uneven, int mode);
+int ntu_uneven_sync(ntu_uneven* uneven);
+int ntu_uneven_fetch(ntu_uneven* uneven, int n, const int* kind, double* Ta_out,
+                     double* Tb_out, double* info);
+int ntu_uneven_last_launch_count(const ntu_uneven* uneven);
 int ntu_uneven_destroy(ntu_uneven* uneven);
 const char* ntu_uneven_last_error(const ntu_uneven* uneven);
 

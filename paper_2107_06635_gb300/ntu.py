@@ -65,6 +65,11 @@ _SIGS = {
     "ntu_gate_qr_noalloc": [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P],
     "ntu_uneven_init": [_I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_P)],
     "ntu_uneven_update_host": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I],
+    "ntu_uneven_stage": [_P, _I, _P, _P, _P, _P],
+    "ntu_uneven_run": [_P, _I],
+    "ntu_uneven_sync": [_P],
+    "ntu_uneven_fetch": [_P, _I, _P, _P, _P, _P],
+    "ntu_uneven_last_launch_count": [_P],
     "ntu_uneven_destroy": [_P],
     "ntu_uneven_last_error": [_P],
 }
@@ -271,7 +276,8 @@ class Context:
 
 class UnevenBatch:
     """Independent bond updates of different (D, r) in one call: one context
-    per kind on a shared stream; optionally replayed as one CUDA graph."""
+    and stream per kind, forked from and joined back into one stream;
+    optionally replayed as one CUDA graph."""
 
     def __init__(self, kinds, max_items, d: int = 2, d_anc: int = 1, sweeps: int = 10,
                  precision: int = NTU_FP64, tau_kmin: int = 4, tau_kmax: int = 15, stream=None):
@@ -301,25 +307,63 @@ class UnevenBatch:
         except Exception:
             pass
 
-    def update(self, items, use_graph: bool = False):
-        """items: list of (D, r, Ta, Tb, G) with complex128 arrays.  Returns
-        (list of Ta', list of Tb', info n x 4)."""
-        n = len(items)
+    GROUPED, GRAPH, PER_ITEM = 0, 1, 2
+
+    def _ck(self, st):
+        if st != 0:
+            raise NTUError(st, self.lib.ntu_uneven_last_error(self.h).decode())
+
+    def _pack(self, items):
         index = {k: i for i, k in enumerate(self.kinds)}
         kind = np.array([index[(it[0], it[1])] for it in items], dtype=np.int32)
         ta = np.ascontiguousarray(np.concatenate([np.asarray(it[2], np.complex128).ravel() for it in items]))
         tb = np.ascontiguousarray(np.concatenate([np.asarray(it[3], np.complex128).ravel() for it in items]))
         gg = np.ascontiguousarray(np.stack([np.asarray(it[4], np.complex128) for it in items]))
-        oa, ob = np.empty_like(ta), np.empty_like(tb)
-        info = np.empty((n, 4))
-        st = self.lib.ntu_uneven_update_host(self.h, n, _ptr(kind), _ptr(ta), _ptr(tb), _ptr(gg),
-                                             _ptr(oa), _ptr(ob), _ptr(info), 1 if use_graph else 0)
-        if st != 0:
-            raise NTUError(st, self.lib.ntu_uneven_last_error(self.h).decode())
+        return kind, ta, tb, gg
+
+    @staticmethod
+    def _unpack(items, oa, ob):
         outs_a, outs_b, o = [], [], 0
         for it in items:
             sz = np.asarray(it[2]).size
             outs_a.append(oa[o:o + sz].reshape(np.asarray(it[2]).shape))
             outs_b.append(ob[o:o + sz].reshape(np.asarray(it[3]).shape))
             o += sz
-        return outs_a, outs_b, info
+        return outs_a, outs_b
+
+    def update(self, items, use_graph: bool = False):
+        """items: list of (D, r, Ta, Tb, G) with complex128 arrays.  Returns
+        (list of Ta', list of Tb', info n x 4)."""
+        n = len(items)
+        kind, ta, tb, gg = self._pack(items)
+        oa, ob = np.empty_like(ta), np.empty_like(tb)
+        info = np.empty((n, 4))
+        self._ck(self.lib.ntu_uneven_update_host(self.h, n, _ptr(kind), _ptr(ta), _ptr(tb), _ptr(gg),
+                                                 _ptr(oa), _ptr(ob), _ptr(info), 1 if use_graph else 0))
+        return (*self._unpack(items, oa, ob), info)
+
+    def stage(self, items):
+        """Copy the items to the device; they stay there for run()."""
+        kind, ta, tb, gg = self._pack(items)
+        self._ck(self.lib.ntu_uneven_stage(self.h, len(items), _ptr(kind), _ptr(ta), _ptr(tb),
+                                           _ptr(gg)))
+
+    def run(self, mode: int = 0):
+        """Enqueue the update of the staged items (GROUPED, GRAPH or
+        PER_ITEM); asynchronous."""
+        self._ck(self.lib.ntu_uneven_run(self.h, mode))
+
+    def sync(self):
+        self._ck(self.lib.ntu_uneven_sync(self.h))
+
+    def fetch(self, items):
+        """Results of the staged items (the same list that was staged)."""
+        kind, ta, tb, _ = self._pack(items)
+        oa, ob = np.empty_like(ta), np.empty_like(tb)
+        info = np.empty((len(items), 4))
+        self._ck(self.lib.ntu_uneven_fetch(self.h, len(items), _ptr(kind), _ptr(oa), _ptr(ob),
+                                           _ptr(info)))
+        return (*self._unpack(items, oa, ob), info)
+
+    def last_launch_count(self) -> int:
+        return self.lib.ntu_uneven_last_launch_count(self.h)

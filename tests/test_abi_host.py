@@ -68,3 +68,10 @@ def test_uneven_init_rejects_bad_kinds(lib):
     assert b"repeats" in lib.ntu_uneven_last_error(None)
     assert lib.ntu_uneven_init(2, 1, 10, 0, 4, 15, 0, None, None, None, None, C.byref(h)) == 1
     assert lib.ntu_uneven_destroy(None) == 0
+    # every uneven call rejects a NULL handle without touching a device
+    assert lib.ntu_uneven_stage(None, 0, None, None, None, None) == 1
+    assert lib.ntu_uneven_run(None, 0) == 1
+    assert lib.ntu_uneven_sync(None) == 1
+    assert lib.ntu_uneven_fetch(None, 0, None, None, None, None) == 1
+    assert lib.ntu_uneven_update_host(None, 0, None, None, None, None, None, None, None, 0) == 1
+    assert lib.ntu_uneven_last_launch_count(None) == 0

@@ -566,34 +566,84 @@ def test_measure_matches_oracle():
 
 
 # ------------------------------------------------------------- uneven batches
-def test_uneven_batch_matches_oracle_and_graph_replay():
-    """Mixed (D, r) items in one call: every item against the oracle's bond
-    update (FP64 context: tensors 1e-9, delta 1e-8); a kind with no items in
-    the call is skipped; the CUDA-graph replay gives bit-identical results on
-    two consecutive calls and agrees bit for bit with the direct enqueue."""
+@pytest.mark.parametrize("D,precision", [(7, 0), (8, 0), (8, 2)])
+def test_batch_update_r4_large_bond(D, precision):
+    """r=4 gates at D=7, 8: K = D r = 28, 32 (the largest bond the library
+    takes), g of size K^2 = 784, 1024 and reduced metrics of n_A = 196, 256;
+    the Heisenberg gate exp(-i 0.01 (XX+YY+ZZ)) has rank 4."""
+    n = 2
+    rng = np.random.default_rng(900 + D)
+    Ta = np.stack([I.random_site_tensor(rng, 2, D) for _ in range(n)])
+    Tb = np.stack([I.random_site_tensor(rng, 2, D) for _ in range(n)])
+    G = np.stack([I.heisenberg_gate(0.01)] * n)
+    ctx = _ctx(D, 4, sweeps=8, precision=precision, max_batch=n, kmax=15 if precision == 0 else 8)
+    Ta_o, Tb_o, info = ctx.batch_update_host(Ta, Tb, G)
+    cfg = O.Config(D=D, r=4, sweeps=8, tau_exponents=tuple(range(4, 16 if precision == 0 else 9)))
+    for i in range(n):
+        A2, B2, inf = O.bond_update(Ta[i], Tb[i], G[i], cfg)
+        if precision == 0:
+            assert _rel(Ta_o[i], A2) < 1e-9
+            assert _rel(Tb_o[i], B2) < 1e-9
+            assert abs(info[i, 1] - inf.delta) < 1e-8
+        else:
+            assert abs(info[i, 1] - inf.delta) <= 1e-2 * inf.delta
+            pair = np.einsum("plurn,qrvwx->plunqvwx", Ta_o[i], Tb_o[i])
+            ref = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
+            assert _rel(pair, ref) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_uneven_batch_matches_oracle_and_modes_agree(precision):
+    """The uneven workload (D uniform in 3..8, r in {2, 4}, complex64 draws,
+    8 sweeps) in one call: every item against the oracle's bond update (FP64
+    context: tensors 1e-9, delta 1e-8; split-BF16 context: delta 1e-2
+    relative, the two-site state 1e-4); a kind with no items in the call is
+    skipped.  Direct enqueue, CUDA-graph replay (twice, and after the counts
+    change), the staged device-resident run in all three modes (grouped,
+    graph, one launch sequence per item) give bit-identical results."""
     from paper_2107_06635_gb300 import ntu
-    items = [it for it in I.uneven_batch(41, 40) if it[0] <= 6][:8]
-    kinds = sorted({(it[0], it[1]) for it in items}) + [(7, 2)]
+    items = I.uneven_batch(41, 14)
+    kinds = sorted({(it[0], it[1]) for it in items})
+    unused = next((D, r) for D in range(3, 9) for r in (2, 4) if (D, r) not in kinds)
+    kinds.append(unused)
     caps = [sum(1 for it in items if (it[0], it[1]) == k) or 1 for k in kinds]
-    ub = ntu.UnevenBatch(kinds, caps, sweeps=10)
+    kmax = 15 if precision == 0 else 8
+    ub = ntu.UnevenBatch(kinds, caps, sweeps=8, precision=precision, tau_kmax=kmax)
     try:
         oa, ob, info = ub.update(items, use_graph=False)
         for i, (D, r, ta, tb, g) in enumerate(items):
-            A2, B2, inf = O.bond_update(ta, tb, g, O.Config(D=D, r=r, sweeps=10))
-            assert _rel(oa[i], A2) < 1e-9, (i, D, r)
-            assert _rel(ob[i], B2) < 1e-9, (i, D, r)
-            assert abs(info[i, 1] - inf.delta) < 1e-8, (i, D, r)
-        ga, gb, gi = ub.update(items, use_graph=True)
-        ha, hb, hi = ub.update(items, use_graph=True)
-        for i in range(len(items)):
-            assert np.array_equal(ga[i], oa[i]) and np.array_equal(ha[i], oa[i])
-            assert np.array_equal(gb[i], ob[i]) and np.array_equal(hb[i], ob[i])
-        assert np.array_equal(gi, info) and np.array_equal(hi, info)
-        # other per-kind counts: the graph is captured again
-        sub = items[:3]
+            cfg = O.Config(D=D, r=r, sweeps=8, tau_exponents=tuple(range(4, kmax + 1)))
+            A2, B2, inf = O.bond_update(ta, tb, g, cfg)
+            if precision == 0:
+                assert _rel(oa[i], A2) < 1e-9, (i, D, r)
+                assert _rel(ob[i], B2) < 1e-9, (i, D, r)
+                assert abs(info[i, 1] - inf.delta) < 1e-8, (i, D, r)
+            else:
+                assert abs(info[i, 1] - inf.delta) <= 1e-2 * inf.delta, (i, D, r)
+                pair = np.einsum("plurn,qrvwx->plunqvwx", oa[i], ob[i])
+                ref = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
+                assert _rel(pair, ref) < 1e-4, (i, D, r)
+
+        def same(res):
+            a, b, inf = res
+            assert np.array_equal(inf, info)
+            for i in range(len(items)):
+                assert np.array_equal(a[i], oa[i]) and np.array_equal(b[i], ob[i])
+
+        same(ub.update(items, use_graph=True))
+        same(ub.update(items, use_graph=True))
+        sub = items[:3]                       # other per-kind counts: captured again
         sa, sb, si = ub.update(sub, use_graph=True)
         for i in range(3):
             assert np.array_equal(sa[i], oa[i]) and np.array_equal(sb[i], ob[i])
+        ub.stage(items)
+        for mode in (ub.GROUPED, ub.GRAPH, ub.GRAPH, ub.PER_ITEM):
+            ub.run(mode)
+            ub.sync()
+            assert ub.last_launch_count() > 0
+            same(ub.fetch(items))
+        with pytest.raises(ntu.NTUError):
+            ub.fetch(sub)                     # counts differ from the staged items
         with pytest.raises(ntu.NTUError):
             ub.update(items + items, use_graph=False)      # beyond max_items
     finally:
