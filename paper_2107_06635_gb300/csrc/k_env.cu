@@ -117,7 +117,11 @@ k_cgemm(GemmArgs g, const C2* __restrict__ A, const C2* __restrict__ B, C2* __re
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
           int n = n0 + tx + j * (BN / TN);
-          if (n < g.N)
+          if (n >= g.N) continue;
+          if (g.mode == 3)
+            store_split_planar(ob, rc + g.colC[n], rk + g.colK[n], g.pitch, g.krp_out,
+                               (float)acc[i][j].x, (float)acc[i][j].y);
+          else
             store_split(ob, rc + g.colC[n], rk + g.colK[n], g.pitch, g.krp_out,
                         (float)acc[i][j].x, (float)acc[i][j].y, g.mode == 2);
         }
@@ -150,6 +154,54 @@ static cudaError_t run_gemm(ntu_ctx* c, const GemmOp& op, int n, const void* A, 
   k_cgemm<C2, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, c->stream>>>(
       a, (const C2*)A, (const C2*)B, (C2*)C);
   return after_launch(c, "k_cgemm");
+}
+
+// Gram matrix of one leg (the side edges E_L, E_R of Fig. 4(b)): for every
+// item E[rowC[x] + colC[x']] = sum_k T[rowA[x] + kA[k]] conj(T[kA[k] + rowA[x']])
+// with at most 64 pairs (x, x').  A 64 x 64 GEMM tile would leave almost every
+// thread idle over the long contraction (dp D^3 terms); here thread (pair,
+// group) sums every fourth term of one pair and the four groups are added in
+// shared memory, one CTA per item.
+template <typename C2>
+__global__ void __launch_bounds__(256) k_gram(int D, int Kd, const int* __restrict__ rowA,
+                                              const int* __restrict__ kA,
+                                              const int* __restrict__ rowC,
+                                              const int* __restrict__ colC, long long sT,
+                                              long long sE, const C2* __restrict__ T,
+                                              C2* __restrict__ E) {
+  typedef typename CplxT<C2>::R R;
+  __shared__ R red[2][4][64];
+  const int tid = threadIdx.x, pr = tid & 63, grp = tid >> 6;
+  const C2* Ti = T + (long long)blockIdx.x * sT;
+  R re = 0, im = 0;
+  if (pr < D * D) {
+    const C2* tx = Ti + rowA[pr / D];
+    const C2* ty = Ti + rowA[pr % D];
+#pragma unroll 4
+    for (int k = grp; k < Kd; k += 4) {
+      const int o = kA[k];
+      const C2 a = tx[o], b = ty[o];
+      re = fma(a.x, b.x, fma(a.y, b.y, re));
+      im = fma(a.y, b.x, fma(-a.x, b.y, im));
+    }
+  }
+  red[0][grp][pr] = re;
+  red[1][grp][pr] = im;
+  __syncthreads();
+  if (grp == 0 && pr < D * D) {
+    const R sr = (red[0][0][pr] + red[0][1][pr]) + (red[0][2][pr] + red[0][3][pr]);
+    const R si = (red[1][0][pr] + red[1][1][pr]) + (red[1][2][pr] + red[1][3][pr]);
+    E[(long long)blockIdx.x * sE + rowC[pr / D] + colC[pr % D]] = CplxT<C2>::mk(sr, si);
+  }
+}
+
+template <typename C2>
+static cudaError_t run_gram(ntu_ctx* c, const GemmOp& op, int n, const void* T, void* E) {
+  if (n == 0) return cudaSuccess;
+  const int* t = c->plan.d_tab;
+  k_gram<C2><<<n, 256, 0, c->stream>>>(op.M, op.Kd, t + op.rowA, t + op.kA, t + op.rowC,
+                                       t + op.colC, op.sA, op.sC, (const C2*)T, (C2*)E);
+  return after_launch(c, "k_gram");
 }
 
 // --------------------------------------------------------------- plan
@@ -307,6 +359,13 @@ int plan_build(ntu_ctx* c) {
     P.e2BL = as_split(P.eBL, 2, P.rowsE * pE, pE, (int)P.krpE);
     P.e2TR = as_split(P.eTR, 2, P.rowsE * pE, pE, (int)P.krpE);
     P.e2BR = as_split(P.eBR, 2, P.rowsE * pE, pE, (int)P.krpE);
+    // the bottom edges are the A operands of h, whose B operand (T2 from
+    // k_t12) has complex column (n', n) with Re and Im planar: K index
+    // y' * D + y, mode 3
+    const int ebK = T.add({{D, 0}, {D, 1}}), ebKc = T.add({{D, 0}, {D, D}});
+    for (GemmOp* o : {&P.e2BL, &P.e2BR}) {
+      o->rowK = ebK; o->colK = ebKc; o->mode = 3;
+    }
     // The composite column indices below are ordered so that each producer's
     // fastest column index is the consumer's K index: the split stores then
     // run along rows (coalesced) instead of across them.
@@ -314,7 +373,8 @@ int plan_build(ntu_ctx* c) {
     // k*64 + u*D + n (64 rows per k, padding rows zero) and complex column
     // (p,e'); conj(Q) as the B operand with row k'*64 + u'*D + n' and column
     // (p,e') (written by k_q_split); the result goes to T2s, the B operand of
-    // h: row (k,k',ht,ht'), complex column (n,n').
+    // h: row (k,k',ht,ht'), complex column (n',n), Re at column c and Im at
+    // krpE/2 + c of each half (planar).
     P.krpY = up(2LL * dp * D, 64);
     P.rowsY = 128LL * K;
     P.rowsQ = 64LL * K;
@@ -426,10 +486,10 @@ static cudaError_t env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, 
                       const void* QB, void* graw) {
   const Plan& P = c->plan;
   Work& W = c->w;
-  RG(run_gemm<C2>(c, P.eL, n, Tb, Tb, W.EL));
+  RG(run_gram<C2>(c, P.eL, n, Tb, W.EL));
   RG(run_gemm<C2>(c, P.eTL, n, Tb, Tb, W.ETL));
   RG(run_gemm<C2>(c, P.eBL, n, Tb, Tb, W.EBL));
-  RG(run_gemm<C2>(c, P.eR, n, Ta, Ta, W.ER));
+  RG(run_gram<C2>(c, P.eR, n, Ta, W.ER));
   RG(run_gemm<C2>(c, P.eTR, n, Ta, Ta, W.ETR));
   RG(run_gemm<C2>(c, P.eBR, n, Ta, Ta, W.EBR));
   // left half: Q_A with E_L, E_TL, E_BL
@@ -508,8 +568,8 @@ static cudaError_t env_chain_bf16x3(ntu_ctx* c, int n, const void* Ta, const voi
                                     const void* QA, const void* QB, void* graw) {
   const Plan& P = c->plan;
   Work& W = c->w;
-  RG(run_gemm<float2>(c, P.eL, n, Tb, Tb, W.EL));
-  RG(run_gemm<float2>(c, P.eR, n, Ta, Ta, W.ER));
+  RG(run_gram<float2>(c, P.eL, n, Tb, W.EL));
+  RG(run_gram<float2>(c, P.eR, n, Ta, W.ER));
   RG(run_gemm<float2>(c, P.e2TL, n, Tb, Tb, W.ETLd));
   RG(run_gemm<float2>(c, P.e2BL, n, Tb, Tb, W.EBLd));
   RG(run_gemm<float2>(c, P.e2TR, n, Ta, Ta, W.ETRd));

@@ -9,7 +9,8 @@
 // result is split into BF16 hi/lo and written by the epilogue warps straight
 // into shared memory as the (128-byte swizzled, K-major) B operand of the
 // second, so T1 never leaves the SM; only T2 goes to HBM, as the split B
-// operand of h (rows (k,k',ht,ht'), complex columns (n,n')).
+// operand of h (rows (k,k',ht,ht'), complex columns (n',n) with the real
+// parts of a row's columns first and the imaginary parts krpE/2 later).
 //
 // Complex products are real GEMMs as in k_tc.cu: A doubled (Re / Im rows 64
 // apart in a 128-row tile), B interleaved (re, im) along K, three split
@@ -20,8 +21,10 @@
 // conj(Q) block per unit, double-buffered), warp 1 issues the MMAs (GEMM1 of
 // unit i, then GEMM2 of unit i-1), warps 2-9 turn accumulator 1 into the B
 // operand of GEMM2 (two buffers), warps 10-17 turn accumulator 2 into output
-// rows through a shared staging block.  Every wait is bounded; every role
-// leaves its loop on a timeout and the epilogue groups leave together.
+// rows: each thread owns one row and sixteen consecutive columns, which the
+// planar layout makes 32 contiguous bytes of hi and of lo, stored from
+// registers.  Every wait is bounded; every role leaves its loop on a timeout
+// and the epilogue groups leave together.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -34,7 +37,6 @@ namespace ntu {
 
 namespace {
 constexpr int EPI = 256;                       // threads of each epilogue group
-static_assert(EPI % 128 == 0 && EPI % 64 == 0, "copy-out: krpE (64 or 128) must divide EPI");
 constexpr int T12_THREADS = 64 + 2 * EPI;
 constexpr long long T12_WAIT = 1ll << 28;
 constexpr int T12_SLEEP_POLLS = 1 << 17;       // x <= 20 us: about 2.6 s
@@ -44,10 +46,7 @@ constexpr int OFF_A2 = 0;                     // 4 A tiles: E_top hi0, hi1, lo0,
 constexpr int OFF_A1 = OFF_A2 + 4 * A_TILE;   // 2 A tiles: Y hi, lo
 constexpr int OFF_B1 = OFF_A1 + 2 * A_TILE;   // 2 buffers x 2 B tiles: conj(Q) hi, lo
 constexpr int OFF_B2 = OFF_B1 + 4 * B_TILE;   // 2 buffers x 4 B tiles: T1 hi0, hi1, lo0, lo1
-constexpr int OFF_OUT = OFF_B2 + 8 * B_TILE;  // output staging, 64 rows x (256 + 2) BF16
-constexpr int OUT_PITCH = 256 + 2;            // odd word count: conflict-free column stores
-constexpr int OUT_BYTES = 64 * OUT_PITCH * 2 + 16 * 16;
-constexpr int OFF_BAR = OFF_OUT + OUT_BYTES;
+constexpr int OFF_BAR = OFF_B2 + 8 * B_TILE;
 constexpr size_t T12_SMEM = (size_t)OFF_BAR + 512 + 1024;
 static_assert(T12_SMEM <= 227 * 1024, "shared memory budget");
 
@@ -96,9 +95,9 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
   // contiguous range of units for this CTA
   const long long u0 = a.units * blockIdx.x / gridDim.x;
   const long long u1 = a.units * (blockIdx.x + 1) / gridDim.x;
-  // padding of the generated operand and of the staging block must read as
-  // zero: clear both once (generic stores, then a proxy fence)
-  for (int i = tid; i < (8 * B_TILE + OUT_BYTES) / 16; i += T12_THREADS)
+  // padding of the generated operand must read as zero: clear it once
+  // (generic stores, then a proxy fence)
+  for (int i = tid; i < 8 * B_TILE / 16; i += T12_THREADS)
     reinterpret_cast<uint4*>(sm + OFF_B2)[i] = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async();
   if (tid == 0) {
@@ -322,15 +321,17 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       if (et == 0) tc::mbar_arrive(&b2_full[b]);
     }
   } else {
-    // ---- epilogue 2: accumulator 2 (rows (ht,ht') Re / Im, columns j =
-    // n' * D + n) -> staging rows of the split T2 operand (complex column
-    // n * D + n') -> contiguous HBM rows
+    // ---- epilogue 2: accumulator 2 (rows (ht,ht') Re / Im, columns
+    // j = n' * D + n) -> row (k,k',ht,ht') of the split T2 operand: hi at
+    // column j (Re) or krpE/2 + j (Im), lo krpE further.  Accumulator
+    // columns j >= D^2 are exact zeros (zero rows of the B operand), so a
+    // sixteen-column group that starts below D^2 is stored whole.
     const int et = tid - 64 - EPI, quarter = warp & 3, row = quarter * 32 + lane;
     const int cs = ((warp - 2 - EPI / 32) >> 2) * 32;
     const int r = row & 63, im = row >> 6;
     const bool rv = r < D2;
-    const int pitch = 2 * a.krpE;             // output row (BF16)
-    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(sm + OFF_OUT);
+    const long long pitch = 2LL * a.krpE;
+    const int coff = im * (a.krpE / 2);
     long long i = 0;
     for (long long u = u0; u < u1; ++u, ++i) {
       const int z = (int)(u / KK), kk = (int)(u % KK);
@@ -343,55 +344,34 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
         break;
       }
       tc::fence_after_sync();
-      if (DT == 8) {
-        // column j = n' * 8 + n -> complex column n * 8 + n'; krpE = 128
-        __nv_bfloat16* sr = stg + r * OUT_PITCH + im;
+      __nv_bfloat16* orow = a.out + (long long)z * a.sOut + ((long long)kk * D2 + r) * pitch + coff;
 #pragma unroll
-        for (int c0 = cs; c0 < cs + 32; c0 += 16) {
+      for (int c0 = cs; c0 < cs + 32; c0 += 16) {
+        if (DT == 8 || c0 < D2) {                 // uniform over the warp
           float v[16];
           tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(128 + b * 64 + c0), v);
+          if (rv) {
+            uint32_t hw[8], lw[8];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int c = c0 + q, col = (c & 7) * 8 + (c >> 3);
-            __nv_bfloat16 h, l;
-            split_bf16(v[q], h, l);
-            sr[2 * col] = h;
-            sr[128 + 2 * col] = l;
-          }
-        }
-      } else
-#pragma unroll 1
-      for (int c0 = cs; c0 < cs + 32; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(128 + b * 64 + c0), v);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int c = c0 + q;
-          if (rv && c < D2) {
-            const int col = (c % D) * D + c / D;
-            __nv_bfloat16 h, l;
-            split_bf16(v[q], h, l);
-            stg[r * OUT_PITCH + 2 * col + im] = h;
-            stg[r * OUT_PITCH + a.krpE + 2 * col + im] = l;
+            for (int q = 0; q < 8; ++q) {
+              __nv_bfloat16 h0, l0, h1, l1;
+              split_bf16(v[2 * q], h0, l0);
+              split_bf16(v[2 * q + 1], h1, l1);
+              hw[q] = pack_bf16(h0, h1);
+              lw[q] = pack_bf16(l0, l1);
+            }
+            uint4* ph = reinterpret_cast<uint4*>(orow + c0);
+            uint4* pl = reinterpret_cast<uint4*>(orow + a.krpE + c0);
+            ph[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            ph[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+            pl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            pl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
           }
         }
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&c2_empty[b]);
-      tc::bar_sync(2, EPI);
-      // rows (k,k',ht,ht') of this unit are contiguous in the output
-      // staging rows are OUT_PITCH BF16 (an odd number of words) apart,
-      // output rows pitch apart: word-wide copies, consecutive threads on
-      // consecutive words (conflict-free reads, coalesced writes)
-      const int wpr = pitch / 2;                // 4-byte words per row
-      uint32_t* dst = reinterpret_cast<uint32_t*>(
-          a.out + (long long)z * a.sOut + (long long)kk * D2 * pitch);
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(sm + OFF_OUT);
-      const int w = et % wpr, rstep = EPI / wpr;    // wpr = krpE divides EPI
-      for (int rr = et / wpr; rr < D2; rr += rstep)
-        dst[(size_t)rr * wpr + w] = src[rr * (OUT_PITCH / 2) + w];
-      tc::bar_sync(2, EPI);
     }
   }
   tc::fence_before_sync();

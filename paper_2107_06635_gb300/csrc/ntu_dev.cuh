@@ -122,6 +122,22 @@ __device__ __forceinline__ void store_split4(__nv_bfloat16* base, long long r, l
                    pack_bf16(il[3], rl[3]));
   }
 }
+// Doubled A operand with planar K: complex column kc of a real row pair
+// puts its real-part factor at K position kc and its imaginary-part factor at
+// krp/2 + kc (the B operand then holds Re at kc and Im at krp/2 + kc).  The
+// row pair receives (re, -im) and (im, re) as in store_split.
+__device__ __forceinline__ void store_split_planar(__nv_bfloat16* base, long long r, long long kc,
+                                                   int pitch, int krp, float re, float im) {
+  __nv_bfloat16 h0, l0, h1, l1;
+  split_bf16(re, h0, l0);
+  split_bf16(im, h1, l1);
+  __nv_bfloat16* pr = base + ((r / 64) * 128 + (r % 64)) * pitch + kc;
+  __nv_bfloat16* pi = pr + 64LL * pitch;
+  const int half = krp / 2;
+  pr[0] = h0; pr[half] = __hneg(h1); pr[krp] = l0; pr[krp + half] = __hneg(l1);
+  pi[0] = h1; pi[half] = h0; pi[krp] = l1; pi[krp + half] = l0;
+}
+
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
 // a / b by Smith's method (no squares of b, so no underflow or overflow for

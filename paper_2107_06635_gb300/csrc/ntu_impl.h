@@ -15,10 +15,11 @@ namespace ntu {
 //   C[b][rowC[m] + colC[n]] = sum_k A[b][rowA[m] + kA[k]] * B[b][kB[k] + colB[n]]
 // with optional conjugation of A or B.  The six index tables map the
 // composite tensor indices to element offsets; they live in one device int
-// array at the given offsets.  mode 1 / 2 (FP32 path only) write the result
-// instead as the split-BF16 operand of a tensor-core GEMM (see k_tc.cu):
-// row rowC[m] + colC[n], complex column rowK[m] + colK[n], row pitch
-// `pitch` BF16 elements, lo half at +krp_out; mode 2 doubles the rows.
+// array at the given offsets.  mode 1 / 2 / 3 (FP32 path only) write the
+// result instead as the split-BF16 operand of a tensor-core GEMM (see
+// k_tc.cu): row rowC[m] + colC[n], complex column rowK[m] + colK[n], row
+// pitch `pitch` BF16 elements, lo half at +krp_out; mode 2 doubles the rows;
+// mode 3 doubles them with Re / Im factors planar in K (krp_out / 2 apart).
 struct GemmOp {
   int M, N, Kd;
   int rowA, kA, kB, colB, rowC, colC;   // offsets into the table array
