@@ -83,7 +83,9 @@ typedef struct {
 
 /* Create a context for one (D, d, r) configuration.  `stream` is a
  * cudaStream_t (NULL: the context creates its own non-blocking stream).
- * Requires d_p * D^2 >= r so that the gated site matrix has at least K rows.
+ * Requires d_p * D^2 >= r so that the gated site matrix has at least K rows,
+ * and D * r <= 32.  NTU_MIXED_BF16X3 needs a compute capability 10.x GPU and
+ * 2 * d_p * D <= 64 (else NTU_EUNSUPPORTED, before any device work).
  * Allocates all device memory the calls below need for up to max_batch items. */
 int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out);
 int ntu_destroy(ntu_ctx* ctx);

@@ -195,6 +195,12 @@ extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
   if (f.tau_kmin < 0 || f.tau_kmax > 20 || f.tau_kmin > f.tau_kmax)
     return fail(nullptr, NTU_EINVAL, "tau_kmin=%d tau_kmax=%d", f.tau_kmin, f.tau_kmax);
   if (f.max_batch < 1 || f.max_batch > 65535) return fail(nullptr, NTU_EINVAL, "max_batch=%d", f.max_batch);
+  // the fused t1-t2 of the split-BF16 environment holds one 64-wide K tile
+  // of Y and conj(Q): 2 d_p D real columns at most
+  if (f.precision == NTU_MIXED_BF16X3 && 2 * f.d_phys * f.d_anc * f.D > 64)
+    return fail(nullptr, NTU_EUNSUPPORTED,
+                "NTU_MIXED_BF16X3 needs 2*d_phys*d_anc*D <= 64 (got %d); use NTU_MIXED_FP32",
+                2 * f.d_phys * f.d_anc * f.D);
   ntu_ctx* c = new (std::nothrow) ntu_ctx();
   if (!c) return fail(nullptr, NTU_ENOMEM, "host allocation");
   memset(c, 0, sizeof(*c));

@@ -361,17 +361,20 @@ int plan_build(ntu_ctx* c) {
     P.e2BR = as_split(P.eBR, 2, P.rowsE * pE, pE, (int)P.krpE);
     // the bottom edges are the A operands of h, whose B operand (T2 from
     // k_t12) has complex column (n', n) with Re and Im planar: K index
-    // y' * D + y, mode 3
+    // y' * D + y, mode 3; the top edges are the A operands of GEMM2 inside
+    // k_t12, whose B operand has K (u, u') planar: mode 3, K order kept
     const int ebK = T.add({{D, 0}, {D, 1}}), ebKc = T.add({{D, 0}, {D, D}});
     for (GemmOp* o : {&P.e2BL, &P.e2BR}) {
       o->rowK = ebK; o->colK = ebKc; o->mode = 3;
     }
+    P.e2TL.mode = 3;
+    P.e2TR.mode = 3;
     // The composite column indices below are ordered so that each producer's
     // fastest column index is the consumer's K index: the split stores then
     // run along rows (coalesced) instead of across them.
     // Fused t1-t2 (k_t12.cu): Y as the doubled A operand with complex row
     // k*64 + u*D + n (64 rows per k, padding rows zero) and complex column
-    // (p,e'); conj(Q) as the B operand with row k'*64 + u'*D + n' and column
+    // (p,e'); conj(Q) as the B operand with row k'*64 + n'*D + u' and column
     // (p,e') (written by k_q_split); the result goes to T2s, the B operand of
     // h: row (k,k',ht,ht'), complex column (n',n), Re at column c and Im at
     // krpE/2 + c of each half (planar).
@@ -509,7 +512,7 @@ static cudaError_t env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, 
 // Tensor maps of the split operands (the work space is fixed at init, so
 // the maps are encoded once).
 // conj(Q) as the split B operand of the fused t1-t2: Q[p,e,u,n,k] goes to
-// row k*64 + u*D + n, complex column p*D + e.
+// row k*64 + n*D + u, complex column p*D + e.
 __global__ void k_q_split(long long total, int D, int K, const float2* __restrict__ Q,
                           __nv_bfloat16* __restrict__ Qs, long long szQ, long long sOut,
                           int pitch, int krp) {
@@ -523,7 +526,7 @@ __global__ void k_q_split(long long total, int D, int K, const float2* __restric
     const int e = (int)(r % D);
     const int p = (int)(r / D);
     const float2 v = Q[i];
-    store_split(Qs + item * sOut, (long long)k * 64 + u * D + n, (long long)p * D + e, pitch,
+    store_split(Qs + item * sOut, (long long)k * 64 + n * D + u, (long long)p * D + e, pitch,
                 krp, v.x, -v.y, 0);
   }
 }
@@ -554,6 +557,7 @@ int tc_plan_maps(ntu_ctx* c) {
   mk(&P.tc_hL.mapA, W.EBLd, pE, P.rowsE);
   mk(&P.tc_hR.mapA, W.EBRd, pE, P.rowsE);
   mk(&P.tc_hL.mapB, W.T2s, pE, P.rowsT);
+  if (st == NTU_OK) st = tc_make_map(&P.mapT2st, W.T2s, pE, P.rowsT, cap, (int)(P.D * P.D));
   P.tc_hR.mapB = P.tc_hL.mapB;
   mk(&P.tc_join.mapA, W.HLd, pJ, P.rowsHL);
   mk(&P.tc_join.mapB, W.HRs, pJ, P.rowsHR);
@@ -576,11 +580,11 @@ static cudaError_t env_chain_bf16x3(ntu_ctx* c, int n, const void* Ta, const voi
   RG(run_gemm<float2>(c, P.e2BR, n, Ta, Ta, W.EBRd));
   RG(run_gemm<float2>(c, P.y2, n, QA, W.EL, W.Ys));
   RG(launch_q_split(c, n, (const float2*)QA, W.Qs));
-  RG(launch_t12(c, n, P.mapEtopL, W.T2s));
+  RG(launch_t12(c, n, P.mapEtopL));
   RG(launch_tc_gemm(c, P.tc_hL, n, W.HLd));
   RG(run_gemm<float2>(c, P.y2, n, QB, W.ER, W.Ys));
   RG(launch_q_split(c, n, (const float2*)QB, W.Qs));
-  RG(launch_t12(c, n, P.mapEtopR, W.T2s));
+  RG(launch_t12(c, n, P.mapEtopR));
   RG(launch_tc_gemm(c, P.tc_hR, n, W.HRs));
   RG(launch_tc_gemm(c, P.tc_join, n, graw));
   return cudaSuccess;

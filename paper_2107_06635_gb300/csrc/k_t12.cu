@@ -21,10 +21,11 @@
 // conj(Q) block per unit, double-buffered), warp 1 issues the MMAs (GEMM1 of
 // unit i, then GEMM2 of unit i-1), warps 2-9 turn accumulator 1 into the B
 // operand of GEMM2 (two buffers), warps 10-17 turn accumulator 2 into output
-// rows: each thread owns one row and sixteen consecutive columns, which the
-// planar layout makes 32 contiguous bytes of hi and of lo, stored from
-// registers.  Every wait is bounded; every role leaves its loop on a timeout
-// and the epilogue groups leave together.
+// rows in a swizzled shared staging block that one thread stores with TMA.
+// Both epilogues write 16-byte chunks: the planar K of GEMM2 puts the eight
+// u' values of one (u, n') next to each other, and the planar T2 the
+// sixteen columns a thread holds.  Every wait is bounded; every role leaves
+// its loop on a timeout and the epilogue groups leave together.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -46,7 +47,9 @@ constexpr int OFF_A2 = 0;                     // 4 A tiles: E_top hi0, hi1, lo0,
 constexpr int OFF_A1 = OFF_A2 + 4 * A_TILE;   // 2 A tiles: Y hi, lo
 constexpr int OFF_B1 = OFF_A1 + 2 * A_TILE;   // 2 buffers x 2 B tiles: conj(Q) hi, lo
 constexpr int OFF_B2 = OFF_B1 + 4 * B_TILE;   // 2 buffers x 4 B tiles: T1 hi0, hi1, lo0, lo1
-constexpr int OFF_BAR = OFF_B2 + 8 * B_TILE;
+constexpr int STG_BOX = 64 * 128;             // one output box: 64 rows x 64 BF16
+constexpr int OFF_STG = OFF_B2 + 8 * B_TILE;  // output staging: up to 4 boxes (hi Re/Im, lo Re/Im)
+constexpr int OFF_BAR = OFF_STG + 4 * STG_BOX;
 constexpr size_t T12_SMEM = (size_t)OFF_BAR + 512 + 1024;
 static_assert(T12_SMEM <= 227 * 1024, "shared memory budget");
 
@@ -67,9 +70,8 @@ struct T12Args {
   int D, K;
   int nchunk;           // 64-wide K chunks of GEMM2 (krpE / 64)
   int krpY, krpE;
+  int k1;               // 16-wide K steps of GEMM1 that hold data: ceil(2 d_p D / 16)
   long long units;      // items * K * K
-  __nv_bfloat16* out;   // T2 split operand, items x rowsT x 2 krpE
-  long long sOut;       // per-item stride (elements)
   int* err;
 };
 
@@ -79,6 +81,7 @@ template <int DT>
 __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ CUtensorMap mA2,
                                                       const __grid_constant__ CUtensorMap mA1,
                                                       const __grid_constant__ CUtensorMap mB1,
+                                                      const __grid_constant__ CUtensorMap mT2,
                                                       T12Args a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -95,9 +98,9 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
   // contiguous range of units for this CTA
   const long long u0 = a.units * blockIdx.x / gridDim.x;
   const long long u1 = a.units * (blockIdx.x + 1) / gridDim.x;
-  // padding of the generated operand must read as zero: clear it once
-  // (generic stores, then a proxy fence)
-  for (int i = tid; i < 8 * B_TILE / 16; i += T12_THREADS)
+  // padding of the generated operand and of the output staging must read
+  // as zero: clear both once (generic stores, then a proxy fence)
+  for (int i = tid; i < (8 * B_TILE + 4 * STG_BOX) / 16; i += T12_THREADS)
     reinterpret_cast<uint4*>(sm + OFF_B2)[i] = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async();
   if (tid == 0) {
@@ -193,8 +196,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
           const uint64_t al = tc::sdesc_k128(tc::smem_u32(sm + OFF_A1 + A_TILE));
           const uint64_t bh = tc::sdesc_k128(tc::smem_u32(sm + OFF_B1 + b * 2 * B_TILE));
           const uint64_t bl = tc::sdesc_k128(tc::smem_u32(sm + OFF_B1 + b * 2 * B_TILE + B_TILE));
-#pragma unroll
-          for (int kk4 = 0; kk4 < 4; ++kk4) {
+          for (int kk4 = 0; kk4 < a.k1; ++kk4) {     // K beyond 2 d_p D is zero padding
             tc::mma_bf16(acc, ah + 2 * kk4, bh + 2 * kk4, id, kk4 != 0);
             tc::mma_bf16(acc, ah + 2 * kk4, bl + 2 * kk4, id, 1);
             tc::mma_bf16(acc, al + 2 * kk4, bh + 2 * kk4, id, 1);
@@ -247,16 +249,20 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
     }
     __syncwarp();
   } else if (warp < 2 + EPI / 32) {
-    // ---- epilogue 1: accumulator 1 (rows (u,n) Re / Im, columns (u',n'))
-    // -> split B operand of GEMM2 in shared memory, row n' * D + n (this
-    // order spreads a warp's stores over the swizzle chunks; epilogue 2 maps
-    // GEMM2's columns back), K (u,u')
+    // ---- epilogue 1: accumulator 1 (rows (u,n) Re / Im, columns
+    // (n',u')) -> split B operand of GEMM2 in shared memory: row n' * D + n,
+    // K planar, Re of (u,u') at u * D + u' and Im krpE/2 later.  With D = 8
+    // a thread's eight values of one n' (u' = 0..7) are one 16-byte chunk of
+    // hi and one of lo; the chunk of row n'*8 + n that holds (u, .) is the
+    // 128-byte-swizzle slot u ^ n, so the 32 lanes of a warp (4 u x 8 n)
+    // cover all eight slots four times: conflict-free quarter-warp phases.
     // warp w reads TMEM lanes 32 (w % 4) .. +31, columns slice * 32 .. +31
     const int et = tid - 64, quarter = warp & 3, row = quarter * 32 + lane;
     const int cs = ((warp - 2) >> 2) * 32;
     const int r = row & 63, im = row >> 6;
     const bool rv = r < D2;
     const int uu = rv ? r / D : 0, nn = rv ? r % D : 0;
+    const int half = a.krpE / 2;
     long long i = 0;
     for (long long u = u0; u < u1; ++u, ++i) {
       const int b = (int)(i & 1);
@@ -275,23 +281,25 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       tc::fence_after_sync();
       unsigned char* B2 = sm + OFF_B2 + b * 4 * B_TILE;
       if (DT == 8) {
-        // row n' * 8 + n, so (row & 7) = n; K = 16 u + 2 u' + im lies in
-        // chunk u >> 2, 16-byte slot (2u + (u' >> 2)) ^ n, byte 4 (u' & 3) + 2 im
-        unsigned char* bh = B2 + (uu >> 2) * B_TILE + nn * 128 + (im << 1);
-        unsigned char* s0 = bh + (((((2 * uu) & 7) ^ nn)) << 4);
-        unsigned char* s1 = bh + (((((2 * uu + 1) & 7) ^ nn)) << 4);
+        unsigned char* bh = B2 + im * B_TILE + nn * 128 + ((uu ^ nn) << 4);
 #pragma unroll
         for (int c0 = cs; c0 < cs + 32; c0 += 16) {
           float v[16];
           tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 64 + c0), v);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int c = c0 + q, up = c >> 3, np = c & 7;
-            unsigned char* dst = (up >> 2 ? s1 : s0) + np * 1024 + ((up & 3) << 2);
-            __nv_bfloat16 h, l;
-            split_bf16(v[q], h, l);
-            *reinterpret_cast<__nv_bfloat16*>(dst) = h;
-            *reinterpret_cast<__nv_bfloat16*>(dst + 2 * B_TILE) = l;
+          for (int g = 0; g < 2; ++g) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              __nv_bfloat16 h0, l0, h1, l1;
+              split_bf16(v[8 * g + 2 * q], h0, l0);
+              split_bf16(v[8 * g + 2 * q + 1], h1, l1);
+              hw[q] = pack_bf16(h0, h1);
+              lw[q] = pack_bf16(l0, l1);
+            }
+            unsigned char* dst = bh + ((c0 >> 3) + g) * 1024;    // row n' * 8 + n
+            *reinterpret_cast<uint4*>(dst) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(dst + 2 * B_TILE) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
           }
         }
       } else
@@ -303,8 +311,8 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
         for (int q = 0; q < 16; ++q) {
           const int c = c0 + q;
           if (rv && c < D2) {
-            const int up = c / D, np = c % D;
-            const int brow = np * D + nn, kre = 2 * (uu * D + up) + im;
+            const int np = c / D, up = c % D;
+            const int brow = np * D + nn, kre = im * half + uu * D + up;
             const uint32_t off = swz(brow, kre & 63);
             __nv_bfloat16 h, l;
             split_bf16(v[q], h, l);
@@ -322,57 +330,75 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
     }
   } else {
     // ---- epilogue 2: accumulator 2 (rows (ht,ht') Re / Im, columns
-    // j = n' * D + n) -> row (k,k',ht,ht') of the split T2 operand: hi at
-    // column j (Re) or krpE/2 + j (Im), lo krpE further.  Accumulator
-    // columns j >= D^2 are exact zeros (zero rows of the B operand), so a
-    // sixteen-column group that starts below D^2 is stored whole.
+    // j = n' * D + n) -> rows (k,k',ht,ht') of the split T2 operand: hi at
+    // column j (Re) or krpE/2 + j (Im), lo krpE further.  Each thread owns
+    // one row and sixteen consecutive columns, i.e. two 16-byte chunks of hi
+    // and two of lo; they go to a staging copy of the unit's output rows in
+    // 64-column boxes with the 128-byte swizzle (32 lanes = 32 rows cover the
+    // eight slots four times: conflict-free), and one thread stores the
+    // boxes with TMA.  Accumulator columns j >= D^2 are exact zeros (zero
+    // rows of the B operand), so a sixteen-column group that starts below
+    // D^2 is staged whole; staging positions never written stay zero.
     const int et = tid - 64 - EPI, quarter = warp & 3, row = quarter * 32 + lane;
     const int cs = ((warp - 2 - EPI / 32) >> 2) * 32;
     const int r = row & 63, im = row >> 6;
     const bool rv = r < D2;
-    const long long pitch = 2LL * a.krpE;
-    const int coff = im * (a.krpE / 2);
+    const int half = a.krpE / 2, nbox = a.krpE / 32;
+    unsigned char* stg = sm + OFF_STG + r * 128;
     long long i = 0;
     for (long long u = u0; u < u1; ++u, ++i) {
       const int z = (int)(u / KK), kk = (int)(u % KK);
       const int b = (int)(i & 1);
       const long long ub = i >> 1;
-      const bool got =
-          et != 0 || tc::mbar_wait_sleep(&c2_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
+      bool got = true;
+      if (et == 0) {
+        got = tc::mbar_wait_sleep(&c2_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
+        tc::bulk_wait_read();                   // the staging block is free again
+      }
       if (!tc::bar_and(2, EPI, got)) {
         if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
         break;
       }
       tc::fence_after_sync();
-      __nv_bfloat16* orow = a.out + (long long)z * a.sOut + ((long long)kk * D2 + r) * pitch + coff;
 #pragma unroll
       for (int c0 = cs; c0 < cs + 32; c0 += 16) {
         if (DT == 8 || c0 < D2) {                 // uniform over the warp
           float v[16];
           tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(128 + b * 64 + c0), v);
           if (rv) {
-            uint32_t hw[8], lw[8];
+            const int pos = im * half + c0;      // hi column of v[0]
+            unsigned char* bx = stg + (pos >> 6) * STG_BOX;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              __nv_bfloat16 h0, l0, h1, l1;
-              split_bf16(v[2 * q], h0, l0);
-              split_bf16(v[2 * q + 1], h1, l1);
-              hw[q] = pack_bf16(h0, h1);
-              lw[q] = pack_bf16(l0, l1);
+            for (int g = 0; g < 2; ++g) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                __nv_bfloat16 h0, l0, h1, l1;
+                split_bf16(v[8 * g + 2 * q], h0, l0);
+                split_bf16(v[8 * g + 2 * q + 1], h1, l1);
+                hw[q] = pack_bf16(h0, h1);
+                lw[q] = pack_bf16(l0, l1);
+              }
+              const int slot = ((((pos & 63) >> 3) + g) ^ (r & 7)) << 4;
+              *reinterpret_cast<uint4*>(bx + slot) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(bx + (nbox / 2) * STG_BOX + slot) =
+                  make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
-            uint4* ph = reinterpret_cast<uint4*>(orow + c0);
-            uint4* pl = reinterpret_cast<uint4*>(orow + a.krpE + c0);
-            ph[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            ph[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
-            pl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-            pl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
           }
         }
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&c2_empty[b]);
+      fence_proxy_async();                       // staging writes -> TMA reads
+      tc::bar_sync(2, EPI);
+      if (et == 0) {
+        for (int q = 0; q < nbox; ++q)
+          tc::tma_store_3d(&mT2, sm + OFF_STG + q * STG_BOX, 64 * q, kk * D2, z);
+        tc::bulk_commit();
+      }
     }
+    if (et == 0) tc::bulk_wait_all();           // every store has landed before exit
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -382,15 +408,16 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
 
 size_t t12_smem_bytes() { return T12_SMEM; }
 
-cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE, void* out) {
+// The output (T2 split operand, W.T2s) is written through the plan's store
+// map mapT2st, whose box is one unit's D^2 rows.
+cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE) {
   const Plan& P = c->plan;
   T12Args a;
   a.D = P.D; a.K = P.K;
   a.nchunk = (int)(P.krpE / 64);
   a.krpY = (int)P.krpY; a.krpE = (int)P.krpE;
+  a.k1 = (int)((2 * P.dp * P.D + 15) / 16);
   a.units = (long long)n * P.K * P.K;
-  a.out = (__nv_bfloat16*)out;
-  a.sOut = P.rowsT * 2 * P.krpE;
   a.err = c->d_status;
   if (a.units == 0) return cudaSuccess;
   static int sms = 0;
@@ -408,9 +435,9 @@ cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE, void* out) {
     attr = true;
   }
   if (P.D == 8)
-    k_t12<8><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, a);
+    k_t12<8><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, P.mapT2st, a);
   else
-    k_t12<0><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, a);
+    k_t12<0><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, P.mapT2st, a);
   return after_launch(c, "k_t12");
 }
 

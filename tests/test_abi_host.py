@@ -50,6 +50,16 @@ def test_init_rejects_too_few_rows(lib):
     assert lib.ntu_init(ctypes.byref(cfg), None, ctypes.byref(h)) == 1
 
 
+def test_init_rejects_bf16x3_beyond_one_k_tile(lib):
+    # the fused t1-t2 holds one 64-wide K tile of Y: 2 d_p D <= 64; d_phys=4,
+    # d_anc=2, D=8 gives 128 and must be refused before any device work
+    cfg = ntu.Config(8, 4, 2, 2, 10, 2, 4, 8, 1)
+    h = ctypes.c_void_p()
+    assert lib.ntu_init(ctypes.byref(cfg), None, ctypes.byref(h)) == 6
+    assert h.value is None
+    assert b"2*d_phys*d_anc*D" in lib.ntu_last_error(None)
+
+
 def test_null_arguments(lib):
     assert lib.ntu_init(None, None, None) == 1
     assert lib.ntu_destroy(None) == 0
