@@ -215,7 +215,6 @@ struct AlsShared {
   double2 ap[256];
   double2 ph[32];
   int ge;                      // scale exponent of the double-FP32 copy of g
-  int cumX[257];               // item offsets of the row blocks of the double-FP32 build
   double red[2 * NTU_WARPS];
   double eps0, tau_sel;
   int err;
@@ -369,90 +368,73 @@ __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng)
   return e;
 }
 
-// als_reduced in double-FP32 arithmetic: same contractions and the same
-// block lower triangle, each thread holding four q columns in registers;
-// gX comes out in FP64 (scaled back by 2^e) and, for the matrix products of
-// the conjugate-gradient solve, in double-FP32 (gXdf, scaled by 2^-e).  F
-// (the isometric factor) is split into als_fdf(sm).
+// als_reduced in double-FP32 arithmetic, block by block: block (f1, f),
+// f1 >= f, of the reduced metric is
+//   gX[(f1,q1),(f,q)] = sum_{c',c} conj(F[c'][q1]) g[f1*sf + c'*sc][f*sf + c*sc] F[c][q],
+// a K x K block of g contracted with F on both sides.  One warp takes a
+// block: T = g_blk F (K x D) goes to a warp-private tile in the SVD arrays A
+// and V (free between tilts), then F^H T gives the D x D block, written to
+// gX in FP64 (scaled back by 2^e) and to gXdf in double-FP32 (for the matrix
+// products of the conjugate-gradient solve), mirrored into the upper
+// triangle.  Every element of g is read once per call and no intermediate
+// leaves the SM.  F (the isometric factor) is split into als_fdf(sm).
 __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gdf, int e,
-                               int side, float4* Tmdf, double2* gX, float4* gXdf) {
+                               int side, double2* gX, float4* gXdf) {
   const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
+  const int warp = tid >> 5, lane = tid & 31;
   const double2* F = side == 0 ? sm.MB : sm.MA;
   const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
   const int nq = (D + 3) >> 2;
+  const float4* Fd = als_fdf(sm);
+  float4* Tw = reinterpret_cast<float4*>(sm.S.A) + warp * (32 * 8);   // K x D <= 256
   for (int i = tid; i < K * D; i += NTU_CTA) als_fdf(sm)[i] = df_split(F[i]);
   __syncthreads();
-  // Tm[r][(f,q)] = sum_c g[r][f*sf + c*sc] F[c][q] for free(r) = fp >= f.
-  // Work items (pair t = (fp, f), c', q block) are enumerated densely, so
-  // every lane and every thread does the same amount of work.
-  const int npair = K * (K + 1) / 2;
-  for (int idx = tid; idx < npair * K * nq; idx += NTU_CTA) {
-    const int qb = idx % nq, cp = (idx / nq) % K, t = idx / (nq * K);
-    int fp = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while ((fp + 1) * (fp + 2) / 2 <= t) ++fp;
-    while (fp > 0 && fp * (fp + 1) / 2 > t) --fp;
-    const int f = t - fp * (fp + 1) / 2;
-    const int r = side == 0 ? fp * K + cp : cp * K + fp;
-    const float4* gr = gdf + (size_t)r * ng + f * sf;
-    const int q0 = qb * 4;
-    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+  const int nblk = K * (K + 1) / 2;
+  for (int blk = warp; blk < nblk; blk += NTU_WARPS) {
+    int f1 = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+    while ((f1 + 1) * (f1 + 2) / 2 <= blk) ++f1;
+    while (f1 > 0 && f1 * (f1 + 1) / 2 > blk) --f1;
+    const int f = blk - f1 * (f1 + 1) / 2;
+    // T[c'][q] = sum_c g[f1*sf + c'*sc][f*sf + c*sc] F[c][q], four q per item
+    for (int it = lane; it < K * nq; it += 32) {
+      const int c1 = it / nq, q0 = (it % nq) * 4;
+      const float4* gr = gdf + (size_t)(f1 * sf + c1 * sc) * ng + f * sf;
+      float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
 #pragma unroll 4
-    for (int c = 0; c < K; ++c) {
-      const float4 gv = gr[c * sc];
-      const float4* Fc = als_fdf(sm) + c * D + q0;
-      df_cmac<false>(acc0, gv, Fc[0]);
-      if (q0 + 1 < D) df_cmac<false>(acc1, gv, Fc[1]);
-      if (q0 + 2 < D) df_cmac<false>(acc2, gv, Fc[2]);
-      if (q0 + 3 < D) df_cmac<false>(acc3, gv, Fc[3]);
+      for (int c = 0; c < K; ++c) {
+        const float4 gv = gr[c * sc];
+        const float4* Fc = Fd + c * D + q0;
+        df_cmac<false>(acc0, gv, Fc[0]);
+        if (q0 + 1 < D) df_cmac<false>(acc1, gv, Fc[1]);
+        if (q0 + 2 < D) df_cmac<false>(acc2, gv, Fc[2]);
+        if (q0 + 3 < D) df_cmac<false>(acc3, gv, Fc[3]);
+      }
+      float4* out = Tw + c1 * D + q0;
+      out[0] = acc0;
+      if (q0 + 1 < D) out[1] = acc1;
+      if (q0 + 2 < D) out[2] = acc2;
+      if (q0 + 3 < D) out[3] = acc3;
     }
-    float4* out = Tmdf + (size_t)r * nA + f * D + q0;
-    out[0] = acc0;
-    if (q0 + 1 < D) out[1] = acc1;
-    if (q0 + 2 < D) out[2] = acc2;
-    if (q0 + 3 < D) out[3] = acc3;
-  }
-  __syncthreads();
-  // gX[(f1,q1),col] = sum_c conj(F[c][q1]) Tm[f1*sf + c*sc][col], rows >= col.
-  // Row block b = (f1, q block) pairs with the columns col <= its last row;
-  // sm.cumX[b] counts the items of the blocks before b.
-  const int nb = K * nq;
-  for (int idx = tid; idx < sm.cumX[nb]; idx += NTU_CTA) {
-    int lo = 0, hi = nb;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (sm.cumX[mid] <= idx) lo = mid; else hi = mid;
-    }
-    const int col = idx - sm.cumX[lo], qb = lo % nq, f1 = lo / nq;
-    const int q0 = qb * 4, row0 = f1 * D + q0;
-    const int nr = min(4, D - q0);
-    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+    __syncwarp();
+    // block[q1][q] = sum_c' conj(F[c'][q1]) T[c'][q]; the diagonal block keeps
+    // q1 >= q and mirrors it, so gX is Hermitian to the last bit
+    for (int it = lane; it < D * D; it += 32) {
+      const int q1 = it / D, q = it % D;
+      if (f1 == f && q1 < q) continue;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
-    for (int c = 0; c < K; ++c) {
-      const float4 tv = Tmdf[(size_t)(f1 * sf + c * sc) * nA + col];
-      const float4* Fc = als_fdf(sm) + c * D + q0;
-      df_cmac<true>(acc0, Fc[0], tv);
-      if (nr > 1) df_cmac<true>(acc1, Fc[1], tv);
-      if (nr > 2) df_cmac<true>(acc2, Fc[2], tv);
-      if (nr > 3) df_cmac<true>(acc3, Fc[3], tv);
-    }
-    double2* outc = gX + (size_t)col * nA;
-    float4* outd = gXdf + (size_t)col * nA;
-    const float4 accs[4] = {acc0, acc1, acc2, acc3};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int row = row0 + t;
-      if (t < nr && row >= col) {
-        double2 v = df_join(accs[t]);
-        if (e != 0) v = make_double2(scalbn(v.x, e), scalbn(v.y, e));
-        outc[row] = v;
-        outd[row] = accs[t];
-        if (row != col) {                                // upper triangle
-          gX[(size_t)row * nA + col] = cconj(v);
-          gXdf[(size_t)row * nA + col] =
-              make_float4(accs[t].x, -accs[t].y, accs[t].z, -accs[t].w);
-        }
+      for (int c1 = 0; c1 < K; ++c1) df_cmac<true>(acc, Fd[c1 * D + q1], Tw[c1 * D + q]);
+      const int row = f1 * D + q1, col = f * D + q;
+      double2 v = df_join(acc);
+      if (e != 0) v = make_double2(scalbn(v.x, e), scalbn(v.y, e));
+      gX[(size_t)col * nA + row] = v;
+      gXdf[(size_t)col * nA + row] = acc;
+      if (row != col) {                                  // upper triangle
+        gX[(size_t)row * nA + col] = cconj(v);
+        gXdf[(size_t)row * nA + col] = make_float4(acc.x, -acc.y, acc.z, -acc.w);
       }
     }
+    __syncwarp();
   }
   __syncthreads();
 }
@@ -873,17 +855,6 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   const float4* gdf = nullptr;
   int ge = 0;
   if (a.df) {
-    if (tid == 0) {
-      const int nq = (D + 3) >> 2;
-      int acc = 0;
-      for (int b = 0; b < K * nq; ++b) {
-        sm.cumX[b] = acc;
-        const int q0 = (b % nq) * 4;
-        acc += (b / nq) * D + q0 + min(4, D - q0);     // columns 0 .. last row of block b
-      }
-      sm.cumX[K * nq] = acc;
-    }
-    __syncthreads();
     ge = als_split_g(sm, g, a.gdf + item * (long long)ng * ng, ng);
     if (tid == 0) sm.ge = ge;
     gdf = a.gdf + item * (long long)ng * ng;
@@ -896,8 +867,7 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     for (int side = 0; side < 2; ++side) {
       if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
       if (a.df)
-        als_reduced_df(sm, a, gdf, ge, side, reinterpret_cast<float4*>(Tm), gX,
-                       reinterpret_cast<float4*>(gC));
+        als_reduced_df(sm, a, gdf, ge, side, gX, reinterpret_cast<float4*>(gC));
       else als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
       als_source(sm, a, side, jv, gx0);
       if (!als_solve_chol(sm, a, side, gX, gC, jv, tau_max)) {
