@@ -241,6 +241,7 @@ struct AlsArgs {
   int* status;
   int df;                      // build the reduced metric in double-FP32 arithmetic
   float4* gdf;                 // n x ng^2 scratch: g split into FP32 pairs
+  float4* gdfT;                // the same with kA and kB swapped in rows and columns
 };
 
 // X = MA MB^T -> SVD -> (MA, MB) by mode: 0 tilt before the A step
@@ -352,8 +353,10 @@ __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
 // g (FP64) -> gdf = g 2^-e in FP32 pairs.  e = 0 while max |Re|, |Im| lies
 // in [2^-60, 2^60] (products and sums of the build then stay far inside the
 // FP32 range); otherwise 2^e is the power of two just above the maximum, an
-// exact scaling.  Returns e.
-__device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng) {
+// exact scaling.  gdfT[(kB',kA'),(kB,kA)] = gdf[(kA',kB'),(kA,kB)] lets the B
+// step read its blocks along rows as the A step does.  Returns e.
+__device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, float4* gdfT, int ng,
+                           int K) {
   const int tid = threadIdx.x;
   const size_t nn = (size_t)ng * ng;
   double mx = 0.0;
@@ -362,7 +365,10 @@ __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng)
   const int e = (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ilogb(mx) + 1 : 0;
   for (size_t i = tid; i < nn; i += NTU_CTA) {
     double2 v = g[i];
-    gdf[i] = df_split(make_double2(scalbn(v.x, -e), scalbn(v.y, -e)));
+    const float4 d = df_split(make_double2(scalbn(v.x, -e), scalbn(v.y, -e)));
+    gdf[i] = d;
+    const int r = (int)(i / ng), c = (int)(i % ng);
+    gdfT[(size_t)((r % K) * K + r / K) * ng + (c % K) * K + c / K] = d;
   }
   __syncthreads();
   return e;
@@ -378,12 +384,14 @@ __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, int ng)
 // products of the conjugate-gradient solve), mirrored into the upper
 // triangle.  Every element of g is read once per call and no intermediate
 // leaves the SM.  F (the isometric factor) is split into als_fdf(sm).
-__device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gdf, int e,
-                               int side, double2* gX, float4* gXdf) {
+__device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gdf,
+                               const float4* gdfT, int e, int side, double2* gX, float4* gXdf) {
   const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
   const int warp = tid >> 5, lane = tid & 31;
   const double2* F = side == 0 ? sm.MB : sm.MA;
-  const int sf = side == 0 ? K : 1, sc = side == 0 ? 1 : K;
+  // the B step reads the block (f1, f) of g with rows (c', f1) and columns
+  // (c, f) as rows f1*K + c' and columns f*K + c of gdfT
+  const float4* gb = side == 0 ? gdf : gdfT;
   const int nq = (D + 3) >> 2;
   const float4* Fd = als_fdf(sm);
   float4* Tw = reinterpret_cast<float4*>(sm.S.A) + warp * (32 * 8);   // K x D <= 256
@@ -395,14 +403,15 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
     while ((f1 + 1) * (f1 + 2) / 2 <= blk) ++f1;
     while (f1 > 0 && f1 * (f1 + 1) / 2 > blk) --f1;
     const int f = blk - f1 * (f1 + 1) / 2;
-    // T[c'][q] = sum_c g[f1*sf + c'*sc][f*sf + c*sc] F[c][q], four q per item
+    // T[c'][q] = sum_c g[f1*sf + c'*sc][f*sf + c*sc] F[c][q] (sf = K, sc = 1
+    // on the A step, sf = 1, sc = K on the B step), four q per item
     for (int it = lane; it < K * nq; it += 32) {
       const int c1 = it / nq, q0 = (it % nq) * 4;
-      const float4* gr = gdf + (size_t)(f1 * sf + c1 * sc) * ng + f * sf;
+      const float4* gr = gb + (size_t)(f1 * K + c1) * ng + f * K;
       float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
 #pragma unroll 4
       for (int c = 0; c < K; ++c) {
-        const float4 gv = gr[c * sc];
+        const float4 gv = gr[c];
         const float4* Fc = Fd + c * D + q0;
         df_cmac<false>(acc0, gv, Fc[0]);
         if (q0 + 1 < D) df_cmac<false>(acc1, gv, Fc[1]);
@@ -852,12 +861,14 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   e0 = block_sum(e0, sm.red);
   if (tid == 0) sm.eps0 = e0;
   __syncthreads();
-  const float4* gdf = nullptr;
+  const float4 *gdf = nullptr, *gdfT = nullptr;
   int ge = 0;
   if (a.df) {
-    ge = als_split_g(sm, g, a.gdf + item * (long long)ng * ng, ng);
-    if (tid == 0) sm.ge = ge;
     gdf = a.gdf + item * (long long)ng * ng;
+    gdfT = a.gdfT + item * (long long)ng * ng;
+    ge = als_split_g(sm, g, a.gdf + item * (long long)ng * ng, a.gdfT + item * (long long)ng * ng,
+                     ng, K);
+    if (tid == 0) sm.ge = ge;
   }
   // SVDU start (Fig. 2(c,d)).  X0 = U S V^H gives the balanced start
   // (U sqrt(S), conj(V) sqrt(S)) whose first tilt is (U S, conj(V)): with
@@ -867,7 +878,7 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     for (int side = 0; side < 2; ++side) {
       if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
       if (a.df)
-        als_reduced_df(sm, a, gdf, ge, side, gX, reinterpret_cast<float4*>(gC));
+        als_reduced_df(sm, a, gdf, gdfT, ge, side, gX, reinterpret_cast<float4*>(gC));
       else als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
       als_source(sm, a, side, jv, gx0);
       if (!als_solve_chol(sm, a, side, gX, gC, jv, tau_max)) {
@@ -951,6 +962,7 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   a.rotcap = W.rotcap; a.status = c->d_status;
   a.df = c->cfg.precision != NTU_FP64;
   a.gdf = reinterpret_cast<float4*>(W.gscr);
+  a.gdfT = reinterpret_cast<float4*>(W.gw);     // the repair's eigenvector scratch, free here
   size_t sm = sizeof(AlsShared);
   static int sms = 0;
   if (!sms) {
