@@ -127,8 +127,10 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       // MMA warp issue GEMM1 of the new unit before it releases E_top)
       int a1z = -1, a1k = -1, a2z = -1;
       long long a1n = 0, a2n = 0, qn = 0, i = 0;
-      for (long long u = u0; u < u1; ++u, ++i) {
-        const int z = (int)(u / KK), kk = (int)(u % KK), k = kk / K, kp = kk % K;
+      // unit u = (z, k, kp): kept incrementally (no 64-bit division per unit)
+      int z = (int)(u0 / KK), k = (int)(u0 % KK) / K, kp = (int)(u0 % KK) % K;
+      for (long long u = u0; u < u1; ++u, ++i, kp = kp + 1 < K ? kp + 1 : 0,
+                     k = kp ? k : (k + 1 < K ? k + 1 : 0), z = (kp || k) ? z : z + 1) {
         if (z != a1z || k != a1k) {
           if (a1n > 0 && !tc::mbar_wait(a1_empty, (uint32_t)((a1n - 1) & 1), T12_WAIT)) {
             raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
@@ -179,9 +181,10 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       int a1z = -1, a1k = -1, a2z = -1;
       long long a1n = 0, a2n = 0, i = 0;
       bool ok = true;
+      // unit u = (z, k, kp) kept incrementally; zp is the item of unit u - 1
+      int z = (int)(u0 / KK), k = (int)(u0 % KK) / K, kp = (int)(u0 % KK) % K, zp = -1;
       for (long long u = u0; u <= u1 && ok; ++u, ++i) {
         if (u < u1) {
-          const int z = (int)(u / KK), kk = (int)(u % KK), k = kk / K;
           if (z != a1z || k != a1k) {
             if (!tc::mbar_wait(a1_full, (uint32_t)(a1n & 1), T12_WAIT)) { ok = false; break; }
             ++a1n; a1z = z; a1k = k;
@@ -203,18 +206,14 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
           }
           tc::mma_commit(&q_empty[b]);
           tc::mma_commit(&c1_full[b]);
-          // the Y block is released after the last unit that reads it
-          bool last_k = u + 1 >= u1;
-          if (!last_k) {
-            const int zn = (int)((u + 1) / KK), kn = (int)((u + 1) % KK) / K;
-            last_k = zn != z || kn != k;
-          }
-          if (last_k) tc::mma_commit(a1_empty);
+          // the Y block is released after the last unit that reads it (the
+          // next unit starts a new k, or there is none)
+          if (u + 1 >= u1 || kp == K - 1) tc::mma_commit(a1_empty);
         }
         if (u > u0) {
           // GEMM2 of unit j = u - 1
           const long long j = i - 1;
-          const int zj = (int)((u - 1) / KK);
+          const int zj = zp;
           const int b = (int)(j & 1);
           const long long ub = j >> 1;
           if (zj != a2z) {
@@ -239,7 +238,12 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
           }
           tc::mma_commit(&b2_empty[b]);
           tc::mma_commit(&c2_full[b]);
-          if (u == u1 || (int)(u / KK) != zj) tc::mma_commit(a2_empty);
+          if (u == u1 || z != zj) tc::mma_commit(a2_empty);
+        }
+        zp = z;
+        if (++kp == K) {
+          kp = 0;
+          if (++k == K) { k = 0; ++z; }
         }
       }
       if (!ok) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
@@ -346,8 +350,8 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
     const int half = a.krpE / 2, nbox = a.krpE / 32;
     unsigned char* stg = sm + OFF_STG + r * 128;
     long long i = 0;
-    for (long long u = u0; u < u1; ++u, ++i) {
-      const int z = (int)(u / KK), kk = (int)(u % KK);
+    int z = (int)(u0 / KK), kk = (int)(u0 % KK);
+    for (long long u = u0; u < u1; ++u, ++i, kk = kk + 1 < KK ? kk + 1 : 0, z = kk ? z : z + 1) {
       const int b = (int)(i & 1);
       const long long ub = i >> 1;
       bool got = true;
