@@ -95,14 +95,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     if (lane == 0) {
       // ---- producer
       long long g = 0;
+      int s = 0;                          // stage g % TSTAGES, phase (g / TSTAGES) & 1
+      uint32_t ph = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const int z = (int)(t / per_item), rem = (int)(t % per_item);
         const int mt = rem / ntN, n0 = (rem % ntN) * TBN;
-        for (int it = 0; it < steps; ++it, ++g) {
-          const int s = (int)(g % TSTAGES);
-          const long long u = g / TSTAGES;
-          if (u > 0 && !tc::mbar_wait(&empty[s], (uint32_t)((u - 1) & 1), WAIT_LIMIT)) {
+        for (int it = 0; it < steps; ++it, ++g, s = s + 1 < TSTAGES ? s + 1 : 0, ph ^= s ? 0u : 1u) {
+          if (g >= TSTAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT)) {
             raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
             ok = false;
             break;
@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     if (lane == 0) {
       // ---- MMA issuer
       const uint32_t idesc = tc::idesc_bf16_f32(TBM, TBN);
-      long long g = 0;
+      int s = 0;                          // stage and phase of the next K stage
+      uint32_t ph = 0;
       int i = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
@@ -134,10 +135,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         }
         tc::fence_after_sync();
         const uint32_t acc = tmem + (uint32_t)(b * TBN);
-        for (int it = 0; it < steps; it += 2, g += 2) {
-          const int sh = (int)(g % TSTAGES), sl = (int)((g + 1) % TSTAGES);
-          if (!tc::mbar_wait(&full[sh], (uint32_t)((g / TSTAGES) & 1), WAIT_LIMIT) ||
-              !tc::mbar_wait(&full[sl], (uint32_t)(((g + 1) / TSTAGES) & 1), WAIT_LIMIT)) {
+        for (int it = 0; it < steps; it += 2) {
+          const int sh = s;
+          const uint32_t phh = ph;
+          if (++s == TSTAGES) { s = 0; ph ^= 1u; }
+          const int sl = s;
+          const uint32_t phl = ph;
+          if (++s == TSTAGES) { s = 0; ph ^= 1u; }
+          if (!tc::mbar_wait(&full[sh], phh, WAIT_LIMIT) || !tc::mbar_wait(&full[sl], phl, WAIT_LIMIT)) {
             raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
             ok = false;
             break;
