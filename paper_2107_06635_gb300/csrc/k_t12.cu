@@ -50,6 +50,9 @@ constexpr int OFF_B2 = OFF_B1 + 4 * B_TILE;   // 2 buffers x 4 B tiles: T1 hi0, 
 constexpr int STG_BOX = 64 * 128;             // one output box: 64 rows x 64 BF16
 constexpr int OFF_STG = OFF_B2 + 8 * B_TILE;  // output staging: up to 4 boxes (hi Re/Im, lo Re/Im)
 constexpr int OFF_BAR = OFF_STG + 4 * STG_BOX;
+// TMEM columns: accumulator 1 (two buffers) 0-127, accumulator 2 128-255,
+// E_top as the A operand of GEMM2: hi halves from 256, lo halves from 320
+constexpr uint32_t TM_COLS = 512, TM_A2H = 256, TM_A2L = 320;
 constexpr size_t T12_SMEM = (size_t)OFF_BAR + 512 + 1024;
 static_assert(T12_SMEM <= 227 * 1024, "shared memory budget");
 
@@ -93,6 +96,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
   uint64_t *c2_full = bar + 16, *c2_empty = bar + 18;         // accumulator 2 [2]
   uint64_t* done = bar + 20;
   uint32_t* tmem_slot = (uint32_t*)(bar + 21);
+  uint64_t* a2t_full = bar + 22;                               // E_top copied into TMEM
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = DT ? DT : a.D, K = a.K, D2 = D * D, KK = K * K;
   // contiguous range of units for this CTA
@@ -104,8 +108,9 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
     reinterpret_cast<uint4*>(sm + OFF_B2)[i] = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async();
   if (tid == 0) {
-    tc::mbar_init(a2_full, 1); tc::mbar_init(a2_empty, 1);
+    tc::mbar_init(a2_full, 1); tc::mbar_init(a2_empty, EPI / 32);
     tc::mbar_init(a1_full, 1); tc::mbar_init(a1_empty, 1);
+    tc::mbar_init(a2t_full, EPI / 32);
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&q_full[b], 1); tc::mbar_init(&q_empty[b], 1);
       tc::mbar_init(&c1_full[b], 1); tc::mbar_init(&c1_empty[b], EPI / 32);
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
     tc::mbar_init(done, 1);
     tc::fence_barrier_init();
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, 256);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, TM_COLS);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -216,8 +221,8 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
           const int zj = zp;
           const int b = (int)(j & 1);
           const long long ub = j >> 1;
-          if (zj != a2z) {
-            if (!tc::mbar_wait(a2_full, (uint32_t)(a2n & 1), T12_WAIT)) { ok = false; break; }
+          if (zj != a2z) {                      // E_top of the item is in TMEM
+            if (!tc::mbar_wait(a2t_full, (uint32_t)(a2n & 1), T12_WAIT)) { ok = false; break; }
             ++a2n; a2z = zj;
           }
           if (!tc::mbar_wait(&b2_full[b], (uint32_t)(ub & 1), T12_WAIT)) { ok = false; break; }
@@ -225,20 +230,19 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
           tc::fence_after_sync();
           const uint32_t acc = tmem + 128u + (uint32_t)(b * 64);
           for (int c = 0; c < a.nchunk; ++c) {
-            const uint64_t ah = tc::sdesc_k128(tc::smem_u32(sm + OFF_A2 + c * A_TILE));
-            const uint64_t al = tc::sdesc_k128(tc::smem_u32(sm + OFF_A2 + (2 + c) * A_TILE));
+            const uint32_t ah = tmem + TM_A2H + (uint32_t)(c * 32);
+            const uint32_t al = tmem + TM_A2L + (uint32_t)(c * 32);
             const uint64_t bh = tc::sdesc_k128(tc::smem_u32(sm + OFF_B2 + (b * 4 + c) * B_TILE));
             const uint64_t bl = tc::sdesc_k128(tc::smem_u32(sm + OFF_B2 + (b * 4 + 2 + c) * B_TILE));
 #pragma unroll
             for (int kk4 = 0; kk4 < 4; ++kk4) {
-              tc::mma_bf16(acc, ah + 2 * kk4, bh + 2 * kk4, id, (c | kk4) != 0);
-              tc::mma_bf16(acc, ah + 2 * kk4, bl + 2 * kk4, id, 1);
-              tc::mma_bf16(acc, al + 2 * kk4, bh + 2 * kk4, id, 1);
+              tc::mma_bf16_ts(acc, ah + 8 * kk4, bh + 2 * kk4, id, (c | kk4) != 0);
+              tc::mma_bf16_ts(acc, ah + 8 * kk4, bl + 2 * kk4, id, 1);
+              tc::mma_bf16_ts(acc, al + 8 * kk4, bh + 2 * kk4, id, 1);
             }
           }
           tc::mma_commit(&b2_empty[b]);
           tc::mma_commit(&c2_full[b]);
-          if (u == u1 || z != zj) tc::mma_commit(a2_empty);
         }
         zp = z;
         if (++kp == K) {
@@ -349,9 +353,44 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
     const bool rv = r < D2;
     const int half = a.krpE / 2, nbox = a.krpE / 32;
     unsigned char* stg = sm + OFF_STG + r * 128;
+    const int hl = cs >> 5;                    // this warp copies E_top's hi (0) or lo (1) half
+    int za = -1;                               // item whose E_top is in TMEM
+    long long e2n = 0;
     long long i = 0;
     int z = (int)(u0 / KK), kk = (int)(u0 % KK);
     for (long long u = u0; u < u1; ++u, ++i, kk = kk + 1 < KK ? kk + 1 : 0, z = kk ? z : z + 1) {
+      if (z != za) {
+        // first unit of an item: E_top (shared memory, from TMA) becomes the
+        // TMEM A operand of GEMM2.  Every GEMM2 of the previous item has
+        // completed (this group consumed its last accumulator), so the TMEM
+        // region is free; the shared copy is released for the next item.
+        bool ok2 = true;
+        if (et == 0) ok2 = tc::mbar_wait_sleep(a2_full, (uint32_t)(e2n & 1), T12_SLEEP_POLLS);
+        if (!tc::bar_and(2, EPI, ok2)) {
+          if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
+          break;
+        }
+        for (int c = 0; c < a.nchunk; ++c) {
+          const unsigned char* src = sm + OFF_A2 + (2 * hl + c) * A_TILE + row * 128;
+          uint32_t w[32];
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const uint4 v = *reinterpret_cast<const uint4*>(src + ((g ^ (row & 7)) << 4));
+            w[4 * g] = v.x; w[4 * g + 1] = v.y; w[4 * g + 2] = v.z; w[4 * g + 3] = v.w;
+          }
+          tc::tmem_st32(tmem + ((uint32_t)(quarter * 32) << 16) + (hl ? TM_A2L : TM_A2H) +
+                            (uint32_t)(c * 32), w);
+        }
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) {
+          tc::mbar_arrive(a2t_full);
+          tc::mbar_arrive(a2_empty);
+        }
+        ++e2n;
+        za = z;
+      }
       const int b = (int)(i & 1);
       const long long ub = i >> 1;
       bool got = true;
@@ -407,7 +446,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, TM_COLS);
 }
 
 size_t t12_smem_bytes() { return T12_SMEM; }
