@@ -375,19 +375,12 @@ int plan_build(ntu_ctx* c) {
     // Fused t1-t2 (k_t12.cu): Y as the doubled A operand with complex row
     // k*64 + u*D + n (64 rows per k, padding rows zero) and complex column
     // (p,e'); conj(Q) as the B operand with row k'*64 + n'*D + u' and column
-    // (p,e') (written by k_q_split); the result goes to T2s, the B operand of
+    // (p,e') (both written by k_yq); the result goes to T2s, the B operand of
     // h: row (k,k',ht,ht'), complex column (n',n), Re at column c and Im at
     // krpE/2 + c of each half (planar).
     P.krpY = up(2LL * dp * D, 64);
     P.rowsY = 128LL * K;
     P.rowsQ = 64LL * K;
-    const int pY = (int)(2 * P.krpY);
-    P.y2 = P.y;
-    P.y2.rowC = T.add({{dp, 0}, {D, D}, {D, 1}, {K, 64}});
-    P.y2.colC = T.add({{D, 0}});
-    P.y2.rowK = T.add({{dp, D}, {D, 0}, {D, 0}, {K, 0}});
-    P.y2.colK = T.add({{D, 1}});
-    P.y2.mode = 2; P.y2.sC = P.rowsY * pY; P.y2.pitch = pY; P.y2.krp_out = (int)P.krpY;
     // h: C[(hb,hb'),(k,k',ht,ht')] -> join operand: complex column
     // h = (hb,hb',ht,ht'); H_L doubled (A) with complex row (k,k'), H_R plain
     // (B) with row (k',k) so that the join writes g along its rows
@@ -511,35 +504,95 @@ static cudaError_t env_chain(ntu_ctx* c, int n, const void* Ta, const void* Tb, 
 
 // Tensor maps of the split operands (the work space is fixed at init, so
 // the maps are encoded once).
-// conj(Q) as the split B operand of the fused t1-t2: Q[p,e,u,n,k] goes to
-// row k*64 + n*D + u, complex column p*D + e.
-__global__ void k_q_split(long long total, int D, int K, const float2* __restrict__ Q,
-                          __nv_bfloat16* __restrict__ Qs, long long szQ, long long sOut,
-                          int pitch, int krp) {
+// The two operands of GEMM1 of the fused t1-t2 from one read of Q: thread
+// (item, p, u, n, k) loads Q[p,e,u,n,k] for e < D and writes
+//   Y[p,e',u,n,k] = sum_e Q[p,e,u,n,k] E_side[e][e']   (Fig. 4(c))
+// as the doubled split A operand (complex row k*64 + u*D + n, column p*D + e')
+// and conj(Q) as the split B operand (row k*64 + n*D + u, column p*D + e).
+// The sum runs over e in order with the same FMA sequence as k_cgemm.
+__global__ void __launch_bounds__(256) k_yq(long long total, int D, int K, const float2* __restrict__ Q,
+                                            const float2* __restrict__ E, __nv_bfloat16* __restrict__ Ys,
+                                            __nv_bfloat16* __restrict__ Qs, long long rows, long long szQ,
+                                            long long sY, long long sQs, int pitch, int krp) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long item = i / szQ, j = i % szQ;
-    const int k = (int)(j % K);
-    long long r = j / K;
-    const int n = (int)(r % D); r /= D;
-    const int u = (int)(r % D); r /= D;
-    const int e = (int)(r % D);
-    const int p = (int)(r / D);
-    const float2 v = Q[i];
-    store_split(Qs + item * sOut, (long long)k * 64 + n * D + u, (long long)p * D + e, pitch,
-                krp, v.x, -v.y, 0);
+    const long long item = i / rows;
+    int rem = (int)(i % rows);
+    const int k = rem % K; rem /= K;
+    const int n = rem % D; rem /= D;
+    const int u = rem % D;
+    const int p = rem / D;
+    const long long se = (long long)D * D * K;
+    const float2* q = Q + item * szQ + (((long long)p * D * D + u) * D + n) * K + k;
+    const float2* Ei = E + item * (long long)D * D;
+    float2 qe[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) qe[e] = e < D ? q[e * se] : make_float2(0.f, 0.f);
+    __nv_bfloat16* ys = Ys + item * sY;
+    __nv_bfloat16* qs = Qs + item * sQs;
+    const long long ry = (long long)k * 64 + u * D + n, rq = (long long)k * 64 + n * D + u;
+    if (D == 8) {
+      // the eight columns p*8 + e of a row are 32 contiguous bytes of each of
+      // hi and lo: 16-byte stores (rows are pitch = 2 krp BF16 apart, p*8
+      // complex columns are 32-byte aligned)
+      uint32_t yrh[8], yrl[8], yih[8], yil[8], qh[8], ql[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          const float2 a = qe[f], b = Ei[f * 8 + e];
+          re = fmaf(a.x, b.x, re); re = fmaf(-a.y, b.y, re);
+          im = fmaf(a.x, b.y, im); im = fmaf(a.y, b.x, im);
+        }
+        __nv_bfloat16 h0, l0, h1, l1, g0, m0, g1, m1;
+        split_bf16(re, h0, l0);
+        split_bf16(im, h1, l1);
+        yrh[e] = pack_bf16(h0, __hneg(h1)); yrl[e] = pack_bf16(l0, __hneg(l1));
+        yih[e] = pack_bf16(h1, h0);          yil[e] = pack_bf16(l1, l0);
+        split_bf16(qe[e].x, g0, m0);
+        split_bf16(-qe[e].y, g1, m1);
+        qh[e] = pack_bf16(g0, g1); ql[e] = pack_bf16(m0, m1);
+      }
+      __nv_bfloat16* pr = ys + ((ry / 64) * 128 + ry % 64) * pitch + 2 * p * 8;
+      __nv_bfloat16* pi = pr + 64LL * pitch;
+      __nv_bfloat16* pq = qs + rq * pitch + 2 * p * 8;
+      auto st2 = [](__nv_bfloat16* dst, const uint32_t* w) {
+        reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      };
+      st2(pr, yrh); st2(pr + krp, yrl); st2(pi, yih); st2(pi + krp, yil);
+      st2(pq, qh); st2(pq + krp, ql);
+      continue;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (e >= D) break;
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        if (f >= D) break;
+        const float2 a = qe[f], b = Ei[f * D + e];
+        re = fmaf(a.x, b.x, re); re = fmaf(-a.y, b.y, re);
+        im = fmaf(a.x, b.y, im); im = fmaf(a.y, b.x, im);
+      }
+      store_split(ys, ry, (long long)p * D + e, pitch, krp, re, im, 1);
+      store_split(qs, rq, (long long)p * D + e, pitch, krp, qe[e].x, -qe[e].y, 0);
+    }
   }
 }
 
-cudaError_t launch_q_split(ntu_ctx* c, int n, const float2* Q, void* Qs) {
+static cudaError_t launch_yq(ntu_ctx* c, int n, const float2* Q, const float2* E) {
   const Plan& P = c->plan;
-  const long long total = (long long)n * P.szQ;
+  const long long rows = (long long)P.dp * P.D * P.D * P.K, total = (long long)n * rows;
   if (total == 0) return cudaSuccess;
-  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  k_q_split<<<blocks, 256, 0, c->stream>>>(total, P.D, P.K, Q, (__nv_bfloat16*)Qs, P.szQ,
-                                           P.rowsQ * 2 * P.krpY, (int)(2 * P.krpY),
-                                           (int)P.krpY);
-  return after_launch(c, "k_q_split");
+  const long long want = (total + 255) / 256;
+  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  k_yq<<<blocks, 256, 0, c->stream>>>(total, P.D, P.K, Q, E, (__nv_bfloat16*)c->w.Ys,
+                                      (__nv_bfloat16*)c->w.Qs, rows, P.szQ,
+                                      P.rowsY * 2 * P.krpY, P.rowsQ * 2 * P.krpY,
+                                      (int)(2 * P.krpY), (int)P.krpY);
+  return after_launch(c, "k_yq");
 }
 
 int tc_plan_maps(ntu_ctx* c) {
@@ -578,12 +631,10 @@ static cudaError_t env_chain_bf16x3(ntu_ctx* c, int n, const void* Ta, const voi
   RG(run_gemm<float2>(c, P.e2BL, n, Tb, Tb, W.EBLd));
   RG(run_gemm<float2>(c, P.e2TR, n, Ta, Ta, W.ETRd));
   RG(run_gemm<float2>(c, P.e2BR, n, Ta, Ta, W.EBRd));
-  RG(run_gemm<float2>(c, P.y2, n, QA, W.EL, W.Ys));
-  RG(launch_q_split(c, n, (const float2*)QA, W.Qs));
+  RG(launch_yq(c, n, (const float2*)QA, (const float2*)W.EL));
   RG(launch_t12(c, n, P.mapEtopL));
   RG(launch_tc_gemm(c, P.tc_hL, n, W.HLd));
-  RG(run_gemm<float2>(c, P.y2, n, QB, W.ER, W.Ys));
-  RG(launch_q_split(c, n, (const float2*)QB, W.Qs));
+  RG(launch_yq(c, n, (const float2*)QB, (const float2*)W.ER));
   RG(launch_t12(c, n, P.mapEtopR));
   RG(launch_tc_gemm(c, P.tc_hR, n, W.HRs));
   RG(launch_tc_gemm(c, P.tc_join, n, graw));

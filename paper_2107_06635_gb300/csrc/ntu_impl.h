@@ -60,7 +60,6 @@ struct Plan {
   GemmOp join;                          // join of the two halves (Fig. 4(d,e))
   // split-BF16 tensor-core variant (NTU_MIXED_BF16X3)
   GemmOp e2TL, e2BL, e2TR, e2BR;        // edge tensors written as doubled A operands
-  GemmOp y2;                            // Y written as the doubled A operand of the fused t1-t2
   TcOp tc_hL, tc_hR, tc_join;
   long long krpY, rowsY, rowsQ;         // split operands of the fused t1-t2: Y (doubled A), conj(Q) (B)
   CUtensorMap mapYs, mapQs, mapEtopL, mapEtopR;   // TMA maps of the fused t1-t2 (k_t12.cu)
