@@ -3,6 +3,9 @@
 // grouped by kind (D, r); each kind has its own context (plan, tables, work
 // space) on its own stream, forked from and joined back into the caller's
 // stream by events, so the kinds' pipelines run side by side on the SMs.
+// The kinds with the most work per item (the ALS of Fig. 5 grows as K^4 D)
+// get the streams of highest priority, so their long pipelines start first
+// and the lighter kinds fill the SMs they leave idle.
 // The device part of a call -- copies in, every kind's batched update, copies
 // out -- can be captured once as one CUDA graph (the fork becomes parallel
 // branches) for a given set of per-kind counts and replayed afterwards.
@@ -11,6 +14,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <vector>
 
 #include "../../include/ntu.h"
@@ -44,6 +48,7 @@ struct ntu_uneven {
   std::vector<size_t> szT;                // complex entries of one site tensor per kind
   std::vector<double2*> h_in, h_out;      // pinned staging per kind: [Ta | Tb | gates], [Ta' | Tb' | info]
   std::vector<int> staged;                // per-kind counts of the inputs on the device
+  std::vector<int> order;                 // kinds by decreasing work per item (enqueue order)
   CachedGraph g_host, g_dev;              // copies + update; update only
   int launches = 0;                       // kernels queued by the last run
   char err[256] = {0};
@@ -134,7 +139,8 @@ enum : int { PART_IN = 1, PART_UPDATE = 2, PART_OUT = 4 };
 int enqueue(ntu_uneven* u, const std::vector<int>& cnt, int parts, bool per_item) {
   UCK(cudaEventRecord(u->fork, u->stream), "fork event");
   u->launches = 0;
-  for (int k = 0; k < u->nk; ++k) {
+  for (int kk = 0; kk < u->nk; ++kk) {
+    const int k = u->order[kk];
     const int n = cnt[k];
     if (n == 0) continue;
     cudaStream_t s = u->ks[k];
@@ -274,10 +280,25 @@ extern "C" int ntu_uneven_init(int d_phys, int d_anc, int als_sweeps, int precis
   }
   if (cudaEventCreateWithFlags(&u->fork, cudaEventDisableTiming) != cudaSuccess)
     return bail(NTU_ECUDA, "event creation (kind %d, D=%d, r=%d) %s", 0);
+  // priority rank of each kind by its per-item work K^4 D (K = D r)
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);   // hi <= lo: numerically lower is higher
+  std::vector<int> prio(n_kinds, prio_lo);
+  u->order.assign(n_kinds, 0);
+  for (int k = 0; k < n_kinds; ++k) {
+    const double wk = std::pow((double)D[k] * r[k], 4) * D[k];
+    int heavier = 0;                      // rank of kind k by decreasing work, ties by index
+    for (int j = 0; j < n_kinds; ++j) {
+      const double wj = std::pow((double)D[j] * r[j], 4) * D[j];
+      heavier += wj > wk || (wj == wk && j < k);
+    }
+    prio[k] = prio_hi + heavier < prio_lo ? prio_hi + heavier : prio_lo;
+    u->order[heavier] = k;
+  }
   for (int k = 0; k < n_kinds; ++k) {
     cudaStream_t s = nullptr;
     cudaEvent_t e = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio[k]) != cudaSuccess)
       return bail(NTU_ECUDA, "stream of kind %d (D=%d, r=%d) %s", k);
     u->ks.push_back(s);
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
