@@ -537,6 +537,43 @@ def run_ours(args):
         cx.close()
     fp64 = others.get("fp64_path")
 
+    # the metric names D=6 as well: the same batch and sweeps at D=6, this
+    # precision and the FP64 path (device-resident, L2 flushed per step)
+    def measure_d(Dm, prec, steps, warmup):
+        ta_h, tb_h, g_h = I.batch_items(5 + 1000 * rank, B, 2, Dm, I.zz_gate(0.01))
+        ta, tb, gg = (torch.from_numpy(x).cuda() for x in (ta_h, tb_h, g_h))
+        oa, ob = torch.empty_like(ta), torch.empty_like(tb)
+        inf = torch.empty((B, 4), dtype=torch.float64, device="cuda")
+        cx = ntu.Context(Dm, 2, 1, r, S, prec, 4, 15 if prec == ntu.NTU_FP64 else 8, B,
+                         stream=stream.cuda_stream)
+        ts = []
+        for i in range(warmup + steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cx.batch_update_dev(B, ta, tb, gg, oa, ob, inf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            if i >= warmup:
+                ts.append(e0.elapsed_time(e1))
+        cx.sync()
+        cx.close()
+        ms = max_over_ranks(statistics.mean(ts))
+        return {"value": world * B / (ms / 1e3), "unit": "bond updates/s", "ms_per_step": ms}
+
+    d6 = None
+    if D != 6 and not args.no_d6:
+        d6 = {"D": 6, "batch_per_gpu": B, "path": args.precision,
+              **measure_d(6, head, args.steps, args.warmup)}
+        if not args.no_fp64 and head != ntu.NTU_FP64:
+            f6 = measure_d(6, ntu.NTU_FP64, args.fp64_steps, 1)
+            d6["fp64_path"] = f6
+            d6["speedup_vs_fp64"] = d6["value"] / f6["value"]
+
     if rank != 0:
         return
 
@@ -574,6 +611,7 @@ def run_ours(args):
         "solver_paths": paths_mixed,
         **others,
         "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+        "d6": d6,
         "e2e": {"value": world * B / e2e_s, "unit": "bond updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -598,6 +636,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-d6", action="store_true", help="skip the D=6 lines of the metric")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
