@@ -380,3 +380,25 @@ def test_golden_one_step_d3_regression():
         assert abs(info.delta - ref["bonds"][b]["delta"]) < 1e-12
     Aref = np.array(ref["A_after"][0]) + 1j * np.array(ref["A_after"][1])
     assert np.linalg.norm(A.reshape(-1) - Aref) < 1e-10
+
+
+def test_golden_quench_trajectory_regression():
+    """The stored config-2 trajectory (tests/golden/quench_d4.json) is the
+    oracle's: its first three steps are recomputed and agree to 1e-10, and
+    after one step <sigma_x> = 1 - 8 dt^2 + O(dt^4) (closed form: for the
+    polarised start on the square lattice, [H, X_i] = -2i J sum_j Y_i Z_j over
+    the four neighbours, so d<X>/dt = 0 and d^2<X>/dt^2 = -16 J^2 at t = 0;
+    the field term commutes with X).  Observed 5e-7 from the closed form with
+    the seeded 1e-2 admixture; a doubled gate angle would be off by 2.4e-3."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "quench_d4.json")))
+    gates2, gate1 = I.tfim_real_time_gates(ref["h"], ref["dt"])
+    cfg = O.Config(D=4, r=2, sweeps=10)
+    A, B = I.quench_start(4)
+    for s in range(3):
+        A, B, _ = O.ntu_step(A, B, gates2, gate1, cfg)
+        assert abs(O.measure(A, B, 0, I.pauli("X"), 1).real - ref["sx_A"][s]) < 1e-10
+        assert abs(O.measure(A, B, 1, I.pauli("X"), 1).real - ref["sx_B"][s]) < 1e-10
+    assert abs(ref["sx_A"][0] - (1 - 8 * ref["dt"] ** 2)) < 1e-5
+    assert abs(ref["sx_B"][0] - (1 - 8 * ref["dt"] ** 2)) < 1e-5
