@@ -124,20 +124,23 @@ void carve(ntu_ctx* c, Carver& cv) {
   W.gtau = cv.take<double2>(n * P.ng);
   W.gp = cv.take<double2>(n * P.ng);
   W.diag = cv.take<double>(n * 3);
-  W.x0 = cv.take<double2>(n * P.ng);
-  W.gx0 = cv.take<double2>(n * P.ng);
-  W.Tm = cv.take<double2>(n * (size_t)P.ng * P.nA);
-  W.gA = cv.take<double2>(n * (size_t)P.nA * P.nA);
-  W.gC = cv.take<double2>(n * (size_t)P.nA * P.nA);
-  W.jv = cv.take<double2>(n * P.nA);
-  W.pv = cv.take<double2>(n * P.nA);
-  W.tauv = cv.take<double2>(n * P.nA);
-  W.dv = cv.take<double>(n * P.nA);
-  W.ev = cv.take<double>(n * P.nA);
+  // ALS scratch private to each CTA: an item's ALS may run on als_split CTAs
+  const size_t na = n * (size_t)W.als_split;
+  W.x0 = cv.take<double2>(na * P.ng);
+  W.gx0 = cv.take<double2>(na * P.ng);
+  W.Tm = cv.take<double2>(na * (size_t)P.ng * P.nA);
+  W.gA = cv.take<double2>(na * (size_t)P.nA * P.nA);
+  W.gC = cv.take<double2>(na * (size_t)P.nA * P.nA);
+  W.jv = cv.take<double2>(na * P.nA);
+  W.pv = cv.take<double2>(na * P.nA);
+  W.tauv = cv.take<double2>(na * P.nA);
+  W.dv = cv.take<double>(na * P.nA);
+  W.ev = cv.take<double>(na * P.nA);
   W.rotcap = 6 * P.nA * P.nA + 64;
-  W.rc = cv.take<double>(n * W.rotcap);
-  W.rs = cv.take<double>(n * W.rotcap);
-  W.rk = cv.take<int>(n * W.rotcap);
+  W.rc = cv.take<double>(na * W.rotcap);
+  W.rs = cv.take<double>(na * W.rotcap);
+  W.rk = cv.take<int>(na * W.rotcap);
+  W.als_sync = cv.take<int>(n);
   W.MA = cv.take<double2>(n * (size_t)P.K * P.D);
   W.MB = cv.take<double2>(n * (size_t)P.K * P.D);
   W.info = cv.take<double>(n * 4 + 16);
@@ -171,7 +174,8 @@ static int check_status(ntu_ctx* c) {
     cudaMemcpy(c->d_status, zero, sizeof(zero), cudaMemcpyHostToDevice);
     return fail(c, st[0], "device raised status %d (%s; reason bits 0x%x: 1 SVD non-finite, "
                 "2 ALS eigen-solver, 4 ALS non-finite error, 8 repair eigen-solver, "
-                "16 metric trace not positive)", st[0],
+                "16 metric trace not positive, 32 tensor-core wait, 64 ALS exchange "
+                "between the CTAs of an item)", st[0],
                 st[0] == NTU_ENUMERIC ? "non-finite value or solver non-convergence"
                                       : "bounded wait ran out", st[1]);
   }
@@ -180,6 +184,12 @@ static int check_status(ntu_ctx* c) {
 
 // ------------------------------------------------------------- lifecycle
 extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
+  return ntu::init_context(cfg, stream, out, 4);
+}
+
+// ntu_init with a cap on the number of CTAs one item's ALS may use (the
+// uneven-batch driver lets only its heaviest kind split).
+int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int max_split) {
   if (!cfg || !out) return fail(nullptr, NTU_EINVAL, "ntu_init: NULL argument");
   *out = nullptr;
   const ntu_config& f = *cfg;
@@ -215,6 +225,19 @@ extern "C" int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out) {
   int st = plan_build(c);
   if (st != NTU_OK) { ntu_destroy(c); return fail(nullptr, st, "plan tables"); }
   c->w.cap = f.max_batch;
+  // Batches too small to fill the GPU at three ALS CTAs per SM let each
+  // item's ALS run on 2 or 4 CTAs (mixed contexts, whose reduced-metric
+  // build is split between them; see k_als).
+  c->w.als_split = 1;
+  if (f.precision != NTU_FP64) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+      const int room = 3 * sms / f.max_batch;
+      c->w.als_split = room >= 4 ? 4 : (room >= 2 ? 2 : 1);
+      while (c->w.als_split > max_split && c->w.als_split > 1) c->w.als_split >>= 1;
+    }
+  }
   Carver dry;
   carve(c, dry);
   void* base = nullptr;

@@ -242,7 +242,36 @@ struct AlsArgs {
   int df;                      // build the reduced metric in double-FP32 arithmetic
   float4* gdf;                 // n x ng^2 scratch: g split into FP32 pairs
   float4* gdfT;                // the same with kA and kB swapped in rows and columns
+  int split;                   // CTAs per item (a cluster); the private scratch above
+                               // (x0 ... rk, gA, gC) has n * split copies
+  int* sync;                   // n exchange counters, zero at launch (split > 1)
 };
+
+// Rendezvous of the `split` CTAs of one item (one thread-block cluster, so
+// they run at the same time): each adds one to the item's counter and waits
+// until all have, for the phase-th time; global writes made before are then
+// visible to all.  The wait is bounded: on running out it raises
+// ST_TIMEOUT / WHY_ALS_SYNC and goes on (the results are then flagged).
+__device__ void als_exchange(const AlsArgs& a, long long item, int& phase) {
+  __syncthreads();
+  ++phase;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(a.sync + item, 1);
+    const int target = phase * a.split;
+    const volatile int* cnt = a.sync + item;
+    long long it = 0;
+    while (*cnt < target) {
+      if (++it > (1ll << 23)) {
+        raise_status(a.status, ST_TIMEOUT, WHY_ALS_SYNC);
+        break;
+      }
+      __nanosleep(256);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
 
 // X = MA MB^T -> SVD -> (MA, MB) by mode: 0 tilt before the A step
 // (U S, conj(V)), 1 tilt before the B step (U, conj(V) S), 2 balance
@@ -356,14 +385,14 @@ __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
 // exact scaling.  gdfT[(kB',kA'),(kB,kA)] = gdf[(kA',kB'),(kA,kB)] lets the B
 // step read its blocks along rows as the A step does.  Returns e.
 __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, float4* gdfT, int ng,
-                           int K) {
+                           int K, bool write) {
   const int tid = threadIdx.x;
   const size_t nn = (size_t)ng * ng;
   double mx = 0.0;
   for (size_t i = tid; i < nn; i += NTU_CTA) mx = fmax(mx, fmax(fabs(g[i].x), fabs(g[i].y)));
   mx = block_max(mx, sm.red);
   const int e = (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ilogb(mx) + 1 : 0;
-  for (size_t i = tid; i < nn; i += NTU_CTA) {
+  for (size_t i = tid; i < nn && write; i += NTU_CTA) {
     double2 v = g[i];
     const float4 d = df_split(make_double2(scalbn(v.x, -e), scalbn(v.y, -e)));
     gdf[i] = d;
@@ -384,8 +413,14 @@ __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, float4*
 // products of the conjugate-gradient solve), mirrored into the upper
 // triangle.  Every element of g is read once per call and no intermediate
 // leaves the SM.  F (the isometric factor) is split into als_fdf(sm).
+// When an item's ALS runs on `split` CTAs, CTA `rank` builds every
+// split-th block and writes it into all `split` private copies of gX and
+// gXdf (`cstride` elements apart, the first at gX, gXdf).
+template <bool SPLIT>
 __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gdf,
-                               const float4* gdfT, int e, int side, double2* gX, float4* gXdf) {
+                               const float4* gdfT, int e, int side, double2* gX, float4* gXdf,
+                               int rank_, int split_, long long cstride) {
+  const int rank = SPLIT ? rank_ : 0, split = SPLIT ? split_ : 1;
   const int tid = threadIdx.x, K = a.K, D = a.D, ng = a.ng, nA = a.nA;
   const int warp = tid >> 5, lane = tid & 31;
   const double2* F = side == 0 ? sm.MB : sm.MA;
@@ -398,7 +433,7 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
   for (int i = tid; i < K * D; i += NTU_CTA) als_fdf(sm)[i] = df_split(F[i]);
   __syncthreads();
   const int nblk = K * (K + 1) / 2;
-  for (int blk = warp; blk < nblk; blk += NTU_WARPS) {
+  for (int blk = warp + NTU_WARPS * rank; blk < nblk; blk += NTU_WARPS * split) {
     int f1 = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
     while ((f1 + 1) * (f1 + 2) / 2 <= blk) ++f1;
     while (f1 > 0 && f1 * (f1 + 1) / 2 > blk) --f1;
@@ -436,11 +471,15 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
       const int row = f1 * D + q1, col = f * D + q;
       double2 v = df_join(acc);
       if (e != 0) v = make_double2(scalbn(v.x, e), scalbn(v.y, e));
-      gX[(size_t)col * nA + row] = v;
-      gXdf[(size_t)col * nA + row] = acc;
-      if (row != col) {                                  // upper triangle
-        gX[(size_t)row * nA + col] = cconj(v);
-        gXdf[(size_t)row * nA + col] = make_float4(acc.x, -acc.y, acc.z, -acc.w);
+      for (int cp = 0; cp < split; ++cp) {
+        double2* gXc = gX + cp * cstride;
+        float4* gXdfc = gXdf + cp * cstride;
+        gXc[(size_t)col * nA + row] = v;
+        gXdfc[(size_t)col * nA + row] = acc;
+        if (row != col) {                                // upper triangle
+          gXc[(size_t)row * nA + col] = cconj(v);
+          gXdfc[(size_t)row * nA + col] = make_float4(acc.x, -acc.y, acc.z, -acc.w);
+        }
       }
     }
     __syncwarp();
@@ -810,32 +849,42 @@ __device__ void als_solve(AlsShared& sm, const AlsArgs& a, int side, double2* gX
 
 // MINB: CTAs per SM the register budget is sized for (2: 128 registers, no
 // spills; 3: 80 registers, for batches of more than two items per SM).
-template <int MINB>
+template <int MINB, bool SPLIT>
 __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AlsShared& sm = *reinterpret_cast<AlsShared*>(smem_raw);
   const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
-  const long long item = blockIdx.x;
+  // an item's ALS runs on a.split CTAs (one cluster, rank = position in it):
+  // all of them carry out the whole ALS on identical data, each in its own
+  // scratch copy (index vitem), so their control flow is identical; only
+  // the reduced-metric build is divided between them, and rank 0 writes the
+  // results
+  const int split = SPLIT ? a.split : 1, rank = SPLIT ? (int)(blockIdx.x % split) : 0;
+  const long long item = SPLIT ? blockIdx.x / split : blockIdx.x, vitem = blockIdx.x;
   const int K = a.K, D = a.D, ng = a.ng, nA = a.nA;
   const double2* g = a.g + item * (long long)ng * ng;
   const double2* RA = a.RA + item * K * K;
   const double2* RB = a.RB + item * K * K;
-  double2* x0 = a.x0 + item * ng;
-  double2* gx0 = a.gx0 + item * ng;
-  double2* Tm = a.Tm + item * (long long)ng * nA;
-  double2* gX = a.gA + item * (long long)nA * nA;
-  double2* jv = a.jv + item * nA;
-  double2* pv = a.pv + item * nA;
-  double2* tauv = a.tauv + item * nA;
-  double* dv = a.dv + item * nA;
-  double* ev = a.ev + item * nA;
+  double2* x0 = a.x0 + vitem * ng;
+  double2* gx0 = a.gx0 + vitem * ng;
+  double2* Tm = a.Tm + vitem * (long long)ng * nA;
+  double2* gX = a.gA + vitem * (long long)nA * nA;
+  double2* jv = a.jv + vitem * nA;
+  double2* pv = a.pv + vitem * nA;
+  double2* tauv = a.tauv + vitem * nA;
+  double* dv = a.dv + vitem * nA;
+  double* ev = a.ev + vitem * nA;
   RotLog log;
-  log.c = a.rc + item * (long long)a.rotcap;
-  log.s = a.rs + item * (long long)a.rotcap;
-  log.k = a.rk + item * (long long)a.rotcap;
+  log.c = a.rc + vitem * (long long)a.rotcap;
+  log.s = a.rs + vitem * (long long)a.rotcap;
+  log.k = a.rk + vitem * (long long)a.rotcap;
   log.cap = a.rotcap;
   log.count = 0;
-  double2* gC = a.gC + item * (long long)nA * nA;
+  double2* gC = a.gC + vitem * (long long)nA * nA;
+  const long long nA2 = (long long)nA * nA;
+  double2* gX0 = a.gA + item * split * nA2;                 // the item's first copy
+  double2* gC0 = a.gC + item * split * nA2;
+  int phase = 0;
   const double tau_max = als_tau(a.kmin < 0 ? 0 : a.kmin);
   if (tid == 0) { sm.err = 0; sm.n_cg = 0; sm.n_fast = 0; sm.n_eig = 0; sm.ge = 0; }
   // X0 = R_A R_B^T, x0 = vec(X0) with kA slow
@@ -867,8 +916,9 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     gdf = a.gdf + item * (long long)ng * ng;
     gdfT = a.gdfT + item * (long long)ng * ng;
     ge = als_split_g(sm, g, a.gdf + item * (long long)ng * ng, a.gdfT + item * (long long)ng * ng,
-                     ng, K);
+                     ng, K, rank == 0);
     if (tid == 0) sm.ge = ge;
+    if (split > 1) als_exchange(a, item, phase);          // the split g is written
   }
   // SVDU start (Fig. 2(c,d)).  X0 = U S V^H gives the balanced start
   // (U sqrt(S), conj(V) sqrt(S)) whose first tilt is (U S, conj(V)): with
@@ -877,9 +927,16 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   for (int s = 0; s < a.sweeps; ++s) {
     for (int side = 0; side < 2; ++side) {
       if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
-      if (a.df)
-        als_reduced_df(sm, a, gdf, gdfT, ge, side, gX, reinterpret_cast<float4*>(gC));
-      else als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
+      if (a.df) {
+        // every CTA is done with its copy of the last reduced metric before
+        // any writes the next one, and all blocks are in before anyone reads
+        if (split > 1) als_exchange(a, item, phase);
+        als_reduced_df<SPLIT>(sm, a, gdf, gdfT, ge, side, split > 1 ? gX0 : gX,
+                       reinterpret_cast<float4*>(split > 1 ? gC0 : gC), rank, split, nA2);
+        if (split > 1) als_exchange(a, item, phase);
+      } else {
+        als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
+      }
       als_source(sm, a, side, jv, gx0);
       if (!als_solve_chol(sm, a, side, gX, gC, jv, tau_max)) {
         als_mirror(gX, nA);
@@ -907,6 +964,7 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     if (lid == 0) eps += cmulc(xv[r], acc).x;
   }
   eps = block_sum(eps, sm.red);
+  if (rank != 0) return;                                   // rank 0 writes the results
   double2* MAo = a.MA + item * K * D;
   double2* MBo = a.MB + item * K * D;
   for (int idx = tid; idx < K * D; idx += NTU_CTA) { MAo[idx] = sm.MA[idx]; MBo[idx] = sm.MB[idx]; }
@@ -971,16 +1029,44 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
+  // a batch that leaves SMs idle gives each item 2 or 4 CTAs (one cluster)
+  int split = a.df ? W.als_split : 1;
+  while (split > 1 && (long long)n * split > 3LL * sms) split >>= 1;
+  a.split = split;
+  a.sync = W.als_sync;
+  if (split > 1) {
+    cudaError_t e = cudaMemsetAsync(W.als_sync, 0, sizeof(int) * (size_t)n, c->stream);
+    if (e != cudaSuccess) return e;
+    cudaFuncSetAttribute(k_als<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_als<2, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(n * split), 1, 1);
+    cfg.blockDim = dim3(NTU_CTA, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)split;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_als<2, true>, a);
+    if (e != cudaSuccess) return e;
+    return after_launch(c, "k_als (cluster)");
+  }
   if (n > 2 * sms) {
-    cudaFuncSetAttribute(k_als<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_als<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_als<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_als<3, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    k_als<3><<<n, NTU_CTA, sm, c->stream>>>(a);
+    k_als<3, false><<<n, NTU_CTA, sm, c->stream>>>(a);
   } else {
-    cudaFuncSetAttribute(k_als<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_als<2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_als<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_als<2, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    k_als<2><<<n, NTU_CTA, sm, c->stream>>>(a);
+    k_als<2, false><<<n, NTU_CTA, sm, c->stream>>>(a);
   }
   return after_launch(c, "k_als");
 }

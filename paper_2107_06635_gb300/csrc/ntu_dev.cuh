@@ -229,7 +229,7 @@ enum { ST_NUMERIC = 4, ST_TIMEOUT = 5 };
 // Reason bits recorded next to the status word (status[1]).
 enum {
   WHY_SVD_NONFINITE = 1, WHY_ALS_QR = 2, WHY_ALS_NONFINITE = 4, WHY_REPAIR_QR = 8,
-  WHY_REPAIR_TRACE = 16, WHY_TC_WAIT = 32
+  WHY_REPAIR_TRACE = 16, WHY_TC_WAIT = 32, WHY_ALS_SYNC = 64
 };
 __device__ __forceinline__ void raise_status(int* status, int code, int why = 0) {
   if (status) {

@@ -87,10 +87,13 @@ struct Work {
   double2 *gtau, *gp;         // reflector factors, vector scratch (ng each)
   double *diag;               // 3 per item
   // ALS scratch
+  // (private per CTA: cap x als_split copies, see k_als)
   double2 *x0, *gx0, *Tm, *gA, *gC, *jv, *pv, *tauv;
   double *dv, *ev, *rc, *rs;
   int *rk;
   int rotcap;
+  int als_split;              // most CTAs one item's ALS may use (1, 2 or 4)
+  int* als_sync;              // cap exchange counters of the split ALS
   double2 *MA, *MB;
   double *info;               // 4 per item
   // outputs of a full update when the caller gives none
@@ -136,6 +139,7 @@ cudaError_t after_launch(ntu_ctx* c, const char* name);
 
 // plans and tables (k_env.cu)
 int plan_build(ntu_ctx* c);
+int init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int max_split);
 void plan_free(ntu_ctx* c);
 
 // launchers (return cudaError_t of the launch; they also count launches)

@@ -310,7 +310,9 @@ extern "C" int ntu_uneven_init(int d_phys, int d_anc, int als_sweeps, int precis
     cf.als_sweeps = als_sweeps; cf.precision = precision;
     cf.tau_kmin = tau_kmin; cf.tau_kmax = tau_kmax; cf.max_batch = max_items[k];
     ntu_ctx* c = nullptr;
-    int st = ntu_init(&cf, s, &c);
+    // kinds share the GPU, so splitting an item's ALS over several CTAs pays
+    // only where it shortens the critical path: the heaviest kind
+    int st = ntu::init_context(&cf, s, &c, u->order[0] == k ? 4 : 1);
     if (st != NTU_OK) {
       snprintf(u->err, sizeof(u->err), ": %s", ntu_last_error(nullptr));
       return bail(st, "kind %d (D=%d, r=%d)%s", k);

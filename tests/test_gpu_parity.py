@@ -703,3 +703,26 @@ def test_purification_full_trajectory(precision, tol):
         ctx.step(gates2, gate1)
         assert abs(ctx.measure(0, I.pauli("X")).real - gold["sx_A"][s]) < tol, s
         assert abs(ctx.measure(0, I.pauli("Z")).real - gold["sz_A"][s]) < tol, s
+
+
+@pytest.mark.parametrize("precision", [2, 1])
+def test_split_als_identical_to_single_cta(precision):
+    """A batch too small to fill the GPU runs each item's ALS on a cluster of
+    CTAs that divide the reduced-metric build (a context for at most 3 items
+    splits 4 ways; one for 240 items does not split).  The blocks are the
+    same arithmetic either way, so the bond updates agree bit for bit; both
+    match the oracle within the mixed-path budget.  r=4 gives K=16, D=4."""
+    n = 3
+    rng = np.random.default_rng(910)
+    Ta = np.stack([I.random_site_tensor(rng, 2, 4) for _ in range(n)])
+    Tb = np.stack([I.random_site_tensor(rng, 2, 4) for _ in range(n)])
+    G = np.stack([I.heisenberg_gate(0.01)] * n)
+    small = _ctx(4, 4, precision=precision, max_batch=n, kmax=8)
+    big = _ctx(4, 4, precision=precision, max_batch=240, kmax=8)
+    a1, b1, i1 = small.batch_update_host(Ta, Tb, G)
+    a2, b2, i2 = big.batch_update_host(Ta, Tb, G)
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2) and np.array_equal(i1, i2)
+    cfg = O.Config(D=4, r=4, tau_exponents=tuple(range(4, 9)))
+    for i in range(n):
+        A2, B2, inf = O.bond_update(Ta[i], Tb[i], G[i], cfg)
+        assert abs(i1[i, 1] - inf.delta) <= 1e-2 * inf.delta
