@@ -247,6 +247,34 @@ struct AlsArgs {
   int* sync;                   // n exchange counters, zero at launch (split > 1)
 };
 
+// out = g v in double-FP32 products from the split copy gdf = g 2^-ge (mixed
+// contexts): v is split into the SVD array A (free outside the tilts), one
+// warp per row, two accumulators per lane, rescaled by 2^ge.
+__device__ void als_gmat_df(AlsShared& sm, const float4* gdf, int ge, const double2* v,
+                            double2* out, int ng) {
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
+  float4* vdf = reinterpret_cast<float4*>(sm.S.A);           // ng <= 1024
+  for (int i = tid; i < ng; i += NTU_CTA) vdf[i] = df_split(v[i]);
+  __syncthreads();
+  for (int r = wid; r < ng; r += NTU_WARPS) {
+    const float4* gr = gdf + (size_t)r * ng;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+    for (int c = lid; c < ng; c += 64) {
+      df_cmac<false>(a0, gr[c], vdf[c]);
+      if (c + 32 < ng) df_cmac<false>(a1, gr[c + 32], vdf[c + 32]);
+    }
+    df_add1(a0.x, a0.z, a1.x, a1.z);
+    df_add1(a0.y, a0.w, a1.y, a1.w);
+    a0 = df_warp_sum(a0);
+    if (lid == 0) {
+      double2 y = df_join(a0);
+      if (ge != 0) y = make_double2(scalbn(y.x, ge), scalbn(y.y, ge));
+      out[r] = y;
+    }
+  }
+  __syncthreads();
+}
+
 // Rendezvous of the `split` CTAs of one item (one thread-block cluster, so
 // they run at the same time): each adds one to the item's counter and waits
 // until all have, for the phase-th time; global writes made before are then
@@ -895,21 +923,6 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     x0[idx] = acc;
   }
   __syncthreads();
-  // gx0 = g x0, eps0 = x0^H g x0
-  double e0 = 0.0;
-  for (int r = wid; r < ng; r += NTU_WARPS) {
-    const double2* gr = g + (size_t)r * ng;
-    double2 acc = cz();
-    for (int c = lid; c < ng; c += 32) acc = cfma(gr[c], x0[c], acc);
-    acc = warp_sum2(acc);
-    if (lid == 0) {
-      gx0[r] = acc;
-      e0 += cmulc(x0[r], acc).x;
-    }
-  }
-  e0 = block_sum(e0, sm.red);
-  if (tid == 0) sm.eps0 = e0;
-  __syncthreads();
   const float4 *gdf = nullptr, *gdfT = nullptr;
   int ge = 0;
   if (a.df) {
@@ -920,6 +933,26 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     if (tid == 0) sm.ge = ge;
     if (split > 1) als_exchange(a, item, phase);          // the split g is written
   }
+  // gx0 = g x0 (double-FP32 products on the mixed contexts), eps0 = x0^H g x0
+  double e0 = 0.0;
+  if (a.df) {
+    als_gmat_df(sm, gdf, ge, x0, gx0, ng);
+    for (int r = tid; r < ng; r += NTU_CTA) e0 += cmulc(x0[r], gx0[r]).x;
+  } else {
+    for (int r = wid; r < ng; r += NTU_WARPS) {
+      const double2* gr = g + (size_t)r * ng;
+      double2 acc = cz();
+      for (int c = lid; c < ng; c += 32) acc = cfma(gr[c], x0[c], acc);
+      acc = warp_sum2(acc);
+      if (lid == 0) {
+        gx0[r] = acc;
+        e0 += cmulc(x0[r], acc).x;
+      }
+    }
+  }
+  e0 = block_sum(e0, sm.red);
+  if (tid == 0) sm.eps0 = e0;
+  __syncthreads();
   // SVDU start (Fig. 2(c,d)).  X0 = U S V^H gives the balanced start
   // (U sqrt(S), conj(V) sqrt(S)) whose first tilt is (U S, conj(V)): with
   // sweeps to run, the start goes straight to the tilted pair.
@@ -956,12 +989,17 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   }
   __syncthreads();
   double eps = 0.0;
-  for (int r = wid; r < ng; r += NTU_WARPS) {
-    const double2* gr = g + (size_t)r * ng;
-    double2 acc = cz();
-    for (int c = lid; c < ng; c += 32) acc = cfma(gr[c], xv[c], acc);
-    acc = warp_sum2(acc);
-    if (lid == 0) eps += cmulc(xv[r], acc).x;
+  if (a.df) {
+    als_gmat_df(sm, gdf, ge, xv, gx0, ng);                 // gx0 is free by now
+    for (int r = tid; r < ng; r += NTU_CTA) eps += cmulc(xv[r], gx0[r]).x;
+  } else {
+    for (int r = wid; r < ng; r += NTU_WARPS) {
+      const double2* gr = g + (size_t)r * ng;
+      double2 acc = cz();
+      for (int c = lid; c < ng; c += 32) acc = cfma(gr[c], xv[c], acc);
+      acc = warp_sum2(acc);
+      if (lid == 0) eps += cmulc(xv[r], acc).x;
+    }
   }
   eps = block_sum(eps, sm.red);
   if (rank != 0) return;                                   // rank 0 writes the results
