@@ -114,16 +114,21 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
     }
     return;
   }
+  // an FP32 raw metric (mixed contexts) is certified in double-FP32
+  // arithmetic, which resolves it far below its own rounding; FP64 otherwise
+  constexpr bool kDf = std::is_same<C2in, float2>::value;
   for (size_t idx = tid; idx < nn; idx += NTU_CTA) {
     int r = idx / ng, c = idx % ng;
     double2 a = ld2(gr + idx), b = ld2(gr + (size_t)c * ng + r);
     double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
     gi[idx] = h;
-    sc[(size_t)c * ng + r] = h;          // column-major copy
+    if (kDf) reinterpret_cast<float4*>(sc)[(size_t)c * ng + r] = df_split(h);
+    else sc[(size_t)c * ng + r] = h;     // column-major copy
   }
   // 2. Cholesky of the lower triangle certifies positive definiteness
   __syncthreads();
-  int ok = cta_cholesky(sc, ng, 0.0, &okflag);
+  int ok = kDf ? cta_cholesky_df(reinterpret_cast<float4*>(sc), ng, &okflag)
+               : cta_cholesky(sc, ng, 0.0, &okflag);
   if (tid == 0 && paths) atomicAdd(paths + (ok ? 4 : 5), 1);
   double ratio = __longlong_as_double(0x7ff8000000000000ULL);   // NaN
   if (!ok) {

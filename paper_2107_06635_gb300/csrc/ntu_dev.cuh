@@ -739,6 +739,53 @@ __device__ inline int cta_cholesky(double2* __restrict__ A, int n, double shift,
   return ok;
 }
 
+// cta_cholesky in double-FP32 arithmetic (A column-major as FP32 pairs,
+// (re_hi, im_hi, re_lo, im_lo), lower triangle, no shift): the same
+// right-looking steps, with each pivot's square root and reciprocal taken
+// in FP64 from its exact double value.  Returns 1 if every pivot was positive
+// and finite.  Used as the positive-definiteness certificate where the
+// metric itself carries FP32 rounding.
+__device__ inline int cta_cholesky_df(float4* __restrict__ A, int n, int* flag) {
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
+  if (tid == 0) *flag = 1;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const float4 dj = A[(size_t)j * n + j];
+    const double piv = (double)dj.x + (double)dj.z;
+    if (!(piv > 0.0) || !isfinite(piv)) { if (tid == 0) *flag = 0; break; }
+    const double sp = sqrt(piv), rp = 1.0 / sp;
+    const float rh = (float)rp, rl = (float)(rp - (double)rh);
+    const float4 rdf = make_float4(rh, 0.f, rl, 0.f);
+    float4* cj = A + (size_t)j * n;
+    __syncthreads();
+    if (tid == 0) {
+      const float sh = (float)sp;
+      cj[j] = make_float4(sh, 0.f, (float)(sp - (double)sh), 0.f);
+    }
+    for (int i = j + 1 + tid; i < n; i += NTU_CTA) {
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      df_cmac<false>(acc, cj[i], rdf);
+      cj[i] = acc;
+    }
+    __syncthreads();
+    for (int k = j + 1 + wid; k < n; k += NTU_WARPS) {
+      const float4 lk = cj[k];
+      float4* ck = A + (size_t)k * n;
+      for (int i = k + lid; i < n; i += 32) {
+        const float4 ci = cj[i];
+        float4 acc = ck[i];
+        df_cmac<true>(acc, lk, make_float4(-ci.x, -ci.y, -ci.z, -ci.w));   // -= c_i conj(l_k)
+        ck[i] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  int ok = *flag;
+  __syncthreads();
+  return ok;
+}
+
 // Solve (L L^H) x = b in place with the factor from cta_cholesky, by one
 // warp (no CTA barriers): lane l owns the entries i = l (mod 32) of b, which
 // lives in shared memory.  Must be called by all 32 lanes of one warp.

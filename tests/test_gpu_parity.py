@@ -726,3 +726,28 @@ def test_split_als_identical_to_single_cta(precision):
     for i in range(n):
         A2, B2, inf = O.bond_update(Ta[i], Tb[i], G[i], cfg)
         assert abs(i1[i, 1] - inf.delta) <= 1e-2 * inf.delta
+
+
+def test_mixed_repair_double_fp32_certificate():
+    """Split-BF16 context, D=4 with the rank-4 Heisenberg gate: the metric
+    (entries at the scales 1 and theta^2 of the gate's Schmidt values) is not
+    diagonally dominant, so the repair certifies it by the double-FP32
+    Cholesky factorisation (counted under repair_cholesky) and writes g/tr;
+    the bond update matches the oracle within the mixed-path budget."""
+    n = 2
+    rng = np.random.default_rng(920)
+    Ta = np.stack([I.random_site_tensor(rng, 2, 4) for _ in range(n)])
+    Tb = np.stack([I.random_site_tensor(rng, 2, 4) for _ in range(n)])
+    G = np.stack([I.heisenberg_gate(0.01)] * n)
+    ctx = _ctx(4, 4, precision=2, max_batch=n, kmax=8)
+    ctx.solver_paths()
+    a, b, info = ctx.batch_update_host(Ta, Tb, G)
+    paths = ctx.solver_paths()
+    assert paths["repair_cholesky"] == n and paths["repair_eigen"] == 0, paths
+    cfg = O.Config(D=4, r=4, tau_exponents=tuple(range(4, 9)))
+    for i in range(n):
+        A2, B2, inf = O.bond_update(Ta[i], Tb[i], G[i], cfg)
+        assert abs(info[i, 1] - inf.delta) <= 1e-2 * inf.delta
+        pair = np.einsum("plurn,qrvwx->plunqvwx", a[i], b[i])
+        ref = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
+        assert _rel(pair, ref) < 1e-4
