@@ -631,7 +631,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=8)
     ap.add_argument("--r", type=int, default=2)
-    ap.add_argument("--batch", type=int, default=None, help="default 456 (uniform), 512 (uneven)")
+    ap.add_argument("--batch", type=int, default=None, help="default 912 (uniform), 512 (uneven)")
     ap.add_argument("--sweeps", type=int, default=None, help="default 10 (uniform), 8 (uneven)")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -645,7 +645,7 @@ def main():
     args = ap.parse_args()
     uneven = args.workload == "uneven"
     if args.batch is None:
-        args.batch = 512 if uneven else 456
+        args.batch = 512 if uneven else 912
     if args.sweeps is None:
         args.sweeps = 8 if uneven else 10
     if args.impl == "reference":
