@@ -123,6 +123,29 @@ def env_roof(precision, achieved, peaks):
             "peak_source": "nominal from unit counts and clocks"}
 
 
+# ---------------------------------------------------- multi-rank bookkeeping
+def reduce_max(x: float, dist=None, device: str = "cpu") -> float:
+    """The largest value of x over all ranks (x itself without a process
+    group): the step time of the job is that of its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, items_per_rank: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank updates its own items_per_rank bonds
+    per step (weak scaling) and the step lasts ms_max, the slowest rank's."""
+    return world * items_per_rank / (ms_max / 1e3)
+
+
+def rank_seed(rank: int, base: int = 5) -> int:
+    """Seed of a rank's synthetic batch: ranks draw disjoint inputs."""
+    return base + 1000 * rank
+
+
 # ------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -305,17 +328,13 @@ def run_uneven(args):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, "cuda")
 
     B, S = args.batch, args.sweeps
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    items = I.uneven_batch(5 + 1000 * rank, B)
+    items = I.uneven_batch(rank_seed(rank), B)
     kinds = sorted({(it[0], it[1]) for it in items})
     caps = [sum(1 for it in items if (it[0], it[1]) == k) for k in kinds]
     prec = {"bf16x3": ntu.NTU_MIXED_BF16X3, "fp32": ntu.NTU_MIXED_FP32,
@@ -375,10 +394,10 @@ def run_uneven(args):
         u64 = make(ntu.NTU_FP64)
         ms64, _ = timed(u64, u64.GRAPH, args.fp64_steps, 1)
         u64.close()
-        fp64 = {"value": world * B / (ms64 / 1e3), "unit": "bond updates/s", "ms_per_step": ms64}
+        fp64 = {"value": job_rate(world, B, ms64), "unit": "bond updates/s", "ms_per_step": ms64}
     if rank != 0:
         return
-    value = world * B / (ms_graph / 1e3)
+    value = job_rate(world, B, ms_graph)
     env_total = sum(env_flops(it[0], it[1]) for it in items)
     peaks = measured_peaks()
     roof = env_roof(args.precision, env_total / (ms_graph / 1e3), peaks)
@@ -403,13 +422,13 @@ def run_uneven(args):
         "config": uneven_config(args, args.precision),
         "kinds": {f"D{k[0]}r{k[1]}": c for k, c in zip(kinds, caps)},
         "roofline": roof,
-        "grouped_no_graph": {"value": world * B / (ms_grouped / 1e3), "ms_per_step": ms_grouped},
-        "per_bond_launches": {"value": world * B / (ms_item / 1e3), "ms_per_step": ms_item},
+        "grouped_no_graph": {"value": job_rate(world, B, ms_grouped), "ms_per_step": ms_grouped},
+        "per_bond_launches": {"value": job_rate(world, B, ms_item), "ms_per_step": ms_item},
         "speedup_vs_per_bond": ms_item / ms_graph,
         "fp64_path": fp64,
         "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "delta_median": float(np.median(info[:, 1])),
-        "e2e": {"value": world * B / e2e_s, "unit": "bond updates/s",
+        "e2e": {"value": job_rate(world, B, 1e3 * e2e_s), "unit": "bond updates/s",
                 "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b},
         "gpu_launches": launches,
         "clocks": clk,
@@ -439,11 +458,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, "cuda")
 
     D, r, B, S = args.D, args.r, args.batch, args.sweeps
     # one non-default stream shared by torch (events, L2 flush) and the library
@@ -451,7 +466,7 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    Ta_h, Tb_h, G_h = I.batch_items(5 + 1000 * rank, B, 2, D, I.zz_gate(0.01))
+    Ta_h, Tb_h, G_h = I.batch_items(rank_seed(rank), B, 2, D, I.zz_gate(0.01))
     Ta = torch.from_numpy(Ta_h).cuda()
     Tb = torch.from_numpy(Tb_h).cuda()
     G = torch.from_numpy(G_h).cuda()
@@ -491,7 +506,7 @@ def run_ours(args):
                                                15 if head == ntu.NTU_FP64 else 8)
     clk = clocks.stop()
     ms_mixed = max_over_ranks(statistics.mean(t_mixed))
-    value = world * B / (ms_mixed / 1e3)
+    value = job_rate(world, B, ms_mixed)
     delta_mixed = info[:, 1].cpu().numpy()
     paths_mixed = ctx.paths
 
@@ -530,7 +545,7 @@ def run_ours(args):
         cx, tt, st, _ = measure(prec, args.fp64_steps, 1, 15 if prec == ntu.NTU_FP64 else 8)
         ms = max_over_ranks(statistics.mean(tt))
         others[names[prec]] = {
-            "value": world * B / (ms / 1e3), "unit": "bond updates/s", "ms_per_step": ms,
+            "value": job_rate(world, B, ms), "unit": "bond updates/s", "ms_per_step": ms,
             "env_tflops": B * env_flops(D, r) / (st[1] / 1e3) / 1e12,
             "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
                                  [round(float(x), 3) for x in st]))}
@@ -540,7 +555,7 @@ def run_ours(args):
     # the metric names D=6 as well: the same batch and sweeps at D=6, this
     # precision and the FP64 path (device-resident, L2 flushed per step)
     def measure_d(Dm, prec, steps, warmup):
-        ta_h, tb_h, g_h = I.batch_items(5 + 1000 * rank, B, 2, Dm, I.zz_gate(0.01))
+        ta_h, tb_h, g_h = I.batch_items(rank_seed(rank), B, 2, Dm, I.zz_gate(0.01))
         ta, tb, gg = (torch.from_numpy(x).cuda() for x in (ta_h, tb_h, g_h))
         oa, ob = torch.empty_like(ta), torch.empty_like(tb)
         inf = torch.empty((B, 4), dtype=torch.float64, device="cuda")
@@ -563,7 +578,7 @@ def run_ours(args):
         cx.sync()
         cx.close()
         ms = max_over_ranks(statistics.mean(ts))
-        return {"value": world * B / (ms / 1e3), "unit": "bond updates/s", "ms_per_step": ms}
+        return {"value": job_rate(world, B, ms), "unit": "bond updates/s", "ms_per_step": ms}
 
     d6 = None
     if D != 6 and not args.no_d6:
@@ -612,7 +627,7 @@ def run_ours(args):
         **others,
         "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "d6": d6,
-        "e2e": {"value": world * B / e2e_s, "unit": "bond updates/s",
+        "e2e": {"value": job_rate(world, B, 1e3 * e2e_s), "unit": "bond updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
