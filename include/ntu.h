@@ -86,7 +86,11 @@ typedef struct {
  * Requires d_p * D^2 >= r so that the gated site matrix has at least K rows,
  * and D * r <= 32.  NTU_MIXED_BF16X3 needs a compute capability 10.x GPU and
  * 2 * d_p * D <= 64 (else NTU_EUNSUPPORTED, before any device work).
- * Allocates all device memory the calls below need for up to max_batch items. */
+ * Allocates all device memory the calls below need for up to max_batch items.
+ * On the mixed contexts a max_batch of at most 3 * SMs / 2 (228 on 152 SMs)
+ * lets each item's ALS run on a cluster of 2 CTAs, at most 3 * SMs / 4 on
+ * 4 (same results, bit for bit); its ALS scratch is then allocated that many
+ * times. */
 int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out);
 int ntu_destroy(ntu_ctx* ctx);
 const char* ntu_last_error(const ntu_ctx* ctx);
