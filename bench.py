@@ -117,10 +117,44 @@ def env_roof(precision, achieved, peaks):
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "issued_frac": 3 * achieved / peak,
                 "peak_source": "measured bf16 dense (MEASURED_PEAKS.json)"}
-    peak = FP32_SIMT_PEAK if precision == "fp32" else FP64_PEAK
+    key = "fp32_tflops" if precision == "fp32" else "fp64_tflops"
+    if key in peaks:
+        peak = peaks[key] * 1e12
+        src = f"measured {key[:4]} GEMM (cuBLAS via torch.matmul, this run)"
+    else:
+        peak = FP32_SIMT_PEAK if precision == "fp32" else FP64_PEAK
+        src = "nominal from unit counts and clocks"
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_source": "nominal from unit counts and clocks"}
+            "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src}
+
+
+def measure_gemm_peaks(n: int = 8192, reps: int = 5) -> dict:
+    """FP64 and FP32 (no TF32) GEMM rates of this GPU through the vendor BLAS
+    (torch.matmul), in TFLOP/s: the measured ceilings of the FP64 and FP32
+    environment paths, taken like the measured BF16 peak."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt in (("fp64_tflops", torch.float64), ("fp32_tflops", torch.float32)):
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            for _ in range(2):
+                torch.matmul(a, b)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            out[name] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
 
 
 # ---------------------------------------------------- multi-rank bookkeeping
@@ -536,6 +570,8 @@ def run_ours(args):
     del ctx
 
     # the other precisions on the same GPU, same batch
+    # FP64 / FP32 ceilings of the SIMT environment paths, measured here
+    gemm_peaks = measure_gemm_peaks()
     others = {}
     names = {ntu.NTU_MIXED_BF16X3: "bf16x3_path", ntu.NTU_MIXED_FP32: "fp32_env_path",
              ntu.NTU_FP64: "fp64_path"}
@@ -544,9 +580,12 @@ def run_ours(args):
             continue
         cx, tt, st, _ = measure(prec, args.fp64_steps, 1, 15 if prec == ntu.NTU_FP64 else 8)
         ms = max_over_ranks(statistics.mean(tt))
+        env_rate = B * env_flops(D, r) / (st[1] / 1e3)
         others[names[prec]] = {
             "value": job_rate(world, B, ms), "unit": "bond updates/s", "ms_per_step": ms,
-            "env_tflops": B * env_flops(D, r) / (st[1] / 1e3) / 1e12,
+            "env_tflops": env_rate / 1e12,
+            "env_roofline": env_roof("fp64" if prec == ntu.NTU_FP64 else "fp32", env_rate,
+                                     gemm_peaks),
             "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
                                  [round(float(x), 3) for x in st]))}
         cx.close()
@@ -619,7 +658,8 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved / als_pk,
                      "traffic": als_traffic(args.precision, D, r, S, B),
                      "peak_source": als_pk_src},
-        "env_roofline": env_roof(args.precision, env_achieved, peaks),
+        "env_roofline": env_roof(args.precision, env_achieved, {**peaks, **gemm_peaks}),
+        "measured_gemm_peaks": {k: round(v, 2) for k, v in gemm_peaks.items()},
         "stage_ms": dict(zip(["gate_qr", "env", "repair", "als", "recompose"],
                              [round(float(x), 3) for x in st_mixed])),
         "delta_median": float(np.median(delta_mixed)),
