@@ -13,8 +13,11 @@
 // parts of a row's columns first and the imaginary parts krpE/2 later).
 //
 // Complex products are real GEMMs as in k_tc.cu: A doubled (Re / Im rows 64
-// apart in a 128-row tile), B interleaved (re, im) along K, three split
-// products hi*hi + hi*lo + lo*hi accumulated in FP32.
+// apart in a 128-row tile), three split products hi*hi + hi*lo + lo*hi
+// accumulated in FP32.  GEMM1 (A = Y, B = conj(Q), from TMA) keeps (re, im)
+// interleaved along K; GEMM2 has K planar (all Re factors, then all Im) and
+// takes its A operand, E_top, from tensor memory, where epilogue 2 copies it
+// once per item.
 //
 // One persistent CTA per SM takes a contiguous range of (item, k, k') units.
 // Warp 0 issues TMA (E_top once per item, the Y block once per k, the
