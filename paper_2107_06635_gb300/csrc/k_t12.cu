@@ -25,7 +25,10 @@
 // unit i, then GEMM2 of unit i-1), warps 2-9 turn accumulator 1 into the B
 // operand of GEMM2 (two buffers), warps 10-17 turn accumulator 2 into output
 // rows in a swizzled shared staging block that one thread stores with TMA.
-// Both epilogues write 16-byte chunks: the planar K of GEMM2 puts the eight
+// At D = 8 the units (k, k') and (k, k'+1) form a pair: epilogue 1 writes
+// both into one 128-row operand buffer and GEMM2 of the pair is one N = 128
+// product, which halves the MMA instructions of GEMM2 (their issue, not the
+// tensor pipe, bounds the kernel at N = 64).  Both epilogues write 16-byte chunks: the planar K of GEMM2 puts the eight
 // u' values of one (u, n') next to each other, and the planar T2 the
 // sixteen columns a thread holds.  Every wait is bounded; every role leaves
 // its loop on a timeout and the epilogue groups leave together.
@@ -53,9 +56,10 @@ constexpr int OFF_B2 = OFF_B1 + 4 * B_TILE;   // 2 buffers x 4 B tiles: T1 hi0, 
 constexpr int STG_BOX = 64 * 128;             // one output box: 64 rows x 64 BF16
 constexpr int OFF_STG = OFF_B2 + 8 * B_TILE;  // output staging: up to 4 boxes (hi Re/Im, lo Re/Im)
 constexpr int OFF_BAR = OFF_STG + 4 * STG_BOX;
-// TMEM columns: accumulator 1 (two buffers) 0-127, accumulator 2 128-255,
-// E_top as the A operand of GEMM2: hi halves from 256, lo halves from 320
-constexpr uint32_t TM_COLS = 512, TM_A2H = 256, TM_A2L = 320;
+// TMEM columns: accumulator 1 (two buffers of 64) 0-127, accumulator 2
+// (two buffers of 64, or of 128 for unit pairs) from 128, E_top as the A
+// operand of GEMM2: hi halves from 384, lo halves from 448
+constexpr uint32_t TM_COLS = 512, TM_A2H = 384, TM_A2L = 448;
 constexpr size_t T12_SMEM = (size_t)OFF_BAR + 512 + 1024;
 static_assert(T12_SMEM <= 227 * 1024, "shared memory budget");
 
@@ -102,9 +106,13 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
   uint64_t* a2t_full = bar + 22;                               // E_top copied into TMEM
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = DT ? DT : a.D, K = a.K, D2 = D * D, KK = K * K;
-  // contiguous range of units for this CTA
-  const long long u0 = a.units * blockIdx.x / gridDim.x;
-  const long long u1 = a.units * (blockIdx.x + 1) / gridDim.x;
+  // D = 8: units (k, k') and (k, k'+1) are paired (K = 8 r is even): GEMM2
+  // of a pair is one N = 128 product, from one 128-row operand buffer
+  constexpr bool PAIR = DT == 8;
+  // contiguous range of units for this CTA (whole pairs when paired)
+  const long long ug = PAIR ? a.units / 2 : a.units;
+  const long long u0 = (PAIR ? 2 : 1) * (ug * blockIdx.x / gridDim.x);
+  const long long u1 = (PAIR ? 2 : 1) * (ug * (blockIdx.x + 1) / gridDim.x);
   // padding of the generated operand and of the output staging must read
   // as zero: clear both once (generic stores, then a proxy fence)
   for (int i = tid; i < (8 * B_TILE + 4 * STG_BOX) / 16; i += T12_THREADS)
@@ -218,9 +226,10 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
           // next unit starts a new k, or there is none)
           if (u + 1 >= u1 || kp == K - 1) tc::mma_commit(a1_empty);
         }
-        if (u > u0) {
-          // GEMM2 of unit j = u - 1
-          const long long j = i - 1;
+        if (u > u0 && (!PAIR || (i & 1) == 0)) {
+          // GEMM2 of unit j = u - 1, or of pair j = i / 2 - 1 (units u - 2,
+          // u - 1) into 128 accumulator columns from the single pair buffer
+          const long long j = PAIR ? (i >> 1) - 1 : i - 1;
           const int zj = zp;
           const int b = (int)(j & 1);
           const long long ub = j >> 1;
@@ -228,23 +237,30 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
             if (!tc::mbar_wait(a2t_full, (uint32_t)(a2n & 1), T12_WAIT)) { ok = false; break; }
             ++a2n; a2z = zj;
           }
-          if (!tc::mbar_wait(&b2_full[b], (uint32_t)(ub & 1), T12_WAIT)) { ok = false; break; }
+          if (PAIR) {
+            if (!tc::mbar_wait(&b2_full[0], (uint32_t)(j & 1), T12_WAIT)) { ok = false; break; }
+          } else {
+            if (!tc::mbar_wait(&b2_full[b], (uint32_t)(ub & 1), T12_WAIT)) { ok = false; break; }
+          }
           if (ub > 0 && !tc::mbar_wait(&c2_empty[b], (uint32_t)((ub - 1) & 1), T12_WAIT)) { ok = false; break; }
           tc::fence_after_sync();
-          const uint32_t acc = tmem + 128u + (uint32_t)(b * 64);
+          const uint32_t acc = tmem + 128u + (uint32_t)(b * (PAIR ? 128 : 64));
+          const uint32_t id2 = PAIR ? tc::idesc_bf16_f32(128, 128) : id;
+          const int tstride = PAIR ? 2 * B_TILE : B_TILE;
+          unsigned char* B2 = sm + OFF_B2 + (PAIR ? 0 : b * 4 * B_TILE);
           for (int c = 0; c < a.nchunk; ++c) {
             const uint32_t ah = tmem + TM_A2H + (uint32_t)(c * 32);
             const uint32_t al = tmem + TM_A2L + (uint32_t)(c * 32);
-            const uint64_t bh = tc::sdesc_k128(tc::smem_u32(sm + OFF_B2 + (b * 4 + c) * B_TILE));
-            const uint64_t bl = tc::sdesc_k128(tc::smem_u32(sm + OFF_B2 + (b * 4 + 2 + c) * B_TILE));
+            const uint64_t bh = tc::sdesc_k128(tc::smem_u32(B2 + c * tstride));
+            const uint64_t bl = tc::sdesc_k128(tc::smem_u32(B2 + (2 + c) * tstride));
 #pragma unroll
             for (int kk4 = 0; kk4 < 4; ++kk4) {
-              tc::mma_bf16_ts(acc, ah + 8 * kk4, bh + 2 * kk4, id, (c | kk4) != 0);
-              tc::mma_bf16_ts(acc, ah + 8 * kk4, bl + 2 * kk4, id, 1);
-              tc::mma_bf16_ts(acc, al + 8 * kk4, bh + 2 * kk4, id, 1);
+              tc::mma_bf16_ts(acc, ah + 8 * kk4, bh + 2 * kk4, id2, (c | kk4) != 0);
+              tc::mma_bf16_ts(acc, ah + 8 * kk4, bl + 2 * kk4, id2, 1);
+              tc::mma_bf16_ts(acc, al + 8 * kk4, bh + 2 * kk4, id2, 1);
             }
           }
-          tc::mma_commit(&b2_empty[b]);
+          tc::mma_commit(&b2_empty[PAIR ? 0 : b]);
           tc::mma_commit(&c2_full[b]);
         }
         zp = z;
@@ -283,16 +299,25 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       bool got = true;
       if (et == 0) {
         got = tc::mbar_wait_sleep(&c1_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
-        if (got && ub > 0) got = tc::mbar_wait_sleep(&b2_empty[b], (uint32_t)((ub - 1) & 1), T12_SLEEP_POLLS);
+        // paired: the single pair buffer is free once GEMM2 of the previous
+        // pair has completed; wait before the pair's first unit only
+        if (PAIR) {
+          if (got && b == 0 && ub > 0)
+            got = tc::mbar_wait_sleep(&b2_empty[0], (uint32_t)((ub - 1) & 1), T12_SLEEP_POLLS);
+        } else if (got && ub > 0) {
+          got = tc::mbar_wait_sleep(&b2_empty[b], (uint32_t)((ub - 1) & 1), T12_SLEEP_POLLS);
+        }
       }
       if (!tc::bar_and(1, EPI, got)) {
         if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
         break;
       }
       tc::fence_after_sync();
-      unsigned char* B2 = sm + OFF_B2 + b * 4 * B_TILE;
+      // paired: unit b of the pair fills rows 64 b .. of 128-row tiles
+      unsigned char* B2 = sm + OFF_B2 + (PAIR ? b * 64 * 128 : b * 4 * B_TILE);
       if (DT == 8) {
-        unsigned char* bh = B2 + im * B_TILE + nn * 128 + ((uu ^ nn) << 4);
+        constexpr int TS = PAIR ? 2 * B_TILE : B_TILE;           // tile stride
+        unsigned char* bh = B2 + im * TS + nn * 128 + ((uu ^ nn) << 4);
 #pragma unroll
         for (int c0 = cs; c0 < cs + 32; c0 += 16) {
           float v[16];
@@ -310,7 +335,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
             }
             unsigned char* dst = bh + ((c0 >> 3) + g) * 1024;    // row n' * 8 + n
             *reinterpret_cast<uint4*>(dst) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4*>(dst + 2 * B_TILE) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            *reinterpret_cast<uint4*>(dst + 2 * TS) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
           }
         }
       } else
@@ -337,7 +362,10 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&c1_empty[b]);
       tc::bar_sync(1, EPI);
-      if (et == 0) tc::mbar_arrive(&b2_full[b]);
+      if (et == 0) {
+        if (!PAIR) tc::mbar_arrive(&b2_full[b]);
+        else if (b == 1) tc::mbar_arrive(&b2_full[0]);     // both units of the pair are in
+      }
     }
   } else {
     // ---- epilogue 2: accumulator 2 (rows (ht,ht') Re / Im, columns
@@ -394,11 +422,16 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
         ++e2n;
         za = z;
       }
-      const int b = (int)(i & 1);
-      const long long ub = i >> 1;
+      // paired: accumulator b holds both units of pair i / 2, unit i % 2 in
+      // columns 64 (i % 2) ..; it is waited for at the pair's first unit and
+      // released after its second
+      const int b = PAIR ? (int)((i >> 1) & 1) : (int)(i & 1);
+      const long long ub = PAIR ? (i >> 2) : (i >> 1);
+      const bool first = !PAIR || (i & 1) == 0, last = !PAIR || (i & 1) == 1;
+      const uint32_t cbase = 128u + (uint32_t)(PAIR ? b * 128 + (int)(i & 1) * 64 : b * 64);
       bool got = true;
       if (et == 0) {
-        got = tc::mbar_wait_sleep(&c2_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
+        if (first) got = tc::mbar_wait_sleep(&c2_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
         tc::bulk_wait_read();                   // the staging block is free again
       }
       if (!tc::bar_and(2, EPI, got)) {
@@ -410,7 +443,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       for (int c0 = cs; c0 < cs + 32; c0 += 16) {
         if (DT == 8 || c0 < D2) {                 // uniform over the warp
           float v[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(128 + b * 64 + c0), v);
+          tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + cbase + (uint32_t)c0, v);
           if (rv) {
             const int pos = im * half + c0;      // hi column of v[0]
             unsigned char* bx = stg + (pos >> 6) * STG_BOX;
@@ -433,9 +466,11 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
           }
         }
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&c2_empty[b]);
+      if (last) {
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&c2_empty[b]);
+      }
       fence_proxy_async();                       // staging writes -> TMA reads
       tc::bar_sync(2, EPI);
       if (et == 0) {
