@@ -605,8 +605,6 @@ int tc_plan_maps(ntu_ctx* c) {
   };
   mk(&P.mapYs, W.Ys, 2 * P.krpY, P.rowsY);
   if (st == NTU_OK) st = tc_make_map(&P.mapQs, W.Qs, 2 * P.krpY, P.rowsQ, cap, 64);
-  mk(&P.mapEtopL, W.ETLd, pE, P.rowsE);
-  mk(&P.mapEtopR, W.ETRd, pE, P.rowsE);
   mk(&P.tc_hL.mapA, W.EBLd, pE, P.rowsE);
   mk(&P.tc_hR.mapA, W.EBRd, pE, P.rowsE);
   mk(&P.tc_hL.mapB, W.T2s, pE, P.rowsT);
@@ -632,10 +630,10 @@ static cudaError_t env_chain_bf16x3(ntu_ctx* c, int n, const void* Ta, const voi
   RG(run_gemm<float2>(c, P.e2TR, n, Ta, Ta, W.ETRd));
   RG(run_gemm<float2>(c, P.e2BR, n, Ta, Ta, W.EBRd));
   RG(launch_yq(c, n, (const float2*)QA, (const float2*)W.EL));
-  RG(launch_t12(c, n, P.mapEtopL));
+  RG(launch_t12(c, n, W.ETLd));
   RG(launch_tc_gemm(c, P.tc_hL, n, W.HLd));
   RG(launch_yq(c, n, (const float2*)QB, (const float2*)W.ER));
-  RG(launch_t12(c, n, P.mapEtopR));
+  RG(launch_t12(c, n, W.ETRd));
   RG(launch_tc_gemm(c, P.tc_hR, n, W.HRs));
   RG(launch_tc_gemm(c, P.tc_join, n, graw));
   return cudaSuccess;

@@ -17,17 +17,18 @@
 // accumulated in FP32.  GEMM1 (A = Y, B = conj(Q), from TMA) keeps (re, im)
 // interleaved along K; GEMM2 has K planar (all Re factors, then all Im) and
 // takes its A operand, E_top, from tensor memory, where epilogue 2 copies it
-// once per item.
+// from global memory once per item (one 128-byte row segment per thread and
+// K chunk).
 //
 // One persistent CTA per SM takes a contiguous range of (item, k, k') units.
-// Warp 0 issues TMA (E_top once per item, the Y block once per k, the
-// conj(Q) block per unit, double-buffered), warp 1 issues the MMAs (GEMM1 of
-// unit i, then GEMM2 of unit i-1), warps 2-9 turn accumulator 1 into the B
-// operand of GEMM2 (two buffers), warps 10-17 turn accumulator 2 into output
-// rows in a swizzled shared staging block that one thread stores with TMA.
+// Warp 0 issues TMA (the Y block once per k, the conj(Q) block per unit,
+// double-buffered), warp 1 issues the MMAs (GEMM1 of unit i, then GEMM2 of
+// unit i-1), warps 2-9 turn accumulator 1 into the B operand of GEMM2 (two
+// buffers), warps 10-17 turn accumulator 2 into output rows in a swizzled
+// shared staging block that one thread stores with TMA.
 // At D = 8 the units (k, k') and (k, k'+1) form a pair: epilogue 1 writes
-// both into one 128-row operand buffer and GEMM2 of the pair is one N = 128
-// product, which halves the MMA instructions of GEMM2 (their issue, not the
+// both into one 128-row operand buffer (two such buffers) and GEMM2 of the
+// pair is one N = 128 product, which halves the MMA instructions of GEMM2 (their issue, not the
 // tensor pipe, bounds the kernel at N = 64).  Both epilogues write 16-byte chunks: the planar K of GEMM2 puts the eight
 // u' values of one (u, n') next to each other, and the planar T2 the
 // sixteen columns a thread holds.  Every wait is bounded; every role leaves
@@ -49,12 +50,14 @@ constexpr long long T12_WAIT = 1ll << 28;
 constexpr int T12_SLEEP_POLLS = 1 << 17;       // x <= 20 us: about 2.6 s
 constexpr int A_TILE = 128 * 128;            // 128 rows x 64 BF16
 constexpr int B_TILE = 64 * 128;             // 64 rows x 64 BF16
-constexpr int OFF_A2 = 0;                     // 4 A tiles: E_top hi0, hi1, lo0, lo1
-constexpr int OFF_A1 = OFF_A2 + 4 * A_TILE;   // 2 A tiles: Y hi, lo
+constexpr int OFF_A1 = 0;                     // 2 A tiles: Y hi, lo
 constexpr int OFF_B1 = OFF_A1 + 2 * A_TILE;   // 2 buffers x 2 B tiles: conj(Q) hi, lo
-constexpr int OFF_B2 = OFF_B1 + 4 * B_TILE;   // 2 buffers x 4 B tiles: T1 hi0, hi1, lo0, lo1
+// GEMM2 B operand, T1 hi0, hi1, lo0, lo1: 2 buffers of 4 64-row tiles, or
+// of 4 128-row tiles for unit pairs
+constexpr int OFF_B2 = OFF_B1 + 4 * B_TILE;
+constexpr int B2_BYTES = 16 * B_TILE;
 constexpr int STG_BOX = 64 * 128;             // one output box: 64 rows x 64 BF16
-constexpr int OFF_STG = OFF_B2 + 8 * B_TILE;  // output staging: up to 4 boxes (hi Re/Im, lo Re/Im)
+constexpr int OFF_STG = OFF_B2 + B2_BYTES;    // output staging: up to 4 boxes (hi Re/Im, lo Re/Im)
 constexpr int OFF_BAR = OFF_STG + 4 * STG_BOX;
 // TMEM columns: accumulator 1 (two buffers of 64) 0-127, accumulator 2
 // (two buffers of 64, or of 128 for unit pairs) from 128, E_top as the A
@@ -82,21 +85,22 @@ struct T12Args {
   int krpY, krpE;
   int k1;               // 16-wide K steps of GEMM1 that hold data: ceil(2 d_p D / 16)
   long long units;      // items * K * K
+  const __nv_bfloat16* E;   // E_top split: per item rows of 2 krpE (hi, then lo)
+  long long e_item;         // elements per item of E
   int* err;
 };
 
 // DT = 8: bond dimension fixed at compile time (every index of the epilogues
 // folds into constants); DT = 0: any D <= 8 at run time.
 template <int DT>
-__global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ CUtensorMap mA2,
-                                                      const __grid_constant__ CUtensorMap mA1,
+__global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ CUtensorMap mA1,
                                                       const __grid_constant__ CUtensorMap mB1,
                                                       const __grid_constant__ CUtensorMap mT2,
                                                       T12Args a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bar = (uint64_t*)(sm + OFF_BAR);
-  uint64_t *a2_full = bar, *a2_empty = bar + 1, *a1_full = bar + 2, *a1_empty = bar + 3;
+  uint64_t *a1_full = bar + 2, *a1_empty = bar + 3;
   uint64_t *q_full = bar + 4, *q_empty = bar + 6;             // [2]
   uint64_t *c1_full = bar + 8, *c1_empty = bar + 10;          // accumulator 1 [2]
   uint64_t *b2_full = bar + 12, *b2_empty = bar + 14;         // GEMM2 B operand [2]
@@ -115,11 +119,10 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
   const long long u1 = (PAIR ? 2 : 1) * (ug * (blockIdx.x + 1) / gridDim.x);
   // padding of the generated operand and of the output staging must read
   // as zero: clear both once (generic stores, then a proxy fence)
-  for (int i = tid; i < (8 * B_TILE + 4 * STG_BOX) / 16; i += T12_THREADS)
+  for (int i = tid; i < (B2_BYTES + 4 * STG_BOX) / 16; i += T12_THREADS)
     reinterpret_cast<uint4*>(sm + OFF_B2)[i] = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async();
   if (tid == 0) {
-    tc::mbar_init(a2_full, 1); tc::mbar_init(a2_empty, EPI / 32);
     tc::mbar_init(a1_full, 1); tc::mbar_init(a1_empty, 1);
     tc::mbar_init(a2t_full, EPI / 32);
     for (int b = 0; b < 2; ++b) {
@@ -138,11 +141,10 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
   const uint32_t tmem = *tmem_slot;
   if (warp == 0) {
     if (lane == 0) {
-      // ---- producer: per unit the Y block if (item, k) changed, the
-      // conj(Q) block, then E_top if the item changed (this order lets the
-      // MMA warp issue GEMM1 of the new unit before it releases E_top)
-      int a1z = -1, a1k = -1, a2z = -1;
-      long long a1n = 0, a2n = 0, qn = 0, i = 0;
+      // ---- producer: per unit the Y block if (item, k) changed, then the
+      // conj(Q) block
+      int a1z = -1, a1k = -1;
+      long long a1n = 0, qn = 0, i = 0;
       // unit u = (z, k, kp): kept incrementally (no 64-bit division per unit)
       int z = (int)(u0 / KK), k = (int)(u0 % KK) / K, kp = (int)(u0 % KK) % K;
       for (long long u = u0; u < u1; ++u, ++i, kp = kp + 1 < K ? kp + 1 : 0,
@@ -168,23 +170,10 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
         tc::tma_load_3d(qd, &mB1, &q_full[qb], 0, kp * 64, z);
         tc::tma_load_3d(qd + B_TILE, &mB1, &q_full[qb], a.krpY, kp * 64, z);
         ++qn;
-        if (z != a2z) {
-          if (a2n > 0 && !tc::mbar_wait(a2_empty, (uint32_t)((a2n - 1) & 1), T12_WAIT)) {
-            raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
-            break;
-          }
-          tc::mbar_expect_tx(a2_full, 2 * a.nchunk * A_TILE);
-          for (int c = 0; c < a.nchunk; ++c) {
-            tc::tma_load_3d(sm + OFF_A2 + c * A_TILE, &mA2, a2_full, c * 64, 0, z);
-            tc::tma_load_3d(sm + OFF_A2 + (2 + c) * A_TILE, &mA2, a2_full, a.krpE + c * 64, 0, z);
-          }
-          ++a2n; a2z = z;
-        }
       }
       // no TMA copy may still be landing in shared memory when the CTA exits
       bool dr = true;
       if (a1n > 0) dr &= tc::mbar_wait(a1_full, (uint32_t)((a1n - 1) & 1), T12_WAIT);
-      if (a2n > 0) dr &= tc::mbar_wait(a2_full, (uint32_t)((a2n - 1) & 1), T12_WAIT);
       for (long long q = qn - 2 < 0 ? 0 : qn - 2; q < qn; ++q)
         dr &= tc::mbar_wait(&q_full[q & 1], (uint32_t)((q >> 1) & 1), T12_WAIT);
       if (!dr) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
@@ -228,7 +217,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
         }
         if (u > u0 && (!PAIR || (i & 1) == 0)) {
           // GEMM2 of unit j = u - 1, or of pair j = i / 2 - 1 (units u - 2,
-          // u - 1) into 128 accumulator columns from the single pair buffer
+          // u - 1) into 128 accumulator columns; operand buffer j % 2
           const long long j = PAIR ? (i >> 1) - 1 : i - 1;
           const int zj = zp;
           const int b = (int)(j & 1);
@@ -237,17 +226,13 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
             if (!tc::mbar_wait(a2t_full, (uint32_t)(a2n & 1), T12_WAIT)) { ok = false; break; }
             ++a2n; a2z = zj;
           }
-          if (PAIR) {
-            if (!tc::mbar_wait(&b2_full[0], (uint32_t)(j & 1), T12_WAIT)) { ok = false; break; }
-          } else {
-            if (!tc::mbar_wait(&b2_full[b], (uint32_t)(ub & 1), T12_WAIT)) { ok = false; break; }
-          }
+          if (!tc::mbar_wait(&b2_full[b], (uint32_t)(ub & 1), T12_WAIT)) { ok = false; break; }
           if (ub > 0 && !tc::mbar_wait(&c2_empty[b], (uint32_t)((ub - 1) & 1), T12_WAIT)) { ok = false; break; }
           tc::fence_after_sync();
           const uint32_t acc = tmem + 128u + (uint32_t)(b * (PAIR ? 128 : 64));
           const uint32_t id2 = PAIR ? tc::idesc_bf16_f32(128, 128) : id;
           const int tstride = PAIR ? 2 * B_TILE : B_TILE;
-          unsigned char* B2 = sm + OFF_B2 + (PAIR ? 0 : b * 4 * B_TILE);
+          unsigned char* B2 = sm + OFF_B2 + b * (PAIR ? 8 : 4) * B_TILE;
           for (int c = 0; c < a.nchunk; ++c) {
             const uint32_t ah = tmem + TM_A2H + (uint32_t)(c * 32);
             const uint32_t al = tmem + TM_A2L + (uint32_t)(c * 32);
@@ -260,7 +245,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
               tc::mma_bf16_ts(acc, al + 8 * kk4, bh + 2 * kk4, id2, 1);
             }
           }
-          tc::mma_commit(&b2_empty[PAIR ? 0 : b]);
+          tc::mma_commit(&b2_empty[b]);
           tc::mma_commit(&c2_full[b]);
         }
         zp = z;
@@ -297,16 +282,16 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       // one thread waits (suspended in hardware), the group meets at a
       // named barrier that also carries the outcome
       bool got = true;
+      // operand buffer: slot s (the unit, or its pair) goes to buffer s % 2,
+      // free once GEMM2 of slot s - 2 has completed
+      const long long sl = PAIR ? i >> 1 : i;
+      const int sb = (int)(sl & 1);
+      const long long sub = sl >> 1;
+      const bool first = !PAIR || b == 0, last = !PAIR || b == 1;
       if (et == 0) {
         got = tc::mbar_wait_sleep(&c1_full[b], (uint32_t)(ub & 1), T12_SLEEP_POLLS);
-        // paired: the single pair buffer is free once GEMM2 of the previous
-        // pair has completed; wait before the pair's first unit only
-        if (PAIR) {
-          if (got && b == 0 && ub > 0)
-            got = tc::mbar_wait_sleep(&b2_empty[0], (uint32_t)((ub - 1) & 1), T12_SLEEP_POLLS);
-        } else if (got && ub > 0) {
-          got = tc::mbar_wait_sleep(&b2_empty[b], (uint32_t)((ub - 1) & 1), T12_SLEEP_POLLS);
-        }
+        if (got && first && sub > 0)
+          got = tc::mbar_wait_sleep(&b2_empty[sb], (uint32_t)((sub - 1) & 1), T12_SLEEP_POLLS);
       }
       if (!tc::bar_and(1, EPI, got)) {
         if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
@@ -314,7 +299,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       }
       tc::fence_after_sync();
       // paired: unit b of the pair fills rows 64 b .. of 128-row tiles
-      unsigned char* B2 = sm + OFF_B2 + (PAIR ? b * 64 * 128 : b * 4 * B_TILE);
+      unsigned char* B2 = sm + OFF_B2 + (PAIR ? sb * 8 * B_TILE + b * 64 * 128 : b * 4 * B_TILE);
       if (DT == 8) {
         constexpr int TS = PAIR ? 2 * B_TILE : B_TILE;           // tile stride
         unsigned char* bh = B2 + im * TS + nn * 128 + ((uu ^ nn) << 4);
@@ -362,10 +347,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&c1_empty[b]);
       tc::bar_sync(1, EPI);
-      if (et == 0) {
-        if (!PAIR) tc::mbar_arrive(&b2_full[b]);
-        else if (b == 1) tc::mbar_arrive(&b2_full[0]);     // both units of the pair are in
-      }
+      if (et == 0 && last) tc::mbar_arrive(&b2_full[sb]);   // paired: both units are in
     }
   } else {
     // ---- epilogue 2: accumulator 2 (rows (ht,ht') Re / Im, columns
@@ -386,27 +368,26 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
     unsigned char* stg = sm + OFF_STG + r * 128;
     const int hl = cs >> 5;                    // this warp copies E_top's hi (0) or lo (1) half
     int za = -1;                               // item whose E_top is in TMEM
-    long long e2n = 0;
     long long i = 0;
     int z = (int)(u0 / KK), kk = (int)(u0 % KK);
     for (long long u = u0; u < u1; ++u, ++i, kk = kk + 1 < KK ? kk + 1 : 0, z = kk ? z : z + 1) {
       if (z != za) {
-        // first unit of an item: E_top (shared memory, from TMA) becomes the
+        // first unit of an item: this thread's row of E_top (hi or lo half,
+        // 128 bytes per 64-wide K chunk, read from global memory) becomes the
         // TMEM A operand of GEMM2.  Every GEMM2 of the previous item has
         // completed (this group consumed its last accumulator), so the TMEM
-        // region is free; the shared copy is released for the next item.
-        bool ok2 = true;
-        if (et == 0) ok2 = tc::mbar_wait_sleep(a2_full, (uint32_t)(e2n & 1), T12_SLEEP_POLLS);
-        if (!tc::bar_and(2, EPI, ok2)) {
-          if (et == 0) raise_status(a.err, ST_TIMEOUT, WHY_TC_WAIT);
-          break;
-        }
+        // region is free.
+        const uint4* erow = reinterpret_cast<const uint4*>(
+            a.E + (size_t)z * (size_t)a.e_item + (size_t)row * (size_t)(2 * a.krpE) +
+            (size_t)(hl * a.krpE));
+        // one chunk in flight at a time: 32 words per thread (unrolling the
+        // chunks would hold 64 and spill at the 96-register limit)
+#pragma unroll 1
         for (int c = 0; c < a.nchunk; ++c) {
-          const unsigned char* src = sm + OFF_A2 + (2 * hl + c) * A_TILE + row * 128;
           uint32_t w[32];
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
-            const uint4 v = *reinterpret_cast<const uint4*>(src + ((g ^ (row & 7)) << 4));
+            const uint4 v = __ldg(erow + c * 8 + g);
             w[4 * g] = v.x; w[4 * g + 1] = v.y; w[4 * g + 2] = v.z; w[4 * g + 3] = v.w;
           }
           tc::tmem_st32(tmem + ((uint32_t)(quarter * 32) << 16) + (hl ? TM_A2L : TM_A2H) +
@@ -415,11 +396,7 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
         tc::tmem_wait_st();
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) {
-          tc::mbar_arrive(a2t_full);
-          tc::mbar_arrive(a2_empty);
-        }
-        ++e2n;
+        if (lane == 0) tc::mbar_arrive(a2t_full);
         za = z;
       }
       // paired: accumulator b holds both units of pair i / 2, unit i % 2 in
@@ -489,9 +466,11 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
 
 size_t t12_smem_bytes() { return T12_SMEM; }
 
+// Etop: the split top edge of this half (W.ETLd or W.ETRd, doubled A
+// operand rows of 2 krpE BF16, rowsE rows per item), read by epilogue 2.
 // The output (T2 split operand, W.T2s) is written through the plan's store
 // map mapT2st, whose box is one unit's D^2 rows.
-cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE) {
+cudaError_t launch_t12(ntu_ctx* c, int n, const void* Etop) {
   const Plan& P = c->plan;
   T12Args a;
   a.D = P.D; a.K = P.K;
@@ -499,6 +478,8 @@ cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE) {
   a.krpY = (int)P.krpY; a.krpE = (int)P.krpE;
   a.k1 = (int)((2 * P.dp * P.D + 15) / 16);
   a.units = (long long)n * P.K * P.K;
+  a.E = (const __nv_bfloat16*)Etop;
+  a.e_item = P.rowsE * 2 * P.krpE;
   a.err = c->d_status;
   if (a.units == 0) return cudaSuccess;
   static int sms = 0;
@@ -516,9 +497,9 @@ cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE) {
     attr = true;
   }
   if (P.D == 8)
-    k_t12<8><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, P.mapT2st, a);
+    k_t12<8><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(P.mapYs, P.mapQs, P.mapT2st, a);
   else
-    k_t12<0><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(mapE, P.mapYs, P.mapQs, P.mapT2st, a);
+    k_t12<0><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(P.mapYs, P.mapQs, P.mapT2st, a);
   return after_launch(c, "k_t12");
 }
 

@@ -62,7 +62,7 @@ struct Plan {
   GemmOp e2TL, e2BL, e2TR, e2BR;        // edge tensors written as doubled A operands
   TcOp tc_hL, tc_hR, tc_join;
   long long krpY, rowsY, rowsQ;         // split operands of the fused t1-t2: Y (doubled A), conj(Q) (B)
-  CUtensorMap mapYs, mapQs, mapEtopL, mapEtopR;   // TMA maps of the fused t1-t2 (k_t12.cu)
+  CUtensorMap mapYs, mapQs;             // TMA maps of the fused t1-t2 (k_t12.cu)
   CUtensorMap mapT2st;                            // its output T2s, box D^2 rows (TMA store)
   long long krpE, krpJ;                 // padded real K of the t2/h and join GEMMs
   long long rowsE, rowsT, rowsHL, rowsHR;  // allocated rows of the split operands
@@ -168,7 +168,7 @@ size_t als_smem_bytes();
 // tensor-core environment (k_tc.cu, k_env.cu)
 int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items,
                 int box_rows = 128);
-cudaError_t launch_t12(ntu_ctx* c, int n, const CUtensorMap& mapE);
+cudaError_t launch_t12(ntu_ctx* c, int n, const void* Etop);
 int tc_plan_maps(ntu_ctx* c);
 cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out);
 
