@@ -751,3 +751,48 @@ def test_mixed_repair_double_fp32_certificate():
         pair = np.einsum("plurn,qrvwx->plunqvwx", a[i], b[i])
         ref = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
         assert _rel(pair, ref) < 1e-4
+
+
+# ------------------------------------------- the bench workload, full size
+@pytest.mark.parametrize("D", [8, 6])
+def test_full_size_bench_batch_sampled_against_oracle(D):
+    """The measured workload at its full size and in the launch shapes the
+    measurement uses: 912 bond updates of D=8 (and the D=6 line), d=2, r=2
+    from seed 5, gate
+    exp(-i 0.01 ZZ), 10 sweeps, split-BF16 environment, tau grid 1e-4..1e-8,
+    on a non-default stream.  Three items (first, middle, last: different
+    CTAs of every persistent kernel and both ends of the batch) are checked
+    against the oracle's bond update one by one; all 912 are checked for what
+    holds at any size: unit-norm outputs (A16), delta = eps / eps0 with
+    eps0 > 0 and 0 <= delta <= 1, tau on the grid."""
+    from paper_2107_06635_gb300 import ntu
+    B, r, S = 912, 2, 10
+    Ta_h, Tb_h, G_h = I.batch_items(5, B, 2, D, I.zz_gate(0.01))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        Ta, Tb, G = _dev(Ta_h), _dev(Tb_h), _dev(G_h)
+        Ta_o, Tb_o = torch.empty_like(Ta), torch.empty_like(Tb)
+        info = torch.empty((B, 4), dtype=torch.float64, device="cuda")
+        ctx = ntu.Context(D, 2, 1, r, S, ntu.NTU_MIXED_BF16X3, 4, 8, B,
+                          stream=stream.cuda_stream)
+        ctx.batch_update_dev(B, Ta, Tb, G, Ta_o, Tb_o, info)
+        ctx.sync()
+    A_o, B_o, inf = Ta_o.cpu().numpy(), Tb_o.cpu().numpy(), info.cpu().numpy()
+    assert np.all(np.isfinite(A_o)) and np.all(np.isfinite(B_o)) and np.all(np.isfinite(inf))
+    nA = np.linalg.norm(A_o.reshape(B, -1), axis=1)
+    nB = np.linalg.norm(B_o.reshape(B, -1), axis=1)
+    assert np.max(np.abs(nA - 1)) < 1e-12 and np.max(np.abs(nB - 1)) < 1e-12
+    eps, delta, eps0, tau = inf[:, 0], inf[:, 1], inf[:, 2], inf[:, 3]
+    assert np.all(eps0 > 0)
+    assert np.all(delta >= 0) and np.all(delta <= 1)
+    np.testing.assert_allclose(delta, eps / eps0, rtol=1e-12, atol=0)
+    grid = np.array([10.0 ** -k for k in range(4, 9)])
+    assert np.all(np.min(np.abs(tau[:, None] / grid[None, :] - 1), axis=1) < 1e-12)
+    cfg = O.Config(D=D, r=r, sweeps=S, tau_exponents=tuple(range(4, 9)))
+    for i in (0, B // 2, B - 1):
+        A2, B2, ref = O.bond_update(Ta_h[i], Tb_h[i], G_h[i], cfg)
+        assert abs(inf[i, 2] - ref.eps0) <= 1e-4 * ref.eps0
+        assert abs(inf[i, 1] - ref.delta) <= 1e-2 * ref.delta
+        pair = np.einsum("plurn,qrvwx->plunqvwx", A_o[i], B_o[i])
+        pref = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
+        assert _rel(pair, pref) < 1e-4
