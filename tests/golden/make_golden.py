@@ -41,7 +41,7 @@ def one_step_d3():
 
 
 def quench(D, steps=200):
-    """TFIM quench h=2.5, dt=0.01 to t=2 (Sec. III, config 2): the start of
+    """TFIM quench h=2.5, dt=0.01 to t=2 (Sec. III): the start of
     inputs.quench_start(D) (|+x> zero-padded to D plus the seeded 1e-2
     admixture), second-order Trotter steps, 10 ALS sweeps, FP64; <sigma_x>
     of sites A and B after every step (cluster estimator)."""
@@ -59,7 +59,7 @@ def quench(D, steps=200):
 
 
 def purification(D, steps=100):
-    """Thermal state by purification (config 3): (|00>+|11>)/sqrt(2) per
+    """Thermal state by purification, h = 2.5, d_anc = 2: (|00>+|11>)/sqrt(2) per
     site zero-padded to D plus a seeded 1e-2 admixture (seed 77, both sites
     from one generator, each normalised), imaginary-time gates of h=2.5 with
     dbeta=0.005 to beta=0.5 on the physical index, 10 ALS sweeps, FP64;

@@ -433,7 +433,7 @@ def test_batch_update_host_and_dev_agree_and_empty_batch():
 
 
 # --------------------------------------------------------- unit cell
-def test_unit_cell_step_matches_oracle_config1():
+def test_unit_cell_step_matches_oracle_d3():
     """One Trotter step of the 2-site cell, D=3, seed 1, exp(-i 0.01 ZZ),
     10 sweeps: R, g, delta per bond and the final state."""
     A, B = I.random_pair(1, 2, 3)
@@ -652,7 +652,7 @@ def test_uneven_batch_matches_oracle_and_modes_agree(precision):
         ub.close()
 
 
-# ------------------------------------------------- full trajectories (configs 2, 3)
+# ------------------------- full trajectories (TFIM quench, purification)
 def _golden(name):
     import json
     return json.load(open(os.path.join(os.path.dirname(__file__), "golden", name)))
@@ -660,7 +660,7 @@ def _golden(name):
 
 @pytest.mark.parametrize("D,precision,tol", [(4, 0, 1e-4), (4, 2, 1e-3), (5, 0, 1e-4)])
 def test_quench_full_trajectory(D, precision, tol):
-    """Config 2 to t = 2 (200 steps): <sigma_x> of both sites after every step
+    """TFIM quench h = 2.5, dt = 0.01 to t = 2 (200 steps): <sigma_x> of both sites after every step
     against the oracle's trajectory stored by tests/golden/make_golden.py.
     The early steps truncate singular values of weight ~1e-15 (delta ~ 1e-15),
     so the kept directions are chosen by rounding: a 1e-14 relative
@@ -687,7 +687,7 @@ def test_quench_full_trajectory(D, precision, tol):
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-4), (2, 1e-4)])
 def test_purification_full_trajectory(precision, tol):
-    """Config 3 to beta = 0.5 (100 imaginary-time steps of dbeta = 0.005),
+    """Purification with h = 2.5 to beta = 0.5 (100 imaginary-time steps of dbeta = 0.005),
     D = 4: <sigma_x>, <sigma_z> of site A after every step against the
     oracle's stored trajectory (observed 1.4e-5 on both paths; the start is
     a padded product state, conditioned as in the quench)."""
