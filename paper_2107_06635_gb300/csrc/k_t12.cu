@@ -26,10 +26,14 @@
 // unit i-1), warps 2-9 turn accumulator 1 into the B operand of GEMM2 (two
 // buffers), warps 10-17 turn accumulator 2 into output rows in a swizzled
 // shared staging block that one thread stores with TMA.
+//
 // At D = 8 the units (k, k') and (k, k'+1) form a pair: epilogue 1 writes
 // both into one 128-row operand buffer (two such buffers) and GEMM2 of the
-// pair is one N = 128 product, which halves the MMA instructions of GEMM2 (their issue, not the
-// tensor pipe, bounds the kernel at N = 64).  Both epilogues write 16-byte chunks: the planar K of GEMM2 puts the eight
+// pair is one N = 128 product.  This halves GEMM2's MMA instructions, whose
+// issue (about 77 cycles each, whatever N), not the tensor pipe, sets the
+// kernel's pace.
+//
+// Both epilogues write 16-byte chunks: the planar K of GEMM2 puts the eight
 // u' values of one (u, n') next to each other, and the planar T2 the
 // sixteen columns a thread holds.  Every wait is bounded; every role leaves
 // its loop on a timeout and the epilogue groups leave together.
