@@ -222,6 +222,23 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
     if (e != cudaSuccess) { int st = cuda_check(nullptr, e, "stream"); delete c; return st; }
     c->own_stream = true;
   }
+  {
+    // the device this context runs on: its SM count sizes the persistent
+    // grids, and the kernels' shared-memory limits are set on it
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && c->sms < 1) c->sms = 1;
+    if (e == cudaSuccess) e = gate_qr_attributes();
+    if (e == cudaSuccess) e = t12_attributes();
+    if (e == cudaSuccess) e = tc_attributes();
+    if (e != cudaSuccess) {
+      int st = cuda_check(nullptr, e, "device attributes");
+      if (c->own_stream) cudaStreamDestroy(c->stream);
+      delete c;
+      return st;
+    }
+  }
   int st = plan_build(c);
   if (st != NTU_OK) { ntu_destroy(c); return fail(nullptr, st, "plan tables"); }
   c->w.cap = f.max_batch;
@@ -230,13 +247,9 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
   // build is split between them; see k_als).
   c->w.als_split = 1;
   if (f.precision != NTU_FP64) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
-      const int room = 3 * sms / f.max_batch;
-      c->w.als_split = room >= 4 ? 4 : (room >= 2 ? 2 : 1);
-      while (c->w.als_split > max_split && c->w.als_split > 1) c->w.als_split >>= 1;
-    }
+    const int room = 3 * c->sms / f.max_batch;
+    c->w.als_split = room >= 4 ? 4 : (room >= 2 ? 2 : 1);
+    while (c->w.als_split > max_split && c->w.als_split > 1) c->w.als_split >>= 1;
   }
   Carver dry;
   carve(c, dry);

@@ -493,6 +493,16 @@ __global__ void __launch_bounds__(NTU_CTA) k_measure(int d, int danc, int D,
 }
 
 // ------------------------------------------------------------ launchers
+static size_t gate_split_smem() { return sizeof(SvdSmem) + 16 * 16 * sizeof(double2); }
+
+cudaError_t gate_qr_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_gate_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gate_split_smem());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_qr_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)qr_df_smem_bytes());
+}
+
 static inline int grid_for(long long work) {
   long long b = (work + NTU_CTA - 1) / NTU_CTA;
   return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
@@ -503,12 +513,7 @@ cudaError_t launch_gate_qr(ntu_ctx* c, int n, const double2* Ta, const double2* 
                            double2* QB, double2* RB) {
   const Plan& P = c->plan;
   Work& W = c->w;
-  size_t sm = sizeof(SvdSmem) + 16 * 16 * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gate_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
+  const size_t sm = gate_split_smem();
   k_gate_split<<<n, NTU_CTA, sm, c->stream>>>(P.d, P.r, swap_sites, G, W.GA, W.GB);
   cudaError_t e = after_launch(c, "k_gate_split");
   if (e != cudaSuccess) return e;
@@ -520,11 +525,6 @@ cudaError_t launch_gate_qr(ntu_ctx* c, int n, const double2* Ta, const double2* 
   if (e != cudaSuccess) return e;
   if (c->cfg.precision != NTU_FP64) {
     const size_t sq = qr_df_smem_bytes();
-    static bool attr_df = false;
-    if (!attr_df) {
-      cudaFuncSetAttribute(k_qr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq);
-      attr_df = true;
-    }
     k_qr_df<<<dim3(n, 2), NTU_CTA, sq, c->stream>>>(P.m, P.K, W.Mg, (float4*)W.Qcm, QA, RA, QB,
                                                    RB, W.qrflag, c->d_paths);
     e = after_launch(c, "k_qr_df");

@@ -1065,13 +1065,7 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   a.gdf = reinterpret_cast<float4*>(W.gscr);
   a.gdfT = reinterpret_cast<float4*>(W.gw);     // the repair's eigenvector scratch, free here
   size_t sm = sizeof(AlsShared);
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  const int sms = c->sms;
   // a batch that leaves SMs idle gives each item 2 or 4 CTAs (one cluster)
   int split = a.df ? W.als_split : 1;
   while (split > 1 && (long long)n * split > 3LL * sms) split >>= 1;

@@ -470,6 +470,13 @@ __global__ void __launch_bounds__(T12_THREADS, 1) k_t12(const __grid_constant__ 
 
 size_t t12_smem_bytes() { return T12_SMEM; }
 
+cudaError_t t12_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_t12<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)T12_SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_t12<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T12_SMEM);
+}
+
 // Etop: the split top edge of this half (W.ETLd or W.ETRd, doubled A
 // operand rows of 2 krpE BF16, rowsE rows per item), read by epilogue 2.
 // The output (T2 split operand, W.T2s) is written through the plan's store
@@ -486,20 +493,7 @@ cudaError_t launch_t12(ntu_ctx* c, int n, const void* Etop) {
   a.e_item = P.rowsE * 2 * P.krpE;
   a.err = c->d_status;
   if (a.units == 0) return cudaSuccess;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  const int grid = (int)(a.units < sms ? a.units : sms);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_t12<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T12_SMEM);
-    cudaFuncSetAttribute(k_t12<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T12_SMEM);
-    attr = true;
-  }
+  const int grid = (int)(a.units < c->sms ? a.units : c->sms);
   if (P.D == 8)
     k_t12<8><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(P.mapYs, P.mapQs, P.mapT2st, a);
   else

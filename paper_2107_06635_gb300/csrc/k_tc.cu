@@ -291,6 +291,18 @@ int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, lo
   return r == CUDA_SUCCESS ? NTU_OK : NTU_ECUDA;
 }
 
+cudaError_t tc_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcCfg<0>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcCfg<1>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcCfg<2>::SMEM);
+  return e;
+}
+
 cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out) {
   TcArgs a = op.args;
   const int* t = c->plan.d_tab;
@@ -300,25 +312,14 @@ cudaError_t launch_tc_gemm(ntu_ctx* c, const TcOp& op, int n, void* out) {
   a.out = out;
   a.err = c->d_status;
   a.mtiles = op.mtiles;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
   const long long tiles = (long long)((a.N + TBN - 1) / TBN) * op.mtiles * n;
-  const int grid = (int)(tiles < sms ? tiles : sms);
+  const int grid = (int)(tiles < c->sms ? tiles : c->sms);
   if (grid <= 0) return cudaSuccess;
-  static bool attr[3] = {false, false, false};
   if (op.mode == 0) {
-    if (!attr[0]) { cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<0>::SMEM); attr[0] = true; }
     k_tc_gemm<0><<<grid, TC_THREADS, TcCfg<0>::SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   } else if (op.mode == 1) {
-    if (!attr[1]) { cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<1>::SMEM); attr[1] = true; }
     k_tc_gemm<1><<<grid, TC_THREADS, TcCfg<1>::SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   } else {
-    if (!attr[2]) { cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<2>::SMEM); attr[2] = true; }
     k_tc_gemm<2><<<grid, TC_THREADS, TcCfg<2>::SMEM, c->stream>>>(op.mapA, op.mapB, a, n);
   }
   return after_launch(c, "k_tc_gemm");

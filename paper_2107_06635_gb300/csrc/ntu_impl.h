@@ -127,6 +127,7 @@ struct ntu_ctx {
                       //  repair Gershgorin, repair Cholesky, repair eigen,
                       //  QR CholeskyQR2, QR Householder]
   int debug_sync;     // synchronise and check after every launch (NTU_DEBUG_SYNC=1)
+  int sms;            // streaming multiprocessors of the context's device
 };
 
 namespace ntu {
@@ -164,6 +165,12 @@ cudaError_t launch_measure(ntu_ctx* c, const double2* T, const double2* N, const
                            double2* out);
 cudaError_t launch_copy_raw(ntu_ctx* c, int n, const void* graw, double2* g);
 size_t als_smem_bytes();
+// Dynamic shared-memory limits of the fixed-size kernels, set on the
+// current device when a context is created there (k_gate_qr.cu, k_t12.cu,
+// k_tc.cu).
+cudaError_t gate_qr_attributes();
+cudaError_t t12_attributes();
+cudaError_t tc_attributes();
 
 // tensor-core environment (k_tc.cu, k_env.cu)
 int tc_make_map(CUtensorMap* map, void* base, long long cols, long long rows, long long items,
