@@ -85,3 +85,18 @@ def test_uneven_init_rejects_bad_kinds(lib):
     assert lib.ntu_uneven_fetch(None, 0, None, None, None, None) == 1
     assert lib.ntu_uneven_update_host(None, 0, None, None, None, None, None, None, None, 0) == 1
     assert lib.ntu_uneven_last_launch_count(None) == 0
+
+
+def test_init_without_a_device_fails_cleanly(lib):
+    """A valid configuration on a machine without a usable GPU: context
+    creation reports a CUDA error (NTU_ECUDA = 3) with a message, returns no
+    handle and leaves the library usable."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = ntu.Config(4, 2, 1, 2, 10, 2, 4, 8, 8)
+    h = ctypes.c_void_p()
+    assert lib.ntu_init(ctypes.byref(cfg), None, ctypes.byref(h)) == 3
+    assert h.value is None
+    assert lib.ntu_last_error(None)
+    assert lib.ntu_init(None, None, None) == 1
