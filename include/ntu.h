@@ -120,7 +120,8 @@ int ntu_env_metric(ntu_ctx* ctx, int bond, double* g_out, double* diag_out);
 /* Fig. 5, Eqs. 2-5: SVDU start, als_sweeps ALS sweeps with the tolerance
  * chosen to minimise eps, balancing, then A' = Q_A M_A, B' = Q_B M_B written
  * back into the context's state (unit Frobenius norm each).  Outputs (may be
- * NULL): eps, delta = eps / eps0, and the last selected tolerance. */
+ * NULL): eps, delta = eps / eps0, and the last selected tolerance (NaN when
+ * als_sweeps = 0: the result is then the SVDU truncation of Fig. 2(c,d)). */
 int ntu_als_truncate(ntu_ctx* ctx, int bond, double* eps_out, double* delta_out,
                      double* tau_out);
 
@@ -143,7 +144,7 @@ int ntu_measure(ntu_ctx* ctx, int site, const double* op, double* value_out);
  * items; work is queued on the context's stream and the call returns at once. */
 
 /* The whole update: Ta_out / Tb_out receive A', B'; info (n x 4 doubles)
- * receives [eps, delta, eps0, tau] per item. */
+ * receives [eps, delta, eps0, tau] per item (tau NaN when als_sweeps = 0). */
 int ntu_batch_update_dev(ntu_ctx* ctx, int n, const double* Ta, const double* Tb,
                          const double* gates, double* Ta_out, double* Tb_out,
                          double* info);

@@ -919,7 +919,11 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   double2* gC0 = a.gC + item * split * nA2;
   int phase = 0;
   const double tau_max = als_tau(a.kmin < 0 ? 0 : a.kmin);
-  if (tid == 0) { sm.err = 0; sm.n_cg = 0; sm.n_fast = 0; sm.n_eig = 0; sm.ge = 0; }
+  // tau_sel stays NaN when no solve runs (zero sweeps: the SVDU truncation)
+  if (tid == 0) {
+    sm.err = 0; sm.n_cg = 0; sm.n_fast = 0; sm.n_eig = 0; sm.ge = 0;
+    sm.tau_sel = __longlong_as_double(0x7ff8000000000000ll);
+  }
   // X0 = R_A R_B^T, x0 = vec(X0) with kA slow
   for (int idx = tid; idx < K * K; idx += NTU_CTA) {
     int i = idx / K, j = idx % K;

@@ -281,12 +281,14 @@ def test_repair_clips_negative_eigenvalues():
 
 # ------------------------------------------------------------------ ALS
 @pytest.mark.parametrize("D,r,sweeps,kmin", [(2, 2, 3, 4), (3, 2, 10, 4), (4, 2, 5, 4),
-                                             (3, 4, 4, 4), (3, 2, 4, 0), (5, 2, 2, 0)])
+                                             (3, 4, 4, 4), (3, 2, 4, 0), (5, 2, 2, 0),
+                                             (4, 2, 0, 4)])
 def test_als_matches_oracle(D, r, sweeps, kmin):
     """kmin=4: g_A is well conditioned, the Cholesky certificate decides the
     tolerance selection.  kmin=0: the grid starts at tau=1, which drops every
     eigenpair, so the certificate cannot hold and every solve goes through
-    the eigendecomposition and the full selection."""
+    the eigendecomposition and the full selection.  sweeps=0: the balanced
+    SVDU truncation with no solve, reported tau NaN."""
     n = 2
     Ta, Tb, G = _items(600 + D, n, 2, D)
     cfg = O.Config(D=D, r=r, sweeps=sweeps, tau_exponents=tuple(range(kmin, 16)))
@@ -305,7 +307,9 @@ def test_als_matches_oracle(D, r, sweeps, kmin):
     ctx.sync()
     paths = ctx.solver_paths()
     solves = n * 2 * sweeps
-    if kmin == 4:
+    if sweeps == 0:
+        assert sum(paths[k] for k in ("als_gershgorin", "als_cholesky", "als_eigen")) == 0
+    elif kmin == 4:
         # random-tensor metrics give diagonally dominant g_A: the discs decide
         assert paths["als_gershgorin"] + paths["als_cholesky"] == solves
         assert paths["als_gershgorin"] > 0 and paths["als_eigen"] == 0
@@ -318,7 +322,10 @@ def test_als_matches_oracle(D, r, sweeps, kmin):
         assert abs(inf[2] - eps0) < 1e-12 * eps0
         assert abs(inf[1] - delta) < 1e-8
         assert abs(inf[0] - eps) < 1e-8 * eps0
-        assert inf[3] == tau
+        if sweeps == 0:
+            assert tau is None and np.isnan(inf[3])
+        else:
+            assert inf[3] == tau
         assert _rel(MA[i].cpu().numpy(), ma) < 1e-8
         assert _rel(MB[i].cpu().numpy(), mb) < 1e-8
 

@@ -190,6 +190,29 @@ def test_p5_identity_metric_keeps_svdu():
     assert abs(eps0 - np.sum(s ** 2)) <= 1e-12 * eps0
 
 
+def test_zero_sweeps_is_the_balanced_svdu_truncation():
+    """No ALS sweep (the standalone SVDU mode, Fig. 2(c,d)): M_A M_B^T is the
+    rank-D truncated SVD of R_A R_B^T (Eckart-Young), both factors carry
+    sqrt(S) (Fig. 5(d)), no tolerance was selected, and eps is that
+    product's error in the metric g, whatever g is."""
+    rng = np.random.default_rng(16)
+    K, D = 8, 3
+    RA = rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K))
+    RB = rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K))
+    Z = rng.standard_normal((K * K, K * K)) + 1j * rng.standard_normal((K * K, K * K))
+    g = Z @ Z.conj().T
+    MA, MB, eps, delta, eps0, tau = O.als_truncate(g, RA, RB, D, 0, O.Config(D=D).taus)
+    U, s, Vh = np.linalg.svd(RA @ RB.T)
+    best = (U[:, :D] * s[:D]) @ Vh[:D]
+    assert np.linalg.norm(MA @ MB.T - best) <= 1e-12 * np.linalg.norm(best)
+    assert np.allclose(np.linalg.svd(MA, compute_uv=False), np.sqrt(s[:D]), rtol=1e-12)
+    assert np.allclose(np.linalg.svd(MB, compute_uv=False), np.sqrt(s[:D]), rtol=1e-12)
+    assert tau is None
+    x = (best - RA @ RB.T).reshape(-1)
+    assert abs(eps - np.real(np.vdot(x, g @ x))) <= 1e-10 * eps0
+    assert delta == pytest.approx(eps / eps0, rel=1e-14)
+
+
 # --------------------------------------------- P6: separable metric optimum
 def _sqrtm_h(m):
     lam, w = np.linalg.eigh(m)
