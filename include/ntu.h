@@ -74,7 +74,8 @@ typedef struct {
   int d_phys;       /* physical dimension, 2 <= d_phys <= 4                  */
   int d_anc;        /* ancilla dimension (1: none, 2: purification)         */
   int r;            /* gate rank kept by the split, 1 <= r <= d_phys^2      */
-  int als_sweeps;   /* fixed number of ALS sweeps (Fig. 5, Eq. 5)           */
+  int als_sweeps;   /* fixed number of ALS sweeps (Fig. 5, Eq. 5), 0..1000; */
+                    /*   0: the SVDU truncation of Fig. 2(c,d) only          */
   int precision;    /* ntu_precision                                         */
   int tau_kmin;     /* candidate pseudo-inverse tolerances are 10^-k,       */
   int tau_kmax;     /*   k = tau_kmin..tau_kmax (Eq. 4)                      */
@@ -83,6 +84,10 @@ typedef struct {
 
 /* Create a context for one (D, d, r) configuration.  `stream` is a
  * cudaStream_t (NULL: the context creates its own non-blocking stream).
+ * The context belongs to the device current at this call: its memory, the
+ * SM count that sizes its persistent grids and the kernels' shared-memory
+ * limits are that device's, so make it current for every later call on the
+ * context.  Without a usable device the call returns NTU_ECUDA.
  * Requires d_p * D^2 >= r so that the gated site matrix has at least K rows,
  * and D * r <= 32.  NTU_MIXED_BF16X3 needs a compute capability 10.x GPU and
  * 2 * d_p * D <= 64 (else NTU_EUNSUPPORTED, before any device work).
