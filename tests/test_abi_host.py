@@ -100,3 +100,13 @@ def test_init_without_a_device_fails_cleanly(lib):
     assert h.value is None
     assert lib.ntu_last_error(None)
     assert lib.ntu_init(None, None, None) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises
+    instead of computing anything."""
+    monkeypatch.setattr(ntu, "_LIB", None)
+    monkeypatch.setattr(B, "LIB", str(tmp_path / "libntu_missing.so"))
+    with pytest.raises(OSError):
+        ntu.load(build=False)
+    assert ntu._LIB is None
