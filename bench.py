@@ -112,11 +112,13 @@ def env_roof(precision, achieved, peaks):
     BF16 tensor cores (measured dense peak; the split products issue 3x the
     algorithmic flops), FP32 FMA or FP64."""
     if precision == "bf16x3":
-        peak = peaks.get("bf16_tflops", 1900.0) * 1e12
+        if "bf16_tflops" in peaks:
+            peak, src = peaks["bf16_tflops"] * 1e12, "measured bf16 dense (MEASURED_PEAKS.json)"
+        else:
+            peak, src = 1900.0e12, "fallback bf16 dense 1.9 PFLOP/s (no measured peak)"
         return {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "issued_frac": 3 * achieved / peak,
-                "peak_source": "measured bf16 dense (MEASURED_PEAKS.json)"}
+                "issued_frac": 3 * achieved / peak, "peak_source": src}
     key = "fp32_tflops" if precision == "fp32" else "fp64_tflops"
     if key in peaks:
         peak = peaks[key] * 1e12

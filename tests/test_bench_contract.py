@@ -44,3 +44,14 @@ def test_reference_arm_other_ranks_exit_quietly():
     out = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip() == ""
+
+
+def test_environment_roofline_names_its_peak():
+    sys.path.insert(0, ROOT)
+    import bench
+    m = bench.env_roof("bf16x3", 950e12, {"bf16_tflops": 1900.0})
+    assert m["frac"] == 0.5 and m["issued_frac"] == 1.5 and "measured" in m["peak_source"]
+    f = bench.env_roof("bf16x3", 950e12, {})
+    assert f["peak"] == 1900.0 and "fallback" in f["peak_source"]
+    a = bench.env_roof("fp64", 1.1e12, {"fp64_tflops": 1.1})
+    assert a["bound"] == "alu" and abs(a["frac"] - 1.0) < 1e-12 and "measured" in a["peak_source"]
