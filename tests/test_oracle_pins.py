@@ -425,3 +425,158 @@ def test_golden_quench_trajectory_regression():
         assert abs(O.measure(A, B, 1, I.pauli("X"), 1).real - ref["sx_B"][s]) < 1e-10
     assert abs(ref["sx_A"][0] - (1 - 8 * ref["dt"] ** 2)) < 1e-5
     assert abs(ref["sx_B"][0] - (1 - 8 * ref["dt"] ** 2)) < 1e-5
+
+
+# ------------------------------- bond orientation and gate-site order pins
+# Axis of T[p, l, u, r, dn] that carries bond b on site A and on site B
+# (bond b is A's leg b in the order r, u, l, dn; B's leg is the opposite one).
+_BOND_LEGS = {0: (3, 1), 1: (2, 4), 2: (1, 3), 3: (4, 2)}
+
+
+def _zx_gate(t):
+    """exp(-i t Z(x)X) = cos t 1 - i sin t Z(x)X: operator-Schmidt rank 2 and
+    not symmetric under exchanging the two sites."""
+    return I.two_site(np.cos(t) * np.eye(4)
+                      - 1j * np.sin(t) * np.kron(I.pauli("Z"), I.pauli("X")))
+
+
+def _exact_pair_after_zx(psiA, psiB, t):
+    """(exp(-i t Z_A X_B)) |psiA>|psiB> as a 2 x 2 array [sA, sB], written
+    out from (Z(x)X)^2 = 1."""
+    Z, X = I.pauli("Z"), I.pauli("X")
+    return np.cos(t) * np.outer(psiA, psiB) - 1j * np.sin(t) * np.outer(Z @ psiA, X @ psiB)
+
+
+def _bond_pin(update, bond, t=0.3):
+    """A D=1 product state zero-padded to D=2 and the site-asymmetric gate
+    exp(-i t Z_A X_B) on one bond: the exact two-site state has bond rank 2,
+    so the update is exact.  Returns (A' support only on its bond leg,
+    B' support only on its bond leg, |overlap| of the contracted pair with the
+    exact state)."""
+    psiA = np.array([0.6, 0.8], dtype=np.complex128)
+    psiB = np.array([0.8, -0.6j], dtype=np.complex128)
+    A, B = I.product_state(psiA, 2), I.product_state(psiB, 2)
+    A2, B2, _ = update(A, B, bond, _zx_gate(t), O.Config(D=2, r=2, sweeps=4))
+    la, lb = _BOND_LEGS[bond]
+
+    def only_on(T, leg):
+        other = [k for k in range(1, 5) if k != leg]
+        idx = np.argwhere(np.abs(T) > 1e-12 * np.abs(T).max())
+        return all(all(ix[k] == 0 for k in other) for ix in idx)
+
+    a = np.moveaxis(A2, la, -1)[:, 0, 0, 0, :]      # [sA, bond]
+    b = np.moveaxis(B2, lb, -1)[:, 0, 0, 0, :]      # [sB, bond]
+    pair = (a @ b.T).reshape(-1)
+    ref = _exact_pair_after_zx(psiA, psiB, t).reshape(-1)
+    ov = abs(np.vdot(pair, ref)) / (np.linalg.norm(pair) * np.linalg.norm(ref))
+    return only_on(A2, la), only_on(B2, lb), ov
+
+
+@pytest.mark.parametrize("bond", [0, 1, 2, 3])
+def test_bond_orientation_and_gate_site_order(bond):
+    """Bond b joins A's leg b (r, u, l, dn) to B's opposite leg, and the gate's
+    first site is A (Sec. II: four inequivalent bonds; Fig. 2).  From a
+    product state the exact result of exp(-i t Z_A X_B) has bond rank 2, so
+    every update is exact: A' and B' must carry the new bond on the right legs
+    (all other legs stay at index 0) and contract to the exact state with Z
+    on A and X on B.  A counter-clockwise rotation moves the support of
+    bonds 1 and 3 onto the opposite legs; a missing site swap on bonds 2 and
+    3 puts X on A."""
+    onA, onB, ov = _bond_pin(O.update_bond, bond)
+    assert onA and onB
+    assert abs(ov - 1) < 1e-13
+
+
+def test_bond_pin_catches_planted_mistakes(monkeypatch):
+    """The pin above fails on the two plausible mistakes it is there for."""
+    def no_swap(A, B, bond, G, cfg, keep=False):
+        if bond in (1, 3):
+            A, B = O.rotate(A), O.rotate(B)
+        if bond in (0, 1):
+            A, B, info = O.bond_update(A, B, G, cfg, keep)
+        else:
+            B, A, info = O.bond_update(B, A, G, cfg, keep)     # gate not swapped
+        if bond in (1, 3):
+            A, B = O.unrotate(A), O.unrotate(B)
+        return A, B, info
+
+    for bond in (2, 3):
+        assert abs(_bond_pin(no_swap, bond)[2] - 1) > 1e-2
+    monkeypatch.setattr(O, "rotate", lambda T: np.ascontiguousarray(T.transpose(0, 2, 3, 4, 1)))
+    monkeypatch.setattr(O, "unrotate", lambda T: np.ascontiguousarray(T.transpose(0, 4, 1, 2, 3)))
+    for bond in (1, 3):
+        onA, onB, _ = _bond_pin(O.update_bond, bond)
+        assert not (onA and onB)
+
+
+# ------------------------------------------ Hermitisation and repair pins
+def _metric_with_spectrum(rng, lam, antiherm=0.0):
+    """W diag(lam) W^H for a random unitary W, plus `antiherm` times a random
+    anti-Hermitian matrix (which the Hermitisation must remove)."""
+    n = lam.size
+    W = _random_unitary(rng, n)
+    H = (W * lam) @ W.conj().T
+    S = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return H + antiherm * 0.5 * (S - S.conj().T), W
+
+
+def test_repair_of_an_indefinite_metric_is_the_nearest_psd_matrix():
+    """Sec. II: g must be Hermitian and non-negative.  For a Hermitian part
+    H = W diag(lam) W^H with negative lam, the nearest PSD matrix in the
+    Frobenius norm is W diag(max(lam, 0)) W^H, at distance
+    sqrt(sum_{lam<0} lam^2).  The repaired g times the removed trace
+    t = exp(diag[2]) must be that matrix, the unit-trace result PSD, and the
+    diagnostics ||g - g^H|| / ||g|| and lam_min / lam_max equal their values
+    from the construction."""
+    rng = np.random.default_rng(17)
+    lam = np.array([3.0, 2.0, 1.5, 1.0, 0.5, 0.25, -0.2, -0.7])
+    g, W = _metric_with_spectrum(rng, lam, antiherm=0.3)
+    H = 0.5 * (g + g.conj().T)
+    rep, (herm_err, ratio, logt) = O.hermitise_repair(g)
+    t = np.exp(logt)
+    nearest = (W * np.maximum(lam, 0)) @ W.conj().T
+    assert abs(t - np.maximum(lam, 0).sum()) < 1e-13 * t
+    assert np.linalg.norm(t * rep - nearest) < 1e-13 * np.linalg.norm(nearest)
+    assert abs(np.linalg.norm(t * rep - H) - np.sqrt(np.sum(lam[lam < 0] ** 2))) < 1e-13
+    assert np.linalg.norm(rep - rep.conj().T) <= 1e-15 * np.linalg.norm(rep)
+    assert abs(np.trace(rep) - 1) < 1e-14
+    assert np.linalg.eigvalsh(0.5 * (rep + rep.conj().T))[0] > -1e-15
+    assert abs(herm_err - np.linalg.norm(g - H) * 2 / np.linalg.norm(g)) < 1e-14
+    assert abs(ratio - lam.min() / lam.max()) < 1e-13
+
+
+def test_repair_of_a_psd_metric_only_normalises():
+    """A Hermitian PSD metric is returned as g / tr g, and log(tr g) reported."""
+    rng = np.random.default_rng(18)
+    lam = np.array([5.0, 2.0, 1.0, 0.3, 0.1, 0.0])
+    g, _ = _metric_with_spectrum(rng, lam)
+    g = 0.5 * (g + g.conj().T)
+    rep, (herm_err, ratio, logt) = O.hermitise_repair(g)
+    tr = np.real(np.trace(g))
+    assert np.linalg.norm(rep - g / tr) < 1e-14 * np.linalg.norm(g / tr)
+    assert abs(logt - np.log(lam.sum())) < 1e-14
+    assert herm_err < 1e-15
+
+
+def test_repair_pins_catch_planted_mistakes(monkeypatch):
+    """Clipping to |lam| instead of max(lam, 0), or skipping the
+    Hermitisation, breaks the nearest-PSD pin."""
+    rng = np.random.default_rng(17)
+    lam = np.array([3.0, 2.0, 1.5, 1.0, 0.5, 0.25, -0.2, -0.7])
+    g, W = _metric_with_spectrum(rng, lam, antiherm=0.3)
+    nearest = (W * np.maximum(lam, 0)) @ W.conj().T
+
+    def abs_clip(gg):
+        h = 0.5 * (gg + gg.conj().T)
+        lm, V = np.linalg.eigh(h)
+        gr = (V * np.abs(lm)) @ V.conj().T
+        return gr / np.real(np.trace(gr)), (0.0, 0.0, float(np.log(np.real(np.trace(gr)))))
+
+    def no_herm(gg):
+        lm, V = np.linalg.eigh(gg)             # reads one triangle only
+        gr = (V * np.maximum(lm, 0)) @ V.conj().T
+        return gr / np.real(np.trace(gr)), (0.0, 0.0, float(np.log(np.real(np.trace(gr)))))
+
+    for bad in (abs_clip, no_herm):
+        rep, (_, _, logt) = bad(g)
+        assert np.linalg.norm(np.exp(logt) * rep - nearest) > 1e-2 * np.linalg.norm(nearest)
