@@ -80,6 +80,12 @@ typedef struct {
   int tau_kmin;     /* candidate pseudo-inverse tolerances are 10^-k,       */
   int tau_kmax;     /*   k = tau_kmin..tau_kmax (Eq. 4)                      */
   int max_batch;    /* largest n accepted by the ntu_batch_* calls          */
+  int wait_budget;  /* polls (about 0.25 us each) a device-side rendezvous  */
+                    /*   between the CTAs of one item may wait before it     */
+                    /*   gives up and raises NTU_ETIMEOUT; 0: 2^23 (~2 s).   */
+                    /*   The tensor-core kernels' internal pipeline waits    */
+                    /*   keep a fixed limit of 2^28 polls: a short budget    */
+                    /*   there would end a CTA with copies in flight.        */
 } ntu_config;
 
 /* Create a context for one (D, d, r) configuration.  `stream` is a
@@ -238,6 +244,16 @@ int ntu_batch_als_dev(ntu_ctx* ctx, int n, const double* g, const double* RA,
 int ntu_batch_recompose_dev(ntu_ctx* ctx, int n, const double* QA, const double* QB,
                             const double* MA, const double* MB, double* Ta_out,
                             double* Tb_out);
+
+/* Failure-detection test hook.  With `on` = 1 every later ALS rendezvous of
+ * the context waits for one arrival more than the CTAs of an item make, so
+ * each such wait runs out after wait_budget polls and the next synchronising
+ * call returns NTU_ETIMEOUT (the results of that call are invalid); `on` = 0
+ * restores normal operation.  Only contexts whose ALS runs on CTA clusters
+ * have this rendezvous (mixed precision and max_batch <= 3 * SMs / 2);
+ * others return NTU_EUNSUPPORTED.  No wait is unbounded, nothing faults, and
+ * the context stays usable. */
+int ntu_inject_wait_timeout(ntu_ctx* ctx, int on);
 
 /* Number of kernel launches the last ntu_batch_update_* call queued. */
 int ntu_last_launch_count(const ntu_ctx* ctx);

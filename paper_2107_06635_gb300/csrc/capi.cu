@@ -205,6 +205,7 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
   if (f.tau_kmin < 0 || f.tau_kmax > 20 || f.tau_kmin > f.tau_kmax)
     return fail(nullptr, NTU_EINVAL, "tau_kmin=%d tau_kmax=%d", f.tau_kmin, f.tau_kmax);
   if (f.max_batch < 1 || f.max_batch > 65535) return fail(nullptr, NTU_EINVAL, "max_batch=%d", f.max_batch);
+  if (f.wait_budget < 0) return fail(nullptr, NTU_EINVAL, "wait_budget=%d", f.wait_budget);
   // the fused t1-t2 of the split-BF16 environment holds one 64-wide K tile
   // of Y and conj(Q): 2 d_p D real columns at most
   if (f.precision == NTU_MIXED_BF16X3 && 2 * f.d_phys * f.d_anc * f.D > 64)
@@ -215,6 +216,7 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
   if (!c) return fail(nullptr, NTU_ENOMEM, "host allocation");
   memset(c, 0, sizeof(*c));
   c->cfg = f;
+  c->wait_polls = f.wait_budget > 0 ? (long long)f.wait_budget : (1ll << 23);
   c->env_es = f.precision == NTU_FP64 ? sizeof(double2) : sizeof(float2);
   if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
   else {
@@ -316,6 +318,14 @@ extern "C" int ntu_sync(ntu_ctx* c) {
 }
 
 extern "C" int ntu_last_launch_count(const ntu_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" int ntu_inject_wait_timeout(ntu_ctx* c, int on) {
+  if (!c) return fail(c, NTU_EINVAL, "NULL context");
+  if (c->w.als_split < 2)
+    return fail(c, NTU_EUNSUPPORTED, "this context's ALS runs one CTA per item: no rendezvous");
+  c->inject_timeout = on ? 1 : 0;
+  return NTU_OK;
+}
 
 extern "C" int ntu_solver_paths(ntu_ctx* c, int* counts) {
   if (!c || !counts) return fail(c, NTU_EINVAL, "ntu_solver_paths: NULL argument");

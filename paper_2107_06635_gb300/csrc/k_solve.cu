@@ -250,6 +250,8 @@ struct AlsArgs {
   int split;                   // CTAs per item (a cluster); the private scratch above
                                // (x0 ... rk, gA, gC) has n * split copies
   int* sync;                   // n exchange counters, zero at launch (split > 1)
+  long long wait_polls;        // poll limit of a rendezvous
+  int sync_extra;              // 0; 1 only under ntu_inject_wait_timeout
 };
 
 // out = g v in double-FP32 products from the split copy gdf = g 2^-ge (mixed
@@ -291,11 +293,11 @@ __device__ void als_exchange(const AlsArgs& a, long long item, int& phase) {
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(a.sync + item, 1);
-    const int target = phase * a.split;
+    const int target = phase * a.split + a.sync_extra;
     const volatile int* cnt = a.sync + item;
     long long it = 0;
     while (*cnt < target) {
-      if (++it > (1ll << 23)) {
+      if (++it > a.wait_polls) {
         raise_status(a.status, ST_TIMEOUT, WHY_ALS_SYNC);
         break;
       }
@@ -1075,6 +1077,8 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   while (split > 1 && (long long)n * split > 3LL * sms) split >>= 1;
   a.split = split;
   a.sync = W.als_sync;
+  a.wait_polls = c->wait_polls;
+  a.sync_extra = c->inject_timeout;
   if (split > 1) {
     cudaError_t e = cudaMemsetAsync(W.als_sync, 0, sizeof(int) * (size_t)n, c->stream);
     if (e != cudaSuccess) return e;

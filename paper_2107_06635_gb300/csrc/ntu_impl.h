@@ -128,6 +128,8 @@ struct ntu_ctx {
                       //  QR CholeskyQR2, QR Householder]
   int debug_sync;     // synchronise and check after every launch (NTU_DEBUG_SYNC=1)
   int sms;            // streaming multiprocessors of the context's device
+  long long wait_polls;   // poll limit of the ALS rendezvous (wait_budget, or 2^23)
+  int inject_timeout;     // ntu_inject_wait_timeout: rendezvous target one too high
 };
 
 namespace ntu {

@@ -30,7 +30,7 @@ class Config(ctypes.Structure):
     _fields_ = [("D", ctypes.c_int), ("d_phys", ctypes.c_int), ("d_anc", ctypes.c_int),
                 ("r", ctypes.c_int), ("als_sweeps", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tau_kmin", ctypes.c_int), ("tau_kmax", ctypes.c_int),
-                ("max_batch", ctypes.c_int)]
+                ("max_batch", ctypes.c_int), ("wait_budget", ctypes.c_int)]
 
 
 _LIB = None
@@ -59,6 +59,7 @@ _SIGS = {
     "ntu_batch_als_dev": [_P, _I, _P, _P, _P, _P, _P, _P],
     "ntu_batch_recompose_dev": [_P, _I, _P, _P, _P, _P, _P, _P],
     "ntu_last_launch_count": [_P],
+    "ntu_inject_wait_timeout": [_P, _I],
     "ntu_set_profiling": [_P, _I],
     "ntu_stage_times": [_P, _P],
     "ntu_solver_paths": [_P, _P],
@@ -126,9 +127,10 @@ class Context:
 
     def __init__(self, D: int, d: int = 2, d_anc: int = 1, r: int = 2, sweeps: int = 10,
                  precision: int = NTU_FP64, tau_kmin: int = 4, tau_kmax: int = 15,
-                 max_batch: int = 1, stream=None):
+                 max_batch: int = 1, stream=None, wait_budget: int = 0):
         self.lib = load()
-        self.cfg = Config(D, d, d_anc, r, sweeps, precision, tau_kmin, tau_kmax, max_batch)
+        self.cfg = Config(D, d, d_anc, r, sweeps, precision, tau_kmin, tau_kmax, max_batch,
+                          wait_budget)
         self.D, self.d, self.d_anc, self.r = D, d, d_anc, r
         self.d_p = d * d_anc
         self.K = D * r
@@ -246,6 +248,9 @@ class Context:
     def batch_recompose_dev(self, n, QA, QB, MA, MB, Ta_out, Tb_out):
         self._ck(self.lib.ntu_batch_recompose_dev(self.h, n, _ptr(QA), _ptr(QB), _ptr(MA),
                                                   _ptr(MB), _ptr(Ta_out), _ptr(Tb_out)))
+
+    def inject_wait_timeout(self, on: bool = True):
+        self._ck(self.lib.ntu_inject_wait_timeout(self.h, 1 if on else 0))
 
     def last_launch_count(self) -> int:
         return self.lib.ntu_last_launch_count(self.h)

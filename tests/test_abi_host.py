@@ -29,7 +29,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 @pytest.mark.parametrize("field,value", [("D", 0), ("D", 9), ("d_phys", 1), ("r", 0), ("r", 5),
-                                          ("precision", 7), ("tau_kmin", 9), ("max_batch", 0)])
+                                          ("precision", 7), ("tau_kmin", 9), ("max_batch", 0),
+                                          ("wait_budget", -1)])
 def test_init_rejects_bad_config(lib, field, value):
     cfg = ntu.Config(4, 2, 1, 2, 10, 0, 4, 15, 1)
     if field == "tau_kmin":
@@ -64,6 +65,7 @@ def test_null_arguments(lib):
     assert lib.ntu_init(None, None, None) == 1
     assert lib.ntu_destroy(None) == 0
     assert lib.ntu_sync(None) == 1
+    assert lib.ntu_inject_wait_timeout(None, 1) == 1
 
 
 def test_uneven_init_rejects_bad_kinds(lib):

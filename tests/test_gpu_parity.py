@@ -462,6 +462,104 @@ def test_unit_cell_step_matches_oracle_d3():
     assert _rel(A2, Ao) < 1e-9 and _rel(B2, Bo) < 1e-9
 
 
+def test_unit_cell_step_site_asymmetric_gates_d3():
+    """The unit-cell calls with a different random two-site unitary on each
+    bond (not symmetric under exchanging the sites, distinct operator-Schmidt
+    values): exercises the gate-site swap of bonds 2 and 3 and the rotation
+    of bonds 1 and 3 (Sec. II, Fig. 2) against the oracle, stage by stage."""
+    A, B = I.random_pair(3, 2, 3)
+    rng = np.random.default_rng(33)
+    gates = [I.random_gate(rng) for _ in range(4)]
+    for G in gates:
+        assert np.linalg.norm(G - G.transpose(1, 0, 3, 2)) > 0.1
+    cfg = O.Config(D=3, r=2, sweeps=10)
+    ctx = _ctx(3, 2)
+    ctx.set_state(A, B)
+    Ao, Bo = A.copy(), B.copy()
+    for b in range(4):
+        RA, RB = ctx.apply_gate(b, gates[b])
+        g, diag = ctx.env_metric(b)
+        res = ctx.als_truncate(b)
+        Ao, Bo, info = O.update_bond(Ao, Bo, b, gates[b], cfg, keep=True)
+        assert _rel(RA @ RB.T, info.RA @ info.RB.T) < 1e-12, b
+        assert _rel(g, info.g) < 1e-10, b
+        assert abs(res["delta"] - info.delta) < 1e-8, b
+        A2, B2 = ctx.get_state()
+        assert _rel(A2, Ao) < 1e-9 and _rel(B2, Bo) < 1e-9, b
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_step_site_asymmetric_gates_matches_oracle(precision):
+    """One Trotter step (ntu_step) with four different site-asymmetric bond
+    gates and a random single-site unitary, D=4: per-bond delta and the final
+    state against the oracle's step (FP64 context: state 1e-9, delta 1e-8;
+    split-BF16 context: delta 1e-2 relative, the contracted A-B pair on
+    every bond 1e-4)."""
+    D = 4
+    A, B = I.random_pair(4, 2, D)
+    rng = np.random.default_rng(44)
+    gates = [I.random_gate(rng) for _ in range(4)]
+    u1 = _random_unitary(rng, 2)
+    kmax = 15 if precision == 0 else 8
+    cfg = O.Config(D=D, r=2, sweeps=10, tau_exponents=tuple(range(4, kmax + 1)))
+    ctx = _ctx(D, 2, precision=precision, kmax=kmax)
+    ctx.set_state(A, B)
+    deltas = ctx.step(gates, u1)
+    Ao, Bo, dref = O.ntu_step(A, B, gates, u1, cfg)
+    A2, B2 = ctx.get_state()
+    if precision == 0:
+        assert np.max(np.abs(deltas - np.array(dref))) < 1e-8
+        assert _rel(A2, Ao) < 1e-9 and _rel(B2, Bo) < 1e-9
+    else:
+        assert np.all(np.abs(deltas - np.array(dref)) <= 1e-2 * np.array(dref))
+        for la, lb in ((3, 1), (2, 4), (1, 3), (4, 2)):
+            pg = np.tensordot(A2, B2, axes=([la], [lb]))
+            pr = np.tensordot(Ao, Bo, axes=([la], [lb]))
+            assert _rel(pg, pr) < 1e-4
+
+
+def _random_unitary(rng, n):
+    m = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    q, r = np.linalg.qr(m)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_unit_cell_bond_legs_closed_form(precision):
+    """Closed form, no oracle: from a D=1 product state zero-padded to D=2,
+    the gate exp(-i t Z_A X_B) on bond b gives a state of bond rank 2, so the
+    update is exact.  After each bond's update through the unit-cell calls,
+    A' and B' carry the new bond only on the legs of bond b (A's leg b in
+    the order r, u, l, dn; B's opposite leg) and contract to the exact
+    two-site state with Z on A and X on B."""
+    t = 0.3
+    Z, X = I.pauli("Z"), I.pauli("X")
+    G = I.two_site(np.cos(t) * np.eye(4) - 1j * np.sin(t) * np.kron(Z, X))
+    psiA = np.array([0.6, 0.8], dtype=np.complex128)
+    psiB = np.array([0.8, -0.6j], dtype=np.complex128)
+    exact = (np.cos(t) * np.outer(psiA, psiB)
+             - 1j * np.sin(t) * np.outer(Z @ psiA, X @ psiB)).reshape(-1)
+    legs = {0: (3, 1), 1: (2, 4), 2: (1, 3), 3: (4, 2)}
+    ctx = _ctx(2, 2, sweeps=4, precision=precision, kmax=15 if precision == 0 else 8)
+    for b in range(4):
+        ctx.set_state(I.product_state(psiA, 2), I.product_state(psiB, 2))
+        ctx.apply_gate(b, G)
+        ctx.env_metric(b)
+        ctx.als_truncate(b)
+        A2, B2 = ctx.get_state()
+        la, lb = legs[b]
+        for T, leg in ((A2, la), (B2, lb)):
+            rest = np.moveaxis(T, leg, 1)[:, :, :, :, :].copy()
+            rest[:, :, 0, 0, 0] = 0
+            assert np.abs(rest).max() <= (1e-12 if precision == 0 else 1e-5) * np.abs(T).max(), \
+                (b, leg)
+        a = np.moveaxis(A2, la, -1)[:, 0, 0, 0, :]
+        bb = np.moveaxis(B2, lb, -1)[:, 0, 0, 0, :]
+        pair = (a @ bb.T).reshape(-1)
+        ov = abs(np.vdot(pair, exact)) / (np.linalg.norm(pair) * np.linalg.norm(exact))
+        assert abs(ov - 1) < (1e-13 if precision == 0 else 1e-8), (b, ov)   # ov = 1 - O(err^2)
+
+
 def test_unit_cell_call_order_is_enforced():
     from paper_2107_06635_gb300.ntu import NTUError
     ctx = _ctx(2, 2)
