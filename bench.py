@@ -35,11 +35,17 @@ from paper_2107_06635_gb300 import inputs as I  # noqa: E402
 METRIC = "NTU bond updates/s"
 FP64_PEAK = 1.25e12          # nominal GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
 FP32_SIMT_PEAK = 152 * 128 * 2 * 2.07e9   # nominal FP32 FMA pipes
-# The mixed contexts build the ALS reduced metric in double-FP32 arithmetic:
-# one complex multiply-add (8 flops of the FP64 algorithm) costs 48 FP32
-# lane operations, so that part of the work peaks at the FP32 lane rate x 8/48.
-DF_OPS_PER_CMAC = 48
-DF_PEAK = 152 * 128 * 2.07e9 * 8 / DF_OPS_PER_CMAC
+# What each precision computes in which arithmetic (the mixed contexts keep
+# FP64 for the solves, SVDs and eigendecompositions; the ALS reduced
+# metrics, g x0, the final error and the QR's Gram products are double-FP32
+# pairs, about 2^-48 relative).
+DTYPE_BF16X3 = "split-bf16 env (fp32 acc) + double-fp32 ALS metric build + c128 solves"
+DTYPE_FP32 = "c64 env + double-fp32 ALS metric build + c128 solves"
+PRECISION_BF16X3 = ("mixed: split-BF16 tcgen05 environment with FP32 accumulation; "
+                    "CholeskyQR2, ALS reduced metrics, g x0 and final error in double-FP32 "
+                    "(~2^-48); FP64 solves, SVDs and eigendecompositions")
+PRECISION_FP32 = ("mixed: FP32 environment; CholeskyQR2, ALS reduced metrics, g x0 and final "
+                  "error in double-FP32 (~2^-48); FP64 solves, SVDs and eigendecompositions")
 
 
 def measured_peaks():
@@ -58,35 +64,33 @@ def env_flops(D, r, d_p=2):
     return 8.0 * mac
 
 
-def als_flops_parts(D, r, sweeps):
-    """Algorithmic real flops of the ALS stage of one bond update (Fig. 5),
-    as (reduced-metric builds, rest): per half sweep the Hermitian reduced
-    metric g_A, K^4 D + K^3 D^2 complex multiply-adds of which the lower
-    triangle needs half, and the residual J - g_A m of the solve (one
-    n_A x n_A product, n_A = K D); plus g x0 and the final error (8 n_g^2
-    each).  The K x D SVDs of the tilts are not counted."""
-    K = D * r
-    nA, ng = K * D, K * K
-    build = sweeps * 2 * 8.0 * (K ** 4 * D + K ** 3 * D * D) / 2
-    rest = sweeps * 2 * 8.0 * nA * nA + 2 * 8.0 * ng * ng
-    return build, rest
-
-
 def als_flops(D, r, sweeps):
-    return sum(als_flops_parts(D, r, sweeps))
+    """Algorithmic real flops of the ALS stage of one bond update (Fig. 5):
+    per sweep the two reduced problems, 2 (K^4 D + K^3 D^2) complex
+    multiply-adds (g_A = (1 x M_B)^H g (1 x M_B) and its source, then the
+    same for M_B), times 8.  The eigendecompositions of the full count (one
+    of g, two of g_A per sweep) are not credited: the certified solves that
+    the measured workload takes (Gershgorin discs + conjugate gradients)
+    perform none."""
+    K = D * r
+    return sweeps * 2 * 8.0 * (K ** 4 * D + K ** 3 * D * D)
 
 
-def als_peak(precision, D, r, sweeps):
-    """Peak of k_als for its own mix of pipes: FP64 throughout on the FP64
-    context; on the mixed contexts the builds at DF_PEAK and the rest at the
-    FP64 peak, i.e. the time a kernel needs that runs every part at its
-    pipe's peak, converted back to a rate."""
+def als_peak(precision, gemm_peaks):
+    """Measured ceiling of the pipe the ALS contraction runs on: on the mixed
+    contexts the reduced metrics are built in double-FP32 arithmetic on the
+    FP32 lanes, so the in-run FP32 GEMM rate (cuBLAS SGEMM, no TF32); on the
+    FP64 context the in-run FP64 GEMM rate.  Nominal unit-count peaks when no
+    measurement is available."""
     if precision == "fp64":
+        if "fp64_tflops" in gemm_peaks:
+            return gemm_peaks["fp64_tflops"] * 1e12, "measured fp64 GEMM (cuBLAS DGEMM, this run)"
         return FP64_PEAK, "nominal FP64 (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)"
-    build, rest = als_flops_parts(D, r, sweeps)
-    t = build / DF_PEAK + rest / FP64_PEAK
-    return (build + rest) / t, ("pipe-weighted: reduced-metric builds at the double-FP32 rate "
-                                "(FP32 lanes 152x128x2.07 GHz x 8/48), the rest at nominal FP64")
+    if "fp32_tflops" in gemm_peaks:
+        return gemm_peaks["fp32_tflops"] * 1e12, ("measured fp32 GEMM (cuBLAS SGEMM, no TF32, "
+                                                   "this run): the build runs in double-FP32 "
+                                                   "on the FP32 lanes")
+    return FP32_SIMT_PEAK, "nominal FP32 lanes (152 x 128 x 2 x 2.07 GHz)"
 
 
 def als_traffic(precision, D, r, sweeps, items):
@@ -233,34 +237,58 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ oracle leg
-def _oracle_rate(D, r, sweeps, seconds, seed, max_items=64):
-    """Bond updates/s of the CPU oracle on the first items of the workload,
-    run in a fresh child process with all host cores available to BLAS."""
+def _oracle_rate(D, r, sweeps, seconds, seed, max_items=64, threads=None, keep=(),
+                 batch=None, tau_kmax=15):
+    """Bond updates/s of the CPU oracle on items of the workload, run in a
+    fresh child process with `threads` BLAS threads (default: every host
+    core).  The items in `keep` (indices into the workload's batch of
+    `batch` items) run first and their results -- delta, eps0, the repaired
+    metric g, A' and B' -- come back for the accuracy check; the rest are
+    the first items of the batch.  Returns (rate, n, seconds, threads,
+    kept results)."""
     cores = len(os.sched_getaffinity(0))
+    threads = threads or cores
+    batch = batch or max_items
+    fd, out_path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 from oracle import ntu_oracle as O
 from paper_2107_06635_gb300 import inputs as I
-cfg = O.Config(D={D}, r={r}, sweeps={sweeps})
-Ta, Tb, G = I.batch_items({seed}, {max_items}, 2, {D}, I.zz_gate(0.01))
-O.bond_update(Ta[0], Tb[0], G[0], cfg)          # warm-up (BLAS threads, caches)
+cfg = O.Config(D={D}, r={r}, sweeps={sweeps}, tau_exponents=tuple(range(4, {tau_kmax} + 1)))
+keep = {list(keep)!r}
+Ta, Tb, G = I.batch_items({seed}, {batch}, 2, {D}, I.zz_gate(0.01))
+order = keep + [i for i in range({max_items}) if i not in keep]
+O.bond_update(Ta[order[0]], Tb[order[0]], G[order[0]], cfg)     # warm-up (BLAS, caches)
+res = {{}}
 t0 = time.perf_counter(); n = 0
-while n < {max_items} and (n < 2 or time.perf_counter() - t0 < {seconds}):
-    O.bond_update(Ta[n], Tb[n], G[n], cfg); n += 1
+while n < len(order) and (n < max(2, len(keep)) or time.perf_counter() - t0 < {seconds}):
+    i = order[n]
+    A2, B2, info = O.bond_update(Ta[i], Tb[i], G[i], cfg, keep=i in keep)
+    if i in keep:
+        res[f"g{{i}}"] = info.g; res[f"A{{i}}"] = A2; res[f"B{{i}}"] = B2
+        res[f"d{{i}}"] = np.array([info.delta, info.eps0])
+        res[f"x{{i}}"] = np.array([O.measure(A2, B2, 0, I.pauli("X"), 1).real])
+    n += 1
 dt = time.perf_counter() - t0
+np.savez({out_path!r}, **res)
 print(json.dumps({{"n": n, "seconds": dt}}))
 """
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = str(cores)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=600)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    res = json.loads(out.stdout.strip().splitlines()[-1])
-    return res["n"] / res["seconds"], res["n"], res["seconds"], cores
+        env[k] = str(threads)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                             env=env, timeout=900)
+        if out.returncode != 0:
+            raise RuntimeError(out.stderr[-2000:])
+        res = json.loads(out.stdout.strip().splitlines()[-1])
+        kept = dict(np.load(out_path)) if keep else {}
+    finally:
+        os.unlink(out_path)
+    return res["n"] / res["seconds"], res["n"], res["seconds"], threads, kept
 
 
 def _oracle_rate_uneven(sweeps, seconds, seed, n_items):
@@ -304,7 +332,8 @@ def run_reference(args):
         if uneven:
             rate, n, sec, cores = _oracle_rate_uneven(args.sweeps, args.ref_seconds, 5 + i, 8)
         else:
-            rate, n, sec, cores = _oracle_rate(D, r, sweeps, args.ref_seconds, 5 + i, max_items=8)
+            rate, n, sec, cores, _ = _oracle_rate(D, r, sweeps, args.ref_seconds, 5 + i,
+                                                  max_items=args.ref_items)
         if i >= args.warmup:
             times.append(sec)
             items += n
@@ -314,8 +343,12 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": (uneven_config(args, "fp64 oracle (CPU)") if uneven
-                   else workload_config(args, "fp64 oracle (CPU)")),
+        "config": {**(uneven_config(args, "fp64 oracle (CPU)") if uneven
+                       else workload_config(args, "fp64 oracle (CPU)")),
+                   "reference_sample": f"each step times the oracle on a bounded sample of the "
+                                       f"workload: {items // max(1, args.steps)} items on "
+                                       f"average (at most {args.ref_items} per step, "
+                                       f"{args.ref_seconds:g} s), not the whole batch"},
         "cpu_baseline": {"value": value, "unit": "bond updates/s", "cores": cores,
                          "kind": "oracle",
                          "sample": (f"{items} bond updates of the uneven workload" if uneven else
@@ -452,8 +485,7 @@ def run_uneven(args):
         "metric": METRIC, "value": value, "unit": "bond updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16x3": "split-bf16 env (fp32 acc) + c128 solvers",
-                  "fp32": "c64 env + c128 solvers", "fp64": "c128"}[args.precision],
+        "dtype": {"bf16x3": DTYPE_BF16X3, "fp32": DTYPE_FP32, "fp64": "c128"}[args.precision],
         "data": "synthetic",
         "config": uneven_config(args, args.precision),
         "kinds": {f"D{k[0]}r{k[1]}": c for k, c in zip(kinds, caps)},
@@ -568,6 +600,8 @@ def run_ours(args):
     e2e_s = max_over_ranks(statistics.mean(t_e2e))
     h2d = (Ta_h.nbytes + Tb_h.nbytes + G_h.nbytes)
     d2h = (Ta_h.nbytes + Tb_h.nbytes + B * 4 * 8)
+    sample_idx = sorted({0, B // 2, B - 1})
+    gpu_sample = gpu_sample_items(ctx, torch, ntu, Ta, Tb, G, Ta_o, Tb_o, info, sample_idx)
     ctx.close()
     del ctx
 
@@ -635,25 +669,34 @@ def run_ours(args):
 
     als_ms = float(st_mixed[3])
     achieved = B * als_flops(D, r, S) / (als_ms / 1e3)
-    als_pk, als_pk_src = als_peak(args.precision, D, r, S)
+    als_pk, als_pk_src = als_peak(args.precision, gemm_peaks)
     env_achieved = B * env_flops(D, r) / (float(st_mixed[1]) / 1e3)
-    cpu = None
+    cpu, cpu_all, accuracy = None, None, None
     if not args.no_cpu_baseline:
-        rate, n, sec, cores = _oracle_rate(D, r, S, args.cpu_seconds, 5)
-        cpu = {"value": rate, "unit": "bond updates/s", "cores": cores, "kind": "oracle",
+        # the oracle single-threaded (one bond update per core, the plan for
+        # this workload); its first items are the accuracy sample
+        kmax = 15 if args.precision == "fp64" else 8
+        rate, n, sec, th, kept = _oracle_rate(D, r, S, args.cpu_seconds, rank_seed(rank),
+                                              max_items=64, threads=1, keep=sample_idx,
+                                              batch=B, tau_kmax=kmax)
+        cpu = {"value": rate, "unit": "bond updates/s", "cores": th, "kind": "oracle",
                "sample": f"{n} of the D={D} workload's bond updates in {sec:.1f} s "
-                         f"(numpy/BLAS, {cores} threads)"}
+                         f"(numpy/BLAS, 1 thread)"}
+        rate, n, sec, th, _ = _oracle_rate(D, r, S, args.cpu_seconds / 2, rank_seed(rank),
+                                           max_items=64, tau_kmax=kmax)
+        cpu_all = {"value": rate, "unit": "bond updates/s", "cores": th, "kind": "oracle",
+                   "sample": f"{n} of the D={D} workload's bond updates in {sec:.1f} s "
+                             f"(numpy/BLAS, {th} threads)"}
+        accuracy = accuracy_vs_oracle(gpu_sample, kept, sample_idx)
     peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": "bond updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16x3": "split-bf16 env (fp32 acc) + c128 solvers",
-                  "fp32": "c64 env + c128 solvers", "fp64": "c128"}[args.precision],
+        "dtype": {"bf16x3": DTYPE_BF16X3, "fp32": DTYPE_FP32, "fp64": "c128"}[args.precision],
         "data": "synthetic",
         "config": workload_config(args, {
-            "bf16x3": "mixed: split-BF16 tcgen05 environment with FP32 accumulation, FP64 solvers",
-            "fp32": "mixed: FP32 environment, FP64 solvers",
+            "bf16x3": PRECISION_BF16X3, "fp32": PRECISION_FP32,
             "fp64": "FP64 throughout"}[args.precision]),
         "roofline": {"kernel": "k_als (ALS truncation, Fig. 5)", "bound": "alu",
                      "achieved": achieved / 1e12, "peak": als_pk / 1e12,
@@ -674,10 +717,62 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
+        "accuracy_vs_oracle": accuracy,
     }
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def gpu_sample_items(ctx, torch, ntu, Ta, Tb, G, Ta_o, Tb_o, info, idx):
+    """For the sampled items of the measured batch: the repaired metric g
+    from the stage calls (gate + QR, environment, repair) on the same
+    context, the batch's A', B' and [eps, delta, eps0, tau], and the cluster
+    estimator <sigma_x> on site A of the updated pair (all on the GPU)."""
+    n = len(idx)
+    sel = torch.tensor(idx, device="cuda")
+    ta, tb, gg = Ta[sel].contiguous(), Tb[sel].contiguous(), G[sel].contiguous()
+    m, K = ctx.d_p * ctx.D ** 3, ctx.K
+    c128 = dict(dtype=torch.complex128, device="cuda")
+    QA, QB = torch.empty((n, m, K), **c128), torch.empty((n, m, K), **c128)
+    RA, RB = torch.empty((n, K, K), **c128), torch.empty((n, K, K), **c128)
+    g = torch.empty((n, K * K, K * K), **c128)
+    diag = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ctx.batch_gate_qr_dev(n, ta, tb, gg, QA, RA, QB, RB)
+    ctx.batch_env_dev(n, ta, tb, QA, QB, g)
+    ctx.batch_repair_dev(n, g, diag)
+    ctx.sync()
+    A, Bs = Ta_o[sel].cpu().numpy(), Tb_o[sel].cpu().numpy()
+    sx = []
+    for j in range(n):
+        ctx.set_state(A[j], Bs[j])
+        sx.append(ctx.measure(0, I.pauli("X")).real)
+    return {"g": g.cpu().numpy(), "A": A, "B": Bs, "info": info[sel].cpu().numpy(),
+            "sx": np.array(sx)}
+
+
+def accuracy_vs_oracle(gpu, kept, idx):
+    """Errors of the GPU path against the FP64 oracle on the sampled items:
+    relative Frobenius error of the repaired metric g, relative error of the
+    NTU error delta, relative error of the updated two-site state A'B'
+    (contracted over the bond) and |delta <sigma_x>| of the cluster estimator
+    on the updated pair."""
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    pair = lambda a, b: np.einsum("plurn,qrvwx->plunqvwx", a, b)
+    g_err, d_err, p_err, x_err = [], [], [], []
+    for j, i in enumerate(idx):
+        g_err.append(rel(gpu["g"][j], kept[f"g{i}"]))
+        d_ref = kept[f"d{i}"][0]
+        d_err.append(abs(gpu["info"][j, 1] - d_ref) / d_ref)
+        p_err.append(rel(pair(gpu["A"][j], gpu["B"][j]), pair(kept[f"A{i}"], kept[f"B{i}"])))
+        x_err.append(abs(gpu["sx"][j] - kept[f"x{i}"][0]))
+    return {"items": idx, "g_rel_frob_max": max(g_err), "delta_rel_max": max(d_err),
+            "pair_rel_max": max(p_err), "sx_abs_max": max(x_err),
+            "tolerances": {"g_rel_frob": "1e-4 mixed / 1e-10 fp64", "delta_rel": 1e-2,
+                           "pair_rel": 1e-4}}
 
 
 def main():
@@ -697,6 +792,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
+    ap.add_argument("--ref-items", type=int, default=8,
+                    help="most items the reference arm times per step")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven"],
                     help="uniform: the D=8 batch (default); uneven: D in 3..8, r in {2, 4}")
     args = ap.parse_args()
