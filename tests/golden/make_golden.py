@@ -80,6 +80,75 @@ def purification(D, steps=100):
             "h": 2.5, "sx_A": sx, "sz_A": sz}
 
 
+def _quench_member(args):
+    """One member of a perturbed-oracle ensemble of the quench (see
+    quench_spread): <sigma_x> of sites A and B after every step."""
+    D, kind, member, steps = args
+    gates2, gate1 = I.tfim_real_time_gates(2.5, 0.01)
+    A, B = I.quench_start(D)
+    if kind == "fp64":
+        # rounding-level perturbation of the start, FP64 tolerance grid
+        rng = np.random.default_rng(1000 + member)
+        A = A + 1e-14 * I.random_site_tensor(rng, 2, D)
+        B = B + 1e-14 * I.random_site_tensor(rng, 2, D)
+        cfg = O.Config(D=D, r=2, sweeps=10)
+    else:
+        # the split-BF16 environment: every operand of the metric contraction
+        # carried to a 16-bit significand (one hi + lo pair of BF16 values),
+        # modelled as independent per-element relative errors of 2^-17; the
+        # mixed contexts' tolerance grid 1e-4..1e-8
+        rng = np.random.default_rng(5000 + member)
+        orig = O.metric_raw
+
+        def pert(x):
+            z = rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)
+            return x * (1 + 2.0 ** -17 * z / np.sqrt(2))
+
+        def noisy(Ta, Tb, QA, QB, d_p, D_):
+            return orig(pert(Ta), pert(Tb), pert(QA), pert(QB), d_p, D_)
+
+        O.metric_raw = noisy
+        cfg = O.Config(D=D, r=2, sweeps=10, tau_exponents=tuple(range(4, 9)))
+    out = []
+    try:
+        for _ in range(steps):
+            A, B, _ = O.ntu_step(A, B, gates2, gate1, cfg)
+            out.append([O.measure(A, B, 0, I.pauli("X"), 1).real,
+                        O.measure(A, B, 1, I.pauli("X"), 1).real])
+    finally:
+        if kind != "fp64":
+            O.metric_raw = orig
+    return out
+
+
+def quench_spread(D, ref, steps=200, members=(4, 8)):
+    """How far the oracle's own <sigma_x> moves from the stored quench
+    trajectory `ref` when its inputs are perturbed at the level of each GPU
+    path's arithmetic: "fp64", 1e-14 relative perturbations of the start
+    (members[0] members); "split16", the environment operands perturbed by
+    2^-17 per element at every bond update with the mixed tolerance grid
+    (members[1] members).  Returns, per kind, the member trajectories and
+    the per-step largest deviation over members and both sites."""
+    import multiprocessing as mp
+    jobs = [(D, "fp64", m, steps) for m in range(members[0])] + \
+           [(D, "split16", m, steps) for m in range(members[1])]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        res = pool.map(_quench_member, jobs)
+    center = np.array([ref["sx_A"], ref["sx_B"]]).T
+    out = {}
+    for kind, n0 in (("fp64", 0), ("split16", members[0])):
+        k = members[0] if kind == "fp64" else members[1]
+        tr = np.array(res[n0:n0 + k])
+        out[f"spread_{kind}"] = np.abs(tr - center[None]).max(axis=(0, 2)).tolist()
+        out[f"members_{kind}_first12"] = tr[:, :12].tolist()
+    out["spread_recipe"] = (
+        "fp64: start + 1e-14 x random_site_tensor(default_rng(1000 + m)), tau 1e-4..1e-15; "
+        "split16: every operand of the metric contraction (Ta, Tb, QA, QB) times "
+        "(1 + 2^-17 z / sqrt 2), z complex N(0,1) from default_rng(5000 + m), tau 1e-4..1e-8; "
+        "spread = max over members and sites of |<sigma_x> - stored trajectory|")
+    return out
+
+
 def write(name, obj):
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(obj, f, indent=1)
@@ -89,5 +158,7 @@ def write(name, obj):
 if __name__ == "__main__":
     write("one_step_d3.json", one_step_d3())
     for D in (4, 5):
-        write(f"quench_d{D}.json", quench(D))
+        q = quench(D)
+        q.update(quench_spread(D, q))
+        write(f"quench_d{D}.json", q)
     write("purification_d4.json", purification(4))

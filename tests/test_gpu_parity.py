@@ -763,18 +763,28 @@ def _golden(name):
     return json.load(open(os.path.join(os.path.dirname(__file__), "golden", name)))
 
 
-@pytest.mark.parametrize("D,precision,tol", [(4, 0, 1e-4), (4, 2, 1e-3), (5, 0, 1e-4)])
-def test_quench_full_trajectory(D, precision, tol):
-    """TFIM quench h = 2.5, dt = 0.01 to t = 2 (200 steps): <sigma_x> of both sites after every step
-    against the oracle's trajectory stored by tests/golden/make_golden.py.
-    The early steps truncate singular values of weight ~1e-15 (delta ~ 1e-15),
-    so the kept directions are chosen by rounding: a 1e-14 relative
-    perturbation of the oracle's own start moves <sigma_x> by ~1e-6 after
-    eight to fifteen steps.  Any implementation that rounds differently
-    therefore agrees only to that amplified level (observed: FP64 path
-    1.4e-5 at D=4, 2.3e-5 at D=5; split-BF16 path 1.2e-4), and the bound
-    checks that the error stays there instead of growing over the quench;
-    the first steps are held to 1e-6 by test_quench_observable_parity."""
+def _envelope(spread, w=3):
+    """Largest value of a per-step spread within +-w steps."""
+    s = np.asarray(spread)
+    return np.array([s[max(0, i - w):i + w + 1].max() for i in range(s.size)])
+
+
+@pytest.mark.parametrize("D,precision", [(4, 0), (5, 0), (4, 2), (5, 2)])
+def test_quench_full_trajectory(D, precision):
+    """TFIM quench h = 2.5, dt = 0.01 to t = 2 (200 steps, Sec. III):
+    <sigma_x> of both sites after every step against the oracle's stored
+    trajectory, bounded by the oracle's own spread when its inputs are
+    perturbed at the level of the path's arithmetic (stored beside the
+    trajectory by tests/golden/make_golden.py, largest value within +-3
+    steps).  The early steps truncate singular values of weight ~1e-15, so
+    the kept directions are chosen by rounding and any implementation that
+    rounds differently moves <sigma_x> by up to ~2e-5 around steps 7-12.
+    FP64 context: at most twice the spread of an ensemble with 1e-14
+    perturbations of the start (observed at most 0.8 of it).  Split-BF16
+    context: at most four times the spread of an ensemble whose environment
+    operands carry the split representation's 2^-17 relative error and which
+    uses the mixed tolerance grid 1e-4..1e-8 (observed at most 2.9 of it);
+    1e-6 on the steps where that spread is below 1e-7."""
     gold = _golden(f"quench_d{D}.json")
     gates2, gate1 = I.tfim_real_time_gates(gold["h"], gold["dt"])
     ctx = _ctx(D, 2, precision=precision, kmax=15 if precision == 0 else 8)
@@ -786,8 +796,42 @@ def test_quench_full_trajectory(D, precision, tol):
         err.append(max(abs(ctx.measure(0, I.pauli("X")).real - gold["sx_A"][s]),
                        abs(ctx.measure(1, I.pauli("X")).real - gold["sx_B"][s])))
     err = np.array(err)
-    assert err.max() < tol, (err.argmax(), err.max())
-    assert err[100:].max() < tol                      # no growth in the second half
+    if precision == 0:
+        bound = 2 * _envelope(gold["spread_fp64"]) + 1e-12
+    else:
+        bound = 4 * _envelope(gold["spread_split16"]) + 1e-12
+        quiet = np.array(gold["spread_split16"]) < 1e-7
+        assert quiet.any() and np.all(err[quiet] < 1e-6), err[quiet]
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, [(int(i), err[i], bound[i]) for i in bad[:5]]
+
+
+def test_fp64_context_at_the_bench_configuration():
+    """The FP64 GPU path (the denominator of the measured speedup) at the
+    bench configuration D=8, d=2, r=2, exp(-i 0.01 ZZ), 10 sweeps, seed 5:
+    the repaired metric g within 1e-10 (relative Frobenius) of the oracle's,
+    delta within 1e-8 and A', B' within 1e-9."""
+    from paper_2107_06635_gb300 import ntu
+    D, n = 8, 2
+    Ta, Tb, G = I.batch_items(5, n, 2, D, I.zz_gate(0.01))
+    ctx = ntu.Context(D, 2, 1, 2, 10, ntu.NTU_FP64, 4, 15, n)
+    m, K = 2 * D ** 3, D * 2
+    ta, tb, gg = _dev(Ta), _dev(Tb), _dev(G)
+    QA, RA, QB, RB = _empty((n, m, K)), _empty((n, K, K)), _empty((n, m, K)), _empty((n, K, K))
+    g = _empty((n, K * K, K * K))
+    diag = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ctx.batch_gate_qr_dev(n, ta, tb, gg, QA, RA, QB, RB)
+    ctx.batch_env_dev(n, ta, tb, QA, QB, g)
+    ctx.batch_repair_dev(n, g, diag)
+    ctx.sync()
+    a, b, info = ctx.batch_update_host(Ta, Tb, G)
+    cfg = O.Config(D=D, r=2, sweeps=10)
+    for i in range(n):
+        A2, B2, ref = O.bond_update(Ta[i], Tb[i], G[i], cfg, keep=True)
+        assert _rel(g[i].cpu().numpy(), ref.g) < 1e-10
+        assert abs(info[i, 1] - ref.delta) < 1e-8
+        assert _rel(a[i], A2) < 1e-9 and _rel(b[i], B2) < 1e-9
+    ctx.close()
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-4), (2, 1e-4)])
