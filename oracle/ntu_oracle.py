@@ -443,3 +443,100 @@ def measure(A, B, site: int, O: np.ndarray, d_anc: int) -> complex:
     num = _es(net, c(T), Of, T, El, Eu, Er, Ed)
     den = _es(net, c(T), np.eye(d_p), T, El, Eu, Er, Ed)
     return complex(num / den)
+
+
+# ------------------------------------------ simple update (SU), Sec. II
+# The SU keeps a diagonal bond tensor lambda_b (D positive values) on each
+# of the four inequivalent bonds; its metric is g_SU = 1_d (x) 1_d (x)
+# prod_j lambda_j over the six outer bonds of the updated pair (Sec. II).
+# Reading: the site tensors are held in the symmetric gauge, each leg
+# carrying sqrt(lambda) of its bond, so a pair contracted over its bond
+# carries lambda_b once.  With sqrt(lambda) more on each outer leg the pair
+# carries the full lambda_j there, g_SU becomes the plain Frobenius norm, and
+# its minimiser is the local SVD truncation (Fig. 2(c,d)) of the weighted
+# reduced matrices.
+SU_BONDS_A = (2, 1, 0, 3)     # bond carried by A's legs (l, u, r, dn)
+SU_BONDS_B = (0, 3, 2, 1)     # bond carried by B's legs (l, u, r, dn)
+LAMBDA_CUT = 1e-14            # lambda_i <= this x max lambda counts as zero
+
+
+def su_weight(T: np.ndarray, lam: np.ndarray, bonds, skip: int, power: float) -> np.ndarray:
+    """T with each leg j in (l, u, r, dn) multiplied by lam[bonds[j]] ** power,
+    except the leg on bond `skip`.  Negative powers are pseudo-inverses:
+    values at or below LAMBDA_CUT x max give weight 0."""
+    T = T.copy()
+    for j, b in enumerate(bonds):
+        if b == skip:
+            continue
+        lv = np.asarray(lam[b], dtype=np.float64)
+        w = np.zeros_like(lv)
+        ok = lv > LAMBDA_CUT * lv.max() if power < 0 else np.ones(lv.size, bool)
+        w[ok] = lv[ok] ** power
+        shape = [1] * 5
+        shape[j + 1] = lv.size
+        T = T * w.reshape(shape)
+    return T
+
+
+def su_bond_update(Ta: np.ndarray, Tb: np.ndarray, G: np.ndarray, cfg: Config):
+    """SU of the bond Ta.r -- Tb.l (bond-0 orientation) for tensors whose
+    outer legs already carry the full lambda: gate split, apply + QR
+    (Fig. 2(a,b)), truncated SVD of R_A R_B^T keeping D values with sqrt(S)
+    on both sides (Fig. 2(c,d)), recompose.  Returns (A', B', the kept
+    singular values s_1..s_D, delta = sum_{i>D} s_i^2 / sum_i s_i^2, the
+    error of the truncation in the metric g_SU relative to that of no
+    update)."""
+    D = cfg.D
+    GA, GB = gate_split(G, cfg.r)
+    QA, RA = qr_positive(gated_matrix(Ta, GA, cfg.d_anc, "left"))
+    QB, RB = qr_positive(gated_matrix(Tb, GB, cfg.d_anc, "right"))
+    X0 = RA @ RB.T
+    s_all = np.linalg.svd(X0, compute_uv=False)
+    U, s, Vh = svd_truncate(X0, D)
+    rs = np.sqrt(s)
+    MA, MB = U * rs, Vh.T * rs
+    tot = float(np.sum(s_all ** 2))
+    delta = float(np.sum(s_all[D:] ** 2)) / tot if tot > 0 else 0.0
+    return (recompose(QA, MA, cfg.d_p, D, "left"), recompose(QB, MB, cfg.d_p, D, "right"),
+            s, delta)
+
+
+def su_update_bond(A, B, lam, bond: int, G: np.ndarray, cfg: Config):
+    """Simple update of bond `bond` of the checkerboard cell (Sec. II), with
+    the cell's orientation rules of ``update_bond``.  The three outer legs of
+    each site are weighted by sqrt(lambda) (full lambda on the outer bonds),
+    the pair is updated by ``su_bond_update``, the outer weights are removed
+    again (pseudo-inverse), each tensor is normalised, and lambda_bond
+    becomes the kept singular values normalised to unit 2-norm.  Returns
+    (A', B', lam', delta)."""
+    Aw = su_weight(A, lam, SU_BONDS_A, bond, 0.5)
+    Bw = su_weight(B, lam, SU_BONDS_B, bond, 0.5)
+    if bond in (1, 3):
+        Aw, Bw = rotate(Aw), rotate(Bw)
+    if bond in (0, 1):
+        A2, B2, s, delta = su_bond_update(Aw, Bw, G, cfg)
+    else:
+        B2, A2, s, delta = su_bond_update(Bw, Aw, np.ascontiguousarray(G.transpose(1, 0, 3, 2)),
+                                          cfg)
+    if bond in (1, 3):
+        A2, B2 = unrotate(A2), unrotate(B2)
+    A2 = su_weight(A2, lam, SU_BONDS_A, bond, -0.5)
+    B2 = su_weight(B2, lam, SU_BONDS_B, bond, -0.5)
+    lam2 = [np.array(l, dtype=np.float64, copy=True) for l in lam]
+    lam2[bond] = s / np.linalg.norm(s)
+    return A2 / np.linalg.norm(A2), B2 / np.linalg.norm(B2), lam2, delta
+
+
+def su_step(A, B, lam, gates2, gate1, cfg: Config):
+    """One second-order Trotter step of the simple update: half single-site
+    gates, the four bonds in the order 0, 1, 2, 3, half single-site gates.
+    Returns (A, B, lam, [delta per bond])."""
+    if gate1 is not None:
+        A, B = apply_site_gate(A, gate1, cfg.d_anc), apply_site_gate(B, gate1, cfg.d_anc)
+    deltas = []
+    for b in range(4):
+        A, B, lam, d = su_update_bond(A, B, lam, b, gates2[b], cfg)
+        deltas.append(d)
+    if gate1 is not None:
+        A, B = apply_site_gate(A, gate1, cfg.d_anc), apply_site_gate(B, gate1, cfg.d_anc)
+    return A, B, lam, deltas
