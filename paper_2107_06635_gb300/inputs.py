@@ -192,3 +192,84 @@ def uneven_batch(seed: int, n: int, d_p: int = 2, theta: float = 0.01):
         g = zz_gate(theta) if r == 2 else heisenberg_gate(theta)
         items.append((D, r, ta, tb, g))
     return items
+
+
+# ------------------------------------- real Hermitian iPEPO (thermal states)
+def operator_basis():
+    """The Hermitian operator basis of one spin-1/2 site, O^a for
+    a = 0, 1, 2, 3: sigma_x, sigma_y, sigma_z, 1.  Tr(O^a O^b) = 2 delta_ab."""
+    return [_X.copy(), _Y.copy(), _Z.copy(), _I2.copy()]
+
+
+def superoperator_two_site(G: np.ndarray) -> np.ndarray:
+    """The real tensor S[a', b', a, b] with
+    G (O^a (x) O^b) G^dag = sum_{a'b'} S[a', b', a, b] O^a' (x) O^b',
+    i.e. S = Tr((O^a' (x) O^b') G (O^a (x) O^b) G^dag) / 4 (orthogonality of
+    the basis).  G is a 4 x 4 operator on (sA, sB); S is returned in the
+    two-site gate layout [sA', sB', sA, sB] with d = 4."""
+    Ob = operator_basis()
+    S = np.zeros((4, 4, 4, 4))
+    for a in range(4):
+        for b in range(4):
+            M = G @ np.kron(Ob[a], Ob[b]) @ G.conj().T
+            for a2 in range(4):
+                for b2 in range(4):
+                    S[a2, b2, a, b] = np.real(np.trace(np.kron(Ob[a2], Ob[b2]) @ M)) / 4.0
+    return S.astype(np.complex128)
+
+
+def superoperator_one_site(U: np.ndarray) -> np.ndarray:
+    """s[a', a] = Tr(O^a' U O^a U^dag) / 2: the action O -> U O U^dag on the
+    coefficients of one site."""
+    Ob = operator_basis()
+    s = np.zeros((4, 4))
+    for a in range(4):
+        M = U @ Ob[a] @ U.conj().T
+        for a2 in range(4):
+            s[a2, a] = np.real(np.trace(Ob[a2] @ M)) / 2.0
+    return s.astype(np.complex128)
+
+
+def ipepo_thermal_gates(h: float, dbeta: float):
+    """Second-order Trotter gates of rho(beta/2) -> e^{-dbeta H/4} rho e^{-dbeta H/4}
+    for H = -sum ZZ - h sum X, acting on the coefficients of the real
+    iPEPO: four bond gates, the superoperator of G = 1 + tanh(dbeta/4) Z(x)Z
+    (proportional to e^{dbeta ZZ/4}), and the single-site half step, the
+    superoperator of e^{h dbeta X/8}."""
+    G = np.eye(4) + np.tanh(dbeta / 4) * np.kron(_Z, _Z)
+    S2 = superoperator_two_site(G)
+    s1 = superoperator_one_site(x_rotation_imag(h * dbeta / 8))
+    return [S2.copy() for _ in range(4)], s1
+
+
+def ipepo_identity(D: int) -> np.ndarray:
+    """rho(0) = 1 at every site (coefficients (0, 0, 0, 1)), zero-padded to
+    bond dimension D."""
+    return product_state(np.array([0.0, 0.0, 0.0, 1.0]), D)
+
+
+def ipepo_observable(O: np.ndarray) -> np.ndarray:
+    """The 4 x 4 matrix M[a', a] = Tr(O^a' O O^a) / 2 that, put on one site of
+    the coefficient network, turns its norm sum_a c_a^2 (= Tr(rho^2) / 2 per
+    site) into Tr(rho O rho) / 2: with it the cluster estimator of a real
+    iPEPO rho(beta/2) gives <O> = Tr(rho(beta) O) / Tr rho(beta), since
+    rho(beta) = rho(beta/2)^2."""
+    Ob = operator_basis()
+    M = np.zeros((4, 4), dtype=np.complex128)
+    for a2 in range(4):
+        for a in range(4):
+            M[a2, a] = np.trace(Ob[a2] @ O @ Ob[a]) / 2.0
+    return M
+
+
+def ipepo_start(D: int, mix: float = 1e-2, seed: int = 88):
+    """Initial (A, B) of a thermal iPEPO run: rho(0) = 1 zero-padded to D plus
+    a seeded real random admixture of relative weight `mix` (which lifts the
+    exact zero modes of the padded bonds), each normalised; real."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(2):
+        t = rng.standard_normal((4, D, D, D, D))
+        t = ipepo_identity(D) + mix * t / np.linalg.norm(t)
+        out.append(np.ascontiguousarray(t / np.linalg.norm(t)))
+    return out[0], out[1]
