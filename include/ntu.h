@@ -149,6 +149,35 @@ int ntu_step(ntu_ctx* ctx, const double* gates2, const double* gate1_half,
  * one complex. */
 int ntu_measure(ntu_ctx* ctx, int site, const double* op, double* value_out);
 
+/* ---- simple update of the cell (Sec. II) ------------------------------- */
+/* The simple update (SU) keeps a diagonal bond tensor lambda_b (D
+ * non-negative values) on each of the cell's four bonds and uses the metric
+ * g_SU = 1_d (x) 1_d (x) prod_j lambda_j over the six outer bonds of the
+ * updated pair (Sec. II), whose minimiser is a truncated SVD (cost ~D^5, no
+ * environment contraction).  Convention: the state tensors A, B set by
+ * ntu_set_state are in the symmetric gauge, each leg carrying sqrt(lambda)
+ * of its bond.  ntu_init sets every lambda to 1; ntu_set_state leaves the
+ * lambdas alone.
+ * ntu_su_set_lambdas / ntu_su_get_lambdas: lam is 4 x D doubles, row b =
+ *   lambda of bond b (finite, >= 0; else NTU_EINVAL).
+ * ntu_su_update: one SU bond update of `bond` with `gate` (d_phys^4
+ *   complex): the outer legs of both sites are weighted by sqrt(lambda),
+ *   gate + QR (Fig. 2(a,b)), truncation of R_A R_B^T to its D largest
+ *   singular values with sqrt(S) on both sides (Fig. 2(c,d)), recompose,
+ *   the outer weights removed again (values at or below 1e-14 x the bond's
+ *   largest give 0), each tensor normalised; lambda_bond becomes the kept
+ *   singular values normalised to unit 2-norm.  delta_out (may be NULL):
+ *   the discarded weight sum_{i>D} s_i^2 / sum_i s_i^2, the relative error
+ *   in the metric g_SU.
+ * ntu_su_step: the second-order Trotter step of ntu_step with SU bond
+ *   updates (gates2 4 x d_phys^4, gate1_half d_phys x d_phys or NULL);
+ *   delta_out 4 doubles or NULL. */
+int ntu_su_set_lambdas(ntu_ctx* ctx, const double* lam);
+int ntu_su_get_lambdas(ntu_ctx* ctx, double* lam);
+int ntu_su_update(ntu_ctx* ctx, int bond, const double* gate, double* delta_out);
+int ntu_su_step(ntu_ctx* ctx, const double* gates2, const double* gate1_half,
+                double* delta_out);
+
 /* ---- batches of independent bond updates (device pointers) ------------- */
 /* Item i is the bond Ta[i].r - Tb[i].l (bond-0 orientation) of its own
  * two-site cell with gate gates[i].  All arrays are contiguous stacks of n
@@ -254,6 +283,46 @@ int ntu_batch_recompose_dev(ntu_ctx* ctx, int n, const double* QA, const double*
  * others return NTU_EUNSUPPORTED.  No wait is unbounded, nothing faults, and
  * the context stays usable. */
 int ntu_inject_wait_timeout(ntu_ctx* ctx, int on);
+
+/* ---- launch tuning ------------------------------------------------------
+ * Schedule choices of a context's kernels that change speed, never results
+ * (every combination gives the same numbers bit for bit).  Fields:
+ *   t12_pair        -1: automatic (pair at D = 8); 0: the fused t1 -> t2
+ *                   kernel runs one (k, k') unit per GEMM2; 1: pairs of units
+ *                   (k, k'), (k, k'+1) share one N = 128 GEMM2 (D = 8 only);
+ *   als_ctas_per_sm 0: automatic (3 when a batch has more than 2 x SMs items,
+ *                   else 2); 2 or 3: the ALS kernel's register budget for
+ *                   that many CTAs per SM;
+ *   als_split       0: automatic (the split chosen at ntu_init, reduced
+ *                   while items x split exceeds 3 x SMs); 1, 2 or 4 CTAs per
+ *                   item's ALS, at most the split ntu_init allocated for
+ *                   (mixed contexts only; FP64 contexts take 0 or 1).
+ * ntu_set_tuning rejects out-of-range values with NTU_EINVAL and drops the
+ * CUDA graphs the context captured.  ntu_get_tuning reads the settings and,
+ * in split_max, the largest als_split this context accepts.
+ * ntu_uneven_set_tuning / ntu_uneven_get_tuning do the same for one kind
+ * (index into the kinds of ntu_uneven_init) of an uneven batch; setting
+ * drops the uneven's captured graphs. */
+typedef struct {
+  int t12_pair;
+  int als_ctas_per_sm;
+  int als_split;
+} ntu_tuning;
+int ntu_set_tuning(ntu_ctx* ctx, const ntu_tuning* t);
+int ntu_get_tuning(const ntu_ctx* ctx, ntu_tuning* t, int* split_max);
+int ntu_uneven_set_tuning(ntu_uneven* uneven, int kind, const ntu_tuning* t);
+int ntu_uneven_get_tuning(const ntu_uneven* uneven, int kind, ntu_tuning* t, int* split_max);
+
+/* CUDA graphs of the unit-cell step.  With graphs on (the default), the
+ * device work of ntu_step and ntu_su_step -- the single-site gates and the
+ * four bond updates, some 90 launches -- is captured as one CUDA graph on
+ * the first call (one graph per call form: with or without gate1_half) and
+ * replayed by later calls; the gates are copied in before the replay and
+ * the deltas read back after it.  Off: the same launches are issued one by
+ * one.  Results are identical.  Capture needs the context's own or a
+ * non-legacy stream; where capture fails the call runs the launches
+ * directly. */
+int ntu_set_graphs(ntu_ctx* ctx, int on);
 
 /* Number of kernel launches the last ntu_batch_update_* call queued. */
 int ntu_last_launch_count(const ntu_ctx* ctx);

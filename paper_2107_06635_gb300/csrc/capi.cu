@@ -2,6 +2,7 @@
 // management, argument validation, and the host-side sequencing of the
 // kernels of one bond update.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -162,6 +163,7 @@ void carve(ntu_ctx* c, Carver& cv) {
   W.mscr2 = cv.take<double2>(P.szT);
   W.medge = cv.take<double2>(4 * (size_t)P.D * P.D);
   W.mval = cv.take<double2>(2);
+  W.lam = cv.take<double>(4 * (size_t)P.D);
 }
 }  // namespace
 
@@ -216,6 +218,8 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
   if (!c) return fail(nullptr, NTU_ENOMEM, "host allocation");
   memset(c, 0, sizeof(*c));
   c->cfg = f;
+  c->tune.t12_pair = -1;
+  c->use_graphs = 1;
   c->wait_polls = f.wait_budget > 0 ? (long long)f.wait_budget : (1ll << 23);
   c->env_es = f.precision == NTU_FP64 ? sizeof(double2) : sizeof(float2);
   if (stream) { c->stream = (cudaStream_t)stream; c->own_stream = false; }
@@ -274,6 +278,11 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
   const char* dbg = getenv("NTU_DEBUG_SYNC");
   c->debug_sync = (dbg && dbg[0] == '1') ? 1 : 0;
   cudaMemset(base, 0, dry.off);
+  {
+    double ones[32];
+    for (int i = 0; i < 32; ++i) ones[i] = 1.0;
+    cudaMemcpy(c->w.lam, ones, 4 * sizeof(double) * f.D, cudaMemcpyHostToDevice);
+  }
   if (f.precision == NTU_MIXED_BF16X3) {
     int prop = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -297,9 +306,17 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
   return NTU_OK;
 }
 
+void ntu::drop_step_graphs(ntu_ctx* c) {
+  for (int i = 0; i < 4; ++i) {
+    if (c->step_graph[i]) cudaGraphExecDestroy(c->step_graph[i]);
+    c->step_graph[i] = nullptr;
+  }
+}
+
 extern "C" int ntu_destroy(ntu_ctx* c) {
   if (!c) return NTU_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_step_graphs(c);
   if (c->w.GA) cudaFree(c->w.GA);
   if (c->d_status) cudaFree(c->d_status);
   for (int i = 0; i < 6; ++i)
@@ -319,11 +336,44 @@ extern "C" int ntu_sync(ntu_ctx* c) {
 
 extern "C" int ntu_last_launch_count(const ntu_ctx* c) { return c ? c->launches : 0; }
 
+extern "C" int ntu_set_tuning(ntu_ctx* c, const ntu_tuning* t) {
+  if (!c || !t) return fail(c, NTU_EINVAL, "ntu_set_tuning: NULL argument");
+  if (t->t12_pair < -1 || t->t12_pair > 1)
+    return fail(c, NTU_EINVAL, "t12_pair=%d outside -1..1", t->t12_pair);
+  if (t->t12_pair == 1 && (c->cfg.D != 8 || c->cfg.precision != NTU_MIXED_BF16X3))
+    return fail(c, NTU_EINVAL, "t12_pair=1 needs D=8 on a split-BF16 context");
+  if (t->als_ctas_per_sm != 0 && t->als_ctas_per_sm != 2 && t->als_ctas_per_sm != 3)
+    return fail(c, NTU_EINVAL, "als_ctas_per_sm=%d: 0, 2 or 3", t->als_ctas_per_sm);
+  if (t->als_split != 0 && t->als_split != 1 && t->als_split != 2 && t->als_split != 4)
+    return fail(c, NTU_EINVAL, "als_split=%d: 0, 1, 2 or 4", t->als_split);
+  if (t->als_split > c->w.als_split)
+    return fail(c, NTU_EINVAL, "als_split=%d exceeds the %d this context allocated for",
+                t->als_split, c->w.als_split);
+  c->tune = *t;
+  drop_step_graphs(c);
+  return NTU_OK;
+}
+
+extern "C" int ntu_get_tuning(const ntu_ctx* c, ntu_tuning* t, int* split_max) {
+  if (!c || !t) return fail(const_cast<ntu_ctx*>(c), NTU_EINVAL, "ntu_get_tuning: NULL argument");
+  *t = c->tune;
+  if (split_max) *split_max = c->w.als_split;
+  return NTU_OK;
+}
+
+extern "C" int ntu_set_graphs(ntu_ctx* c, int on) {
+  if (!c) return fail(c, NTU_EINVAL, "NULL context");
+  c->use_graphs = on ? 1 : 0;
+  if (!on) drop_step_graphs(c);
+  return NTU_OK;
+}
+
 extern "C" int ntu_inject_wait_timeout(ntu_ctx* c, int on) {
   if (!c) return fail(c, NTU_EINVAL, "NULL context");
   if (c->w.als_split < 2)
     return fail(c, NTU_EUNSUPPORTED, "this context's ALS runs one CTA per item: no rendezvous");
   c->inject_timeout = on ? 1 : 0;
+  drop_step_graphs(c);
   return NTU_OK;
 }
 
@@ -433,6 +483,63 @@ extern "C" int ntu_als_truncate(ntu_ctx* c, int bond, double* eps_out, double* d
   return NTU_OK;
 }
 
+static int su_bond(ntu_ctx* c, int bond, const double2* gate_dev, double* info_dev);
+
+// The device work of one unit-cell Trotter step (NTU or SU bond updates),
+// reading the gates from W.cG / W.op and writing the deltas to info_dev.
+static int step_body(ntu_ctx* c, bool su, bool gate1, double* info_dev) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  const size_t d4 = (size_t)P.d * P.d * P.d * P.d;
+  if (gate1) CK(launch_site_gate(c, W.A, W.B, W.op), "site gate");
+  for (int b = 0; b < 4; ++b) {
+    int st;
+    if (su) {
+      st = su_bond(c, b, W.cG + b * d4, info_dev + 4 * b);
+    } else {
+      st = cell_gate_qr(c, b, W.cG + b * d4);
+      if (!st) st = cell_env(c);
+      if (!st) st = cell_als(c, b, info_dev + 4 * b);
+    }
+    if (st) return st;
+  }
+  if (gate1) CK(launch_site_gate(c, W.A, W.B, W.op), "site gate");
+  return NTU_OK;
+}
+
+// Runs step_body, through a CUDA graph captured on first use when graphs
+// are on (one per form); falls back to direct launches where capture fails.
+static int run_step(ntu_ctx* c, bool su, bool gate1, double* info_dev) {
+  const int slot = (su ? 2 : 0) + (gate1 ? 1 : 0);
+  if (c->use_graphs && !c->debug_sync && c->stream) {
+    if (!c->step_graph[slot]) {
+      cudaGraph_t g = nullptr;
+      const int before = c->launches;
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        int st = step_body(c, su, gate1, info_dev);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (st == NTU_OK && e == cudaSuccess && g) {
+          cudaGraphExec_t x = nullptr;
+          if (cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+            c->step_graph[slot] = x;
+            c->step_graph_launches[slot] = c->launches - before;
+          }
+        }
+        if (g) cudaGraphDestroy(g);
+        if (st != NTU_OK) return st;
+      }
+      cudaGetLastError();          // a refused capture leaves no sticky error
+      c->launches = before;
+    }
+    if (c->step_graph[slot]) {
+      CK(cudaGraphLaunch(c->step_graph[slot], c->stream), "graph launch");
+      c->launches += c->step_graph_launches[slot];
+      return NTU_OK;
+    }
+  }
+  return step_body(c, su, gate1, info_dev);
+}
+
 extern "C" int ntu_step(ntu_ctx* c, const double* gates2, const double* gate1_half,
                         double* delta_out) {
   if (!c || !gates2) return fail(c, NTU_EINVAL, "ntu_step: NULL argument");
@@ -441,19 +548,13 @@ extern "C" int ntu_step(ntu_ctx* c, const double* gates2, const double* gate1_ha
   size_t d4 = (size_t)P.d * P.d * P.d * P.d, d2 = (size_t)P.d * P.d;
   CK(cudaMemcpyAsync(W.cG, gates2, 4 * d4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
      "copy gates");
-  if (gate1_half) {
+  if (gate1_half)
     CK(cudaMemcpyAsync(W.op, gate1_half, d2 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
        "copy gate1");
-    CK(launch_site_gate(c, W.A, W.B, W.op), "site gate");
-  }
   double* info_dev = W.info + 4 * (size_t)W.cap;
-  for (int b = 0; b < 4; ++b) {
-    int st = cell_gate_qr(c, b, W.cG + b * d4);
-    if (!st) st = cell_env(c);
-    if (!st) st = cell_als(c, b, info_dev + 4 * b);
-    if (st) return st;
-  }
-  if (gate1_half) CK(launch_site_gate(c, W.A, W.B, W.op), "site gate");
+  c->launches = 0;
+  int st0 = run_step(c, false, gate1_half != nullptr, info_dev);
+  if (st0) return st0;
   double info[16];
   CK(cudaMemcpyAsync(info, info_dev, sizeof(info), cudaMemcpyDeviceToHost, c->stream), "copy info");
   int st = check_status(c);
@@ -476,6 +577,88 @@ extern "C" int ntu_measure(ntu_ctx* c, int site, const double* op, double* value
   CK(cudaMemcpyAsync(value_out, W.mval, sizeof(double2), cudaMemcpyDeviceToHost, c->stream),
      "copy value");
   return check_status(c);
+}
+
+// ------------------------------------------------ simple update (Sec. II)
+extern "C" int ntu_su_set_lambdas(ntu_ctx* c, const double* lam) {
+  if (!c || !lam) return fail(c, NTU_EINVAL, "ntu_su_set_lambdas: NULL argument");
+  const int D = c->cfg.D;
+  for (int i = 0; i < 4 * D; ++i)
+    if (!(lam[i] >= 0.0) || !(lam[i] < INFINITY))
+      return fail(c, NTU_EINVAL, "lambda[%d][%d] = %g is not a finite non-negative value", i / D,
+                  i % D, lam[i]);
+  CK(cudaMemcpyAsync(c->w.lam, lam, 4 * D * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+     "copy lambdas");
+  return check_status(c);
+}
+
+extern "C" int ntu_su_get_lambdas(ntu_ctx* c, double* lam) {
+  if (!c || !lam) return fail(c, NTU_EINVAL, "ntu_su_get_lambdas: NULL argument");
+  CK(cudaMemcpyAsync(lam, c->w.lam, 4 * c->cfg.D * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream), "copy lambdas");
+  return check_status(c);
+}
+
+// One SU bond update of the cell's state on the device (no synchronisation):
+// weight the outer legs, orient, gate + QR, identity-metric truncation with
+// zero sweeps, recompose, write back, unweight, new lambda_bond.
+static int su_bond(ntu_ctx* c, int bond, const double2* gate_dev, double* info_dev) {
+  Work& W = c->w;
+  CK(launch_su_weight(c, bond, 0, 0, W.A, W.B, W.cA2, W.cB2), "SU weight");
+  CK(launch_orient(c, bond, W.cA2, W.cB2, W.cTa, W.cTb), "orient");
+  CK(launch_gate_qr(c, 1, W.cTa, W.cTb, gate_dev, bond >= 2 ? 1 : 0, W.QA, W.RA, W.QB, W.RB),
+     "gate + QR");
+  CK(launch_identity_metric(c, W.g), "identity metric");
+  CK(launch_als(c, 1, W.g, W.RA, W.RB, W.MA, W.MB, info_dev, 0), "SU truncation");
+  CK(launch_recompose(c, 1, W.QA, W.QB, W.MA, W.MB, W.cA2, W.cB2), "recompose");
+  CK(launch_deorient(c, bond, W.cA2, W.cB2, W.A, W.B), "write back");
+  CK(launch_su_weight(c, bond, 1, 1, W.A, W.B, W.A, W.B), "SU unweight");
+  CK(launch_su_lambda(c, bond), "SU lambda");
+  return NTU_OK;
+}
+
+extern "C" int ntu_su_update(ntu_ctx* c, int bond, const double* gate, double* delta_out) {
+  if (!c || !gate) return fail(c, NTU_EINVAL, "ntu_su_update: NULL argument");
+  if (bond < 0 || bond > 3) return fail(c, NTU_EINVAL, "bond=%d outside 0..3", bond);
+  const Plan& P = c->plan;
+  size_t d4 = (size_t)P.d * P.d * P.d * P.d;
+  CK(cudaMemcpyAsync(c->w.cG, gate, d4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+     "copy gate");
+  double* info_dev = c->w.info + 4 * (size_t)c->w.cap;
+  int st = su_bond(c, bond, c->w.cG, info_dev);
+  if (st) return st;
+  double info[4];
+  CK(cudaMemcpyAsync(info, info_dev, sizeof(info), cudaMemcpyDeviceToHost, c->stream), "copy info");
+  st = check_status(c);
+  c->stage = 0;
+  if (st) return st;
+  if (delta_out) *delta_out = info[1];
+  return NTU_OK;
+}
+
+extern "C" int ntu_su_step(ntu_ctx* c, const double* gates2, const double* gate1_half,
+                           double* delta_out) {
+  if (!c || !gates2) return fail(c, NTU_EINVAL, "ntu_su_step: NULL argument");
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  size_t d4 = (size_t)P.d * P.d * P.d * P.d, d2 = (size_t)P.d * P.d;
+  CK(cudaMemcpyAsync(W.cG, gates2, 4 * d4 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+     "copy gates");
+  if (gate1_half)
+    CK(cudaMemcpyAsync(W.op, gate1_half, d2 * sizeof(double2), cudaMemcpyHostToDevice, c->stream),
+       "copy gate1");
+  double* info_dev = W.info + 4 * (size_t)W.cap;
+  c->launches = 0;
+  int st0 = run_step(c, true, gate1_half != nullptr, info_dev);
+  if (st0) return st0;
+  double info[16];
+  CK(cudaMemcpyAsync(info, info_dev, sizeof(info), cudaMemcpyDeviceToHost, c->stream), "copy info");
+  int st = check_status(c);
+  c->stage = 0;
+  if (st) return st;
+  if (delta_out)
+    for (int b = 0; b < 4; ++b) delta_out[b] = info[4 * b + 1];
+  return NTU_OK;
 }
 
 // ---------------------------------------------------------------- batches

@@ -1056,11 +1056,12 @@ cudaError_t launch_repair(ntu_ctx* c, int n, const void* graw, int raw_is_f32, d
 }
 
 cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
-                       const double2* RB, double2* MA, double2* MB, double* info) {
+                       const double2* RB, double2* MA, double2* MB, double* info, int sweeps) {
   const Plan& P = c->plan;
   Work& W = c->w;
   AlsArgs a;
-  a.D = P.D; a.K = P.K; a.ng = P.ng; a.nA = P.nA; a.sweeps = c->cfg.als_sweeps;
+  a.D = P.D; a.K = P.K; a.ng = P.ng; a.nA = P.nA;
+  a.sweeps = sweeps < 0 ? c->cfg.als_sweeps : sweeps;
   a.kmin = c->cfg.tau_kmin; a.kmax = c->cfg.tau_kmax;
   a.g = g; a.RA = RA; a.RB = RB; a.MA = MA; a.MB = MB; a.info = info;
   a.x0 = W.x0; a.gx0 = W.gx0; a.Tm = W.Tm; a.gA = W.gA; a.gC = W.gC; a.jv = W.jv; a.pv = W.pv;
@@ -1074,7 +1075,9 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   const int sms = c->sms;
   // a batch that leaves SMs idle gives each item 2 or 4 CTAs (one cluster)
   int split = a.df ? W.als_split : 1;
-  while (split > 1 && (long long)n * split > 3LL * sms) split >>= 1;
+  if (c->tune.als_split > 0) split = c->tune.als_split;   // ntu_set_tuning (<= W.als_split)
+  else
+    while (split > 1 && (long long)n * split > 3LL * sms) split >>= 1;
   a.split = split;
   a.sync = W.als_sync;
   a.wait_polls = c->wait_polls;
@@ -1102,7 +1105,8 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
     if (e != cudaSuccess) return e;
     return after_launch(c, "k_als (cluster)");
   }
-  if (n > 2 * sms) {
+  const bool three = c->tune.als_ctas_per_sm ? c->tune.als_ctas_per_sm == 3 : n > 2 * sms;
+  if (three) {
     cudaFuncSetAttribute(k_als<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k_als<3, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);

@@ -494,7 +494,7 @@ cudaError_t launch_t12(ntu_ctx* c, int n, const void* Etop) {
   a.err = c->d_status;
   if (a.units == 0) return cudaSuccess;
   const int grid = (int)(a.units < c->sms ? a.units : c->sms);
-  if (P.D == 8)
+  if (P.D == 8 && c->tune.t12_pair != 0)
     k_t12<8><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(P.mapYs, P.mapQs, P.mapT2st, a);
   else
     k_t12<0><<<grid, T12_THREADS, T12_SMEM, c->stream>>>(P.mapYs, P.mapQs, P.mapT2st, a);

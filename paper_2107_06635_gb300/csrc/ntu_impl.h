@@ -105,6 +105,7 @@ struct Work {
   double2 *cA2, *cB2;
   double2 *mscr1, *mscr2, *medge;   // measurement scratch
   double2 *mval;
+  double* lam;                // simple update: bond tensors lambda_0..3 (4 x D)
 };
 
 }  // namespace ntu
@@ -130,10 +131,16 @@ struct ntu_ctx {
   int sms;            // streaming multiprocessors of the context's device
   long long wait_polls;   // poll limit of the ALS rendezvous (wait_budget, or 2^23)
   int inject_timeout;     // ntu_inject_wait_timeout: rendezvous target one too high
+  ntu_tuning tune;        // schedule choices (ntu_set_tuning)
+  int use_graphs;         // capture the unit-cell step as a CUDA graph
+  cudaGraphExec_t step_graph[4];  // [ntu_step, ntu_su_step] x [no gate1, gate1]
+  int step_graph_launches[4];
 };
 
 namespace ntu {
 
+// drop the captured unit-cell step graphs (after a change that they bake in)
+void drop_step_graphs(ntu_ctx* c);
 // error helper: record message, return status
 int fail(ntu_ctx* c, int status, const char* fmt, ...);
 // Called after every launch: counts it and, in debug mode, synchronises and
@@ -153,8 +160,10 @@ cudaError_t launch_env(ntu_ctx* c, int n, const double2* Ta, const double2* Tb,
                        const double2* QA, const double2* QB, void* graw);
 cudaError_t launch_repair(ntu_ctx* c, int n, const void* graw, int raw_is_f32, double2* g,
                           double* diag);
+// sweeps < 0: the context's als_sweeps
 cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
-                       const double2* RB, double2* MA, double2* MB, double* info);
+                       const double2* RB, double2* MA, double2* MB, double* info,
+                       int sweeps = -1);
 cudaError_t launch_recompose(ntu_ctx* c, int n, const double2* QA, const double2* QB,
                              const double2* MA, const double2* MB, double2* Ta_out,
                              double2* Tb_out);
@@ -166,6 +175,11 @@ cudaError_t launch_site_gate(ntu_ctx* c, double2* A, double2* B, const double2* 
 cudaError_t launch_measure(ntu_ctx* c, const double2* T, const double2* N, const double2* op,
                            double2* out);
 cudaError_t launch_copy_raw(ntu_ctx* c, int n, const void* graw, double2* g);
+// simple update (k_su.cu)
+cudaError_t launch_su_weight(ntu_ctx* c, int skip, int inverse, int normalise,
+                             const double2* A, const double2* B, double2* Aout, double2* Bout);
+cudaError_t launch_su_lambda(ntu_ctx* c, int bond);
+cudaError_t launch_identity_metric(ntu_ctx* c, double2* g);
 size_t als_smem_bytes();
 // Dynamic shared-memory limits of the fixed-size kernels, set on the
 // current device when a context is created there (k_gate_qr.cu, k_t12.cu,

@@ -413,3 +413,23 @@ extern "C" int ntu_uneven_sync(ntu_uneven* u) {
 }
 
 extern "C" int ntu_uneven_last_launch_count(const ntu_uneven* u) { return u ? u->launches : 0; }
+
+extern "C" int ntu_uneven_set_tuning(ntu_uneven* u, int kind, const ntu_tuning* t) {
+  if (!u || !t) return ufail(u, NTU_EINVAL, "ntu_uneven_set_tuning: NULL argument");
+  if (kind < 0 || kind >= u->nk) return ufail(u, NTU_EINVAL, "kind %d outside 0..%d", kind, u->nk - 1);
+  const int st = ntu_set_tuning(u->ctx[kind], t);
+  if (st != NTU_OK)
+    return ufail(u, st, "kind %d (D=%d, r=%d): %s", kind, u->D[kind], u->r[kind],
+                 ntu_last_error(u->ctx[kind]));
+  u->g_host.drop();
+  u->g_dev.drop();
+  return NTU_OK;
+}
+
+extern "C" int ntu_uneven_get_tuning(const ntu_uneven* u, int kind, ntu_tuning* t,
+                                     int* split_max) {
+  if (!u || !t) return ufail(const_cast<ntu_uneven*>(u), NTU_EINVAL, "ntu_uneven_get_tuning: NULL argument");
+  if (kind < 0 || kind >= u->nk)
+    return ufail(const_cast<ntu_uneven*>(u), NTU_EINVAL, "kind %d outside 0..%d", kind, u->nk - 1);
+  return ntu_get_tuning(u->ctx[kind], t, split_max);
+}

@@ -26,6 +26,14 @@ class NTUError(RuntimeError):
         self.status = status
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("t12_pair", ctypes.c_int), ("als_ctas_per_sm", ctypes.c_int),
+                ("als_split", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Config(ctypes.Structure):
     _fields_ = [("D", ctypes.c_int), ("d_phys", ctypes.c_int), ("d_anc", ctypes.c_int),
                 ("r", ctypes.c_int), ("als_sweeps", ctypes.c_int), ("precision", ctypes.c_int),
@@ -51,6 +59,10 @@ _SIGS = {
     "ntu_als_truncate": [_P, _I, _P, _P, _P],
     "ntu_step": [_P, _P, _P, _P],
     "ntu_measure": [_P, _I, _P, _P],
+    "ntu_su_set_lambdas": [_P, _P],
+    "ntu_su_get_lambdas": [_P, _P],
+    "ntu_su_update": [_P, _I, _P, _P],
+    "ntu_su_step": [_P, _P, _P, _P],
     "ntu_batch_update_dev": [_P, _I, _P, _P, _P, _P, _P, _P],
     "ntu_batch_update_host": [_P, _I, _P, _P, _P, _P, _P, _P],
     "ntu_batch_gate_qr_dev": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
@@ -60,6 +72,11 @@ _SIGS = {
     "ntu_batch_recompose_dev": [_P, _I, _P, _P, _P, _P, _P, _P],
     "ntu_last_launch_count": [_P],
     "ntu_inject_wait_timeout": [_P, _I],
+    "ntu_set_tuning": [_P, ctypes.POINTER(Tuning)],
+    "ntu_get_tuning": [_P, ctypes.POINTER(Tuning), _P],
+    "ntu_set_graphs": [_P, _I],
+    "ntu_uneven_set_tuning": [_P, _I, ctypes.POINTER(Tuning)],
+    "ntu_uneven_get_tuning": [_P, _I, ctypes.POINTER(Tuning), _P],
     "ntu_set_profiling": [_P, _I],
     "ntu_stage_times": [_P, _P],
     "ntu_solver_paths": [_P, _P],
@@ -206,6 +223,29 @@ class Context:
         self._ck(self.lib.ntu_step(self.h, _ptr(G), _ptr(g1), _ptr(deltas)))
         return deltas
 
+    # ---- simple update (Sec. II) ----------------------------------------
+    def su_set_lambdas(self, lam):
+        L = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(4, self.D))
+        self._ck(self.lib.ntu_su_set_lambdas(self.h, _ptr(L)))
+
+    def su_get_lambdas(self):
+        L = np.empty((4, self.D))
+        self._ck(self.lib.ntu_su_get_lambdas(self.h, _ptr(L)))
+        return L
+
+    def su_update(self, bond: int, gate) -> float:
+        G = _c128(gate)
+        d = ctypes.c_double()
+        self._ck(self.lib.ntu_su_update(self.h, bond, _ptr(G), ctypes.addressof(d)))
+        return d.value
+
+    def su_step(self, gates2, gate1_half=None):
+        G = _c128(np.stack([_c128(g) for g in gates2]))
+        g1 = None if gate1_half is None else _c128(gate1_half)
+        deltas = np.empty(4)
+        self._ck(self.lib.ntu_su_step(self.h, _ptr(G), _ptr(g1), _ptr(deltas)))
+        return deltas
+
     def measure(self, site: int, op) -> complex:
         O = _c128(op)
         v = np.empty(1, np.complex128)
@@ -249,6 +289,19 @@ class Context:
         self._ck(self.lib.ntu_batch_recompose_dev(self.h, n, _ptr(QA), _ptr(QB), _ptr(MA),
                                                   _ptr(MB), _ptr(Ta_out), _ptr(Tb_out)))
 
+    def set_tuning(self, t12_pair: int = -1, als_ctas_per_sm: int = 0, als_split: int = 0):
+        t = Tuning(t12_pair, als_ctas_per_sm, als_split)
+        self._ck(self.lib.ntu_set_tuning(self.h, ctypes.byref(t)))
+
+    def get_tuning(self):
+        t = Tuning()
+        smax = ctypes.c_int()
+        self._ck(self.lib.ntu_get_tuning(self.h, ctypes.byref(t), ctypes.addressof(smax)))
+        return t.as_dict(), smax.value
+
+    def set_graphs(self, on: bool = True):
+        self._ck(self.lib.ntu_set_graphs(self.h, 1 if on else 0))
+
     def inject_wait_timeout(self, on: bool = True):
         self._ck(self.lib.ntu_inject_wait_timeout(self.h, 1 if on else 0))
 
@@ -289,6 +342,7 @@ class UnevenBatch:
         self.lib = load()
         self.kinds = [tuple(k) for k in kinds]
         self.d, self.d_anc = d, d_anc
+        self.precision = precision
         n = len(self.kinds)
         Ds = (ctypes.c_int * n)(*[k[0] for k in self.kinds])
         rs = (ctypes.c_int * n)(*[k[1] for k in self.kinds])
@@ -372,3 +426,18 @@ class UnevenBatch:
 
     def last_launch_count(self) -> int:
         return self.lib.ntu_uneven_last_launch_count(self.h)
+
+    def set_tuning(self, kind: int, t12_pair: int = -1, als_ctas_per_sm: int = 0,
+                   als_split: int = 0):
+        t = Tuning(t12_pair, als_ctas_per_sm, als_split)
+        self._ck(self.lib.ntu_uneven_set_tuning(self.h, kind, ctypes.byref(t)))
+
+    def get_tuning(self, kind: int):
+        t = Tuning()
+        smax = ctypes.c_int()
+        self._ck(self.lib.ntu_uneven_get_tuning(self.h, kind, ctypes.byref(t),
+                                                ctypes.addressof(smax)))
+        return t.as_dict(), smax.value
+
+    def split_max(self, kind: int) -> int:
+        return self.get_tuning(kind)[1]
