@@ -88,8 +88,12 @@ def als_peak(precision, gemm_peaks):
         return FP64_PEAK, "nominal FP64 (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)"
     if "fp32_tflops" in gemm_peaks:
         return gemm_peaks["fp32_tflops"] * 1e12, ("measured fp32 GEMM (cuBLAS SGEMM, no TF32, "
-                                                   "this run): the build runs in double-FP32 "
-                                                   "on the FP32 lanes")
+                                                   "this run): the ceiling of the lane build "
+                                                   "(double-FP32 on the FP32 lanes); the "
+                                                   "tensor-core build emulates the same FP64-"
+                                                   "accurate contraction with 21 exact BF16 "
+                                                   "slice products, so it is held to the same "
+                                                   "ceiling")
     return FP32_SIMT_PEAK, "nominal FP32 lanes (152 x 128 x 2 x 2.07 GHz)"
 
 
@@ -552,7 +556,10 @@ def run_ours(args):
     def measure(precision, steps, warmup, kmax, tune=False):
         ctx = ntu.Context(D, 2, 1, r, S, precision, 4, kmax, B, stream=stream.cuda_stream)
         ctx.tuning = None
-        if tune:
+        if args.tuning:
+            ctx.set_tuning(**json.loads(args.tuning))
+            ctx.tuning = {"chosen": json.loads(args.tuning), "source": "--tuning"}
+        elif tune:
             ctx.tuning = tuned(ctx, precision)
         ctx.set_profiling(True)
         t_step, stages, launches = [], [], 0
@@ -583,7 +590,8 @@ def run_ours(args):
         region), whose result is cached."""
         from paper_2107_06635_gb300 import autotune
         dev = torch.cuda.get_device_name()
-        key = {"D": D, "r": r, "d": 2, "batch": B, "sweeps": S, "precision": int(precision)}
+        key = {"D": D, "r": r, "d": 2, "batch": B, "sweeps": S, "precision": int(precision),
+           "library": 2}
         rec = None if args.retune else autotune.lookup(dev, key)
         if rec is not None:
             ctx.set_tuning(**rec["chosen"])
@@ -683,6 +691,37 @@ def run_ours(args):
         ms = max_over_ranks(statistics.mean(ts))
         return {"value": job_rate(world, B, ms), "unit": "bond updates/s", "ms_per_step": ms}
 
+    def measure_cell(Dc, prec, steps=20, warmup=3):
+        """The unit-cell Trotter step of one NTU Trotter step of the two-site
+        cell (ntu_step: four bond updates, gate exp(-i 0.01 ZZ), 10 sweeps,
+        iid complex site tensors from seed 1; host gates in, deltas out,
+        synchronised) with its launches replayed from one CUDA graph and
+        issued one by one; wall time per step on the host."""
+        gates2 = [I.zz_gate(0.01)] * 4
+        gate1 = None
+        out = {"D": Dc, "precision": int(prec),
+               "workload": f"one NTU Trotter step of the 2-site cell, D={Dc}, seed 1, "
+                           "exp(-i 0.01 ZZ), 10 sweeps"}
+        for graphs in (True, False):
+            cx = ntu.Context(Dc, 2, 1, r, S, prec, 4, 15 if prec == ntu.NTU_FP64 else 8, 1,
+                             stream=stream.cuda_stream)
+            cx.set_graphs(graphs)
+            cx.set_state(*I.random_pair(1, 2, Dc))
+            for _ in range(warmup):
+                cx.step(gates2, gate1)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                cx.step(gates2, gate1)
+            dt = (time.perf_counter() - t0) / steps
+            out["graph" if graphs else "direct"] = {
+                "ms_per_step": 1e3 * dt, "bond_updates_per_s": 4 / dt,
+                "launches_per_step": cx.last_launch_count()}
+            cx.close()
+        out["speedup_graph"] = out["direct"]["ms_per_step"] / out["graph"]["ms_per_step"]
+        return out
+
+    cell = None if args.no_cell else measure_cell(3, ntu.NTU_FP64)
+
     d6 = None
     if D != 6 and not args.no_d6:
         d6 = {"D": 6, "batch_per_gpu": B, "path": args.precision,
@@ -741,6 +780,7 @@ def run_ours(args):
         **others,
         "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "d6": d6,
+        "cell_step": cell,
         "e2e": {"value": job_rate(world, B, 1e3 * e2e_s), "unit": "bond updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -823,9 +863,13 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--ref-items", type=int, default=8,
                     help="most items the reference arm times per step")
+    ap.add_argument("--no-cell", action="store_true", help="skip the unit-cell step line")
     ap.add_argument("--no-tune", action="store_true",
                     help="run the automatic schedule instead of the autotuner's choice")
     ap.add_argument("--retune", action="store_true", help="search again, ignoring the cache")
+    ap.add_argument("--tuning", default=None,
+                    help='a fixed ntu_set_tuning choice as JSON, e.g. \'{"als_split": 1}\' '
+                         '(replaces the autotuner)')
     ap.add_argument("--workload", default="uniform", choices=["uniform", "uneven"],
                     help="uniform: the D=8 batch (default); uneven: D in 3..8, r in {2, 4}")
     args = ap.parse_args()

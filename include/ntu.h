@@ -104,6 +104,8 @@ typedef struct {
  * times. */
 int ntu_init(const ntu_config* cfg, void* stream, ntu_ctx** out);
 int ntu_destroy(ntu_ctx* ctx);
+/* The last error message of `ctx`; with ctx == NULL, of the calling thread's
+ * last failed call that had no context (ntu_init, ntu_gate_qr_noalloc). */
 const char* ntu_last_error(const ntu_ctx* ctx);
 /* Wait for the context's stream; returns the first device-raised status. */
 int ntu_sync(ntu_ctx* ctx);
@@ -285,8 +287,7 @@ int ntu_batch_recompose_dev(ntu_ctx* ctx, int n, const double* QA, const double*
 int ntu_inject_wait_timeout(ntu_ctx* ctx, int on);
 
 /* ---- launch tuning ------------------------------------------------------
- * Schedule choices of a context's kernels that change speed, never results
- * (every combination gives the same numbers bit for bit).  Fields:
+ * Schedule and arithmetic choices of a context's kernels.  Fields:
  *   t12_pair        -1: automatic (pair at D = 8); 0: the fused t1 -> t2
  *                   kernel runs one (k, k') unit per GEMM2; 1: pairs of units
  *                   (k, k'), (k, k'+1) share one N = 128 GEMM2 (D = 8 only);
@@ -296,7 +297,15 @@ int ntu_inject_wait_timeout(ntu_ctx* ctx, int on);
  *   als_split       0: automatic (the split chosen at ntu_init, reduced
  *                   while items x split exceeds 3 x SMs); 1, 2 or 4 CTAs per
  *                   item's ALS, at most the split ntu_init allocated for
- *                   (mixed contexts only; FP64 contexts take 0 or 1).
+ *                   (mixed contexts only; FP64 contexts take 0 or 1);
+ *   als_build       how the mixed contexts build the ALS reduced metric
+ *                   (Fig. 5(b)): 0 automatic (2 where possible), 1 in
+ *                   double-FP32 on the FP32 lanes, 2 its first stage on the
+ *                   tensor cores with exact BF16 slicing (K = D r = 16 and
+ *                   one CTA per item only; else the lanes).  The two builds
+ *                   agree to ~2^-48 relative, not bit for bit.
+ * The schedule fields change speed only: with the same als_build every
+ * combination gives the same numbers bit for bit.
  * ntu_set_tuning rejects out-of-range values with NTU_EINVAL and drops the
  * CUDA graphs the context captured.  ntu_get_tuning reads the settings and,
  * in split_max, the largest als_split this context accepts.
@@ -307,6 +316,7 @@ typedef struct {
   int t12_pair;
   int als_ctas_per_sm;
   int als_split;
+  int als_build;
 } ntu_tuning;
 int ntu_set_tuning(ntu_ctx* ctx, const ntu_tuning* t);
 int ntu_get_tuning(const ntu_ctx* ctx, ntu_tuning* t, int* split_max);
@@ -363,11 +373,17 @@ int ntu_solver_paths(ntu_ctx* ctx, int* counts);
  * 4 MiB array in device memory, held by every GPU that loads the library
  * until the process exits.  Sizes needing more than 4 MiB of scratch
  * (16 * (2 d^2 r + 4 (d_p D^3)(D r)) bytes) are rejected with NTU_EINVAL.
- * The first call on a device looks up the array's device address, so make
- * that first call before any stream capture.  Every call reuses the same
- * array: calls that overlap on the GPU (different streams, or several host
- * threads) race on it and must be serialised by the caller.  Errors are
- * reported through ntu_last_error(NULL). */
+ * The first call on a device looks up the array's device address and sets a
+ * kernel's shared-memory limit there, so make that first call before any
+ * stream capture; under lazy module loading (the CUDA default) that first
+ * call, or the first launch of its kernels, may also load the module, which
+ * places the array and may synchronise the device, so make a warm-up call
+ * outside latency-critical code.  The looked-up address is kept for the
+ * life of the process: no cudaDeviceReset may come between calls.  Every
+ * call reuses the same array: calls that overlap on the GPU (different
+ * streams, or several host threads) race on it and must be serialised by
+ * the caller.  Errors are reported through ntu_last_error(NULL), whose
+ * message belongs to the calling host thread. */
 int ntu_gate_qr_noalloc(int D, int d_phys, int d_anc, int r, const double* Ta,
                         const double* Tb, const double* gate, double* QA, double* RA,
                         double* QB, double* RB, void* stream);

@@ -26,14 +26,36 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
                              "tuning.json")
 
 
-def candidates(D: int, precision: int, split_max: int):
+AUTOMATIC = {"t12_pair": -1, "als_ctas_per_sm": 0, "als_split": 0, "als_build": 0}
+
+
+def candidates(D: int, precision: int, split_max: int, builds=(0,)):
     """Every valid tuning of a context: t12 pairing (split-BF16 at D = 8
-    only), ALS CTAs per SM, ALS split up to what the context allocated."""
+    only), ALS CTAs per SM, ALS split up to what the context allocated, and
+    the ALS reduced-metric builds in `builds` (1 lanes, 2 tensor cores; the
+    tensor-core build runs only with one CTA per item)."""
     pairs = [0, 1] if (D == 8 and precision == ntu.NTU_MIXED_BF16X3) else [-1]
     ctas = [2, 3]
     splits = [s for s in (1, 2, 4) if s <= split_max] if precision != ntu.NTU_FP64 else [1]
-    return [{"t12_pair": p, "als_ctas_per_sm": c, "als_split": s}
-            for p, c, s in itertools.product(pairs, ctas, splits)]
+    out = []
+    for p, c, s, b in itertools.product(pairs, ctas, splits, builds):
+        if b == 2 and s != 1:
+            continue
+        out.append({"t12_pair": p, "als_ctas_per_sm": c, "als_split": s, "als_build": b})
+    return out
+
+
+def builds_of(setter) -> tuple:
+    """The reduced-metric builds a context accepts: (1, 2) where the
+    tensor-core build is available, else (1,); `setter(**tuning)` applies a
+    tuning and raises NTUError when it is refused."""
+    try:
+        setter(als_build=2)
+        return (1, 2)
+    except ntu.NTUError:
+        return (1,)
+    finally:
+        setter()
 
 
 def _timer(torch, stream, flush):
@@ -67,7 +89,8 @@ def tune_batch(ctx, n, Ta, Tb, G, Ta_out, Tb_out, info, stream, reps: int = 3):
     auto_ms = timed(run, reps)
     _, smax = ctx.get_tuning()
     table = []
-    for t in candidates(ctx.D, ctx.cfg.precision, smax):
+    builds = builds_of(ctx.set_tuning) if ctx.cfg.precision != ntu.NTU_FP64 else (0,)
+    for t in candidates(ctx.D, ctx.cfg.precision, smax, builds):
         ctx.set_tuning(**t)
         table.append((t, timed(run, reps)))
     best, best_ms = min(table, key=lambda x: x[1])
@@ -76,7 +99,7 @@ def tune_batch(ctx, n, Ta, Tb, G, Ta_out, Tb_out, info, stream, reps: int = 3):
         chosen, chosen_ms = best, best_ms
     else:
         ctx.set_tuning()
-        chosen, chosen_ms = {"t12_pair": -1, "als_ctas_per_sm": 0, "als_split": 0}, auto_ms
+        chosen, chosen_ms = dict(AUTOMATIC), auto_ms
     ctx.sync()
     return {"chosen": chosen, "chosen_ms": chosen_ms, "automatic_ms": auto_ms,
             "table": [(t, round(ms, 4)) for t, ms in table]}
@@ -97,7 +120,9 @@ def tune_uneven(ub, kinds, heaviest: int, stream, reps: int = 3, mode=None):
     auto_ms = timed(run, reps)
     D = kinds[heaviest][0]
     table = []
-    for t in candidates(D, ub.precision, ub.split_max(heaviest)):
+    builds = (builds_of(lambda **t: ub.set_tuning(heaviest, **t))
+              if ub.precision != ntu.NTU_FP64 else (0,))
+    for t in candidates(D, ub.precision, ub.split_max(heaviest), builds):
         ub.set_tuning(heaviest, **t)
         table.append((t, timed(run, reps)))
     best, best_ms = min(table, key=lambda x: x[1])
@@ -106,7 +131,7 @@ def tune_uneven(ub, kinds, heaviest: int, stream, reps: int = 3, mode=None):
         chosen, chosen_ms = best, best_ms
     else:
         ub.set_tuning(heaviest)
-        chosen, chosen_ms = {"t12_pair": -1, "als_ctas_per_sm": 0, "als_split": 0}, auto_ms
+        chosen, chosen_ms = dict(AUTOMATIC), auto_ms
     ub.sync()
     return {"kind": list(kinds[heaviest]), "chosen": chosen, "chosen_ms": chosen_ms,
             "automatic_ms": auto_ms, "table": [(t, round(ms, 4)) for t, ms in table]}

@@ -15,7 +15,9 @@
 
 using namespace ntu;
 
-static char g_noctx_err[320] = "";
+// Errors of calls without a context (ntu_init, ntu_gate_qr_noalloc): one
+// message per host thread, read by ntu_last_error(NULL) on that thread.
+static thread_local char g_noctx_err[320] = "";
 
 int ntu::fail(ntu_ctx* c, int status, const char* fmt, ...) {
   char* buf = c ? c->err : g_noctx_err;
@@ -164,6 +166,12 @@ void carve(ntu_ctx* c, Carver& cv) {
   W.medge = cv.take<double2>(4 * (size_t)P.D * P.D);
   W.mval = cv.take<double2>(2);
   W.lam = cv.take<double>(4 * (size_t)P.D);
+  // slices of g for the tensor-core ALS build (mixed contexts, K = 16):
+  // 2 steps x 16 column blocks x 2 row tiles x 3 boxes x 128 rows x 128 bytes
+  const bool oz = mixed && P.K == 16;
+  W.gsl = oz ? (void*)cv.take<char>(n * (size_t)2 * 12288 * 128) : nullptr;
+  W.gexp = oz ? cv.take<short>(n * (size_t)2 * 16 * 256) : nullptr;
+  W.gmap = oz ? cv.take<CUtensorMap>(1) : nullptr;
 }
 }  // namespace
 
@@ -298,6 +306,17 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
       return fail(nullptr, st, "tensor maps of the split operands");
     }
   }
+  if (c->w.gsl) {
+    // the tensor-core ALS build needs tcgen05 (compute capability 10.x)
+    int major = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (major == 10 &&
+        tc_make_map(&c->plan.mapGsl, c->w.gsl, 64, 2 * 12288, f.max_batch, 128) == NTU_OK &&
+        cudaMemcpy(c->w.gmap, &c->plan.mapGsl, sizeof(CUtensorMap), cudaMemcpyHostToDevice) ==
+            cudaSuccess)
+      c->plan.oz_ok = 1;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     ntu_destroy(c);
     return fail(nullptr, NTU_ECUDA, "device synchronize after allocation");
@@ -349,6 +368,11 @@ extern "C" int ntu_set_tuning(ntu_ctx* c, const ntu_tuning* t) {
   if (t->als_split > c->w.als_split)
     return fail(c, NTU_EINVAL, "als_split=%d exceeds the %d this context allocated for",
                 t->als_split, c->w.als_split);
+  if (t->als_build < 0 || t->als_build > 2)
+    return fail(c, NTU_EINVAL, "als_build=%d outside 0..2", t->als_build);
+  if (t->als_build == 2 && !c->plan.oz_ok)
+    return fail(c, NTU_EINVAL, "als_build=2 needs a mixed context with K = D r = 16 on a "
+                "compute capability 10.x GPU");
   c->tune = *t;
   drop_step_graphs(c);
   return NTU_OK;

@@ -9,6 +9,7 @@
 
 #include "ntu_dev.cuh"
 #include "ntu_impl.h"
+#include "oz_build.cuh"
 
 namespace ntu {
 
@@ -226,6 +227,8 @@ struct AlsShared {
   int flag;
   int n_cg, n_fast, n_eig;
 };
+static_assert(OZ_SMEM_BYTES <= 3 * 32 * 32 * sizeof(double2),
+              "the tensor-core build lives in the SVD work arrays A, V, W");
 
 // The double-FP32 split of the isometric factor (during a build) and of the
 // CG direction (during a solve) live in the SVD work array W, which only the
@@ -252,6 +255,11 @@ struct AlsArgs {
   int* sync;                   // n exchange counters, zero at launch (split > 1)
   long long wait_polls;        // poll limit of a rendezvous
   int sync_extra;              // 0; 1 only under ntu_inject_wait_timeout
+  int oz;                      // build the first stage on the tensor cores (K = 16)
+  __nv_bfloat16* gsl;          // n x 2 x OZ_ROWS_PER_SIDE x 64 slices of g
+  short* gexp;                 // n x 2 x K x n_g exponents of the slice segments
+  const CUtensorMap* gmap;     // TMA map of gsl, in global memory (a tensor map as a
+                               // kernel parameter slowed this kernel down 1.85x)
 };
 
 // out = g v in double-FP32 products from the split copy gdf = g 2^-ge (mixed
@@ -520,6 +528,202 @@ __device__ void als_reduced_df(AlsShared& sm, const AlsArgs& a, const float4* gd
     __syncwarp();
   }
   __syncthreads();
+}
+
+// Row tile tau (0..OZ_TILES-1) of a tensor-core build: column block f of
+// g and row tile t (row blocks f1 = 8 t .. 8 t + 7), listing only the tiles
+// that hold a block f1 >= f.
+__device__ __forceinline__ void oz_tile_ft(int tau, int& f, int& t) {
+  if (tau < 16) { f = tau >> 1; t = tau & 1; }
+  else { f = tau - 8; t = 1; }
+}
+
+// als_reduced_df with its first stage, T = g_blk F, on the tensor cores
+// (oz_build.cuh).  Thread 0 issues the TMA loads of the g slices (three
+// 16 KB boxes per tile, two buffers) and the MMAs; all eight warps combine
+// the six accumulator levels into the double-FP32 tile of T in shared
+// memory (warp w: TMEM lanes of quarter w % 4, output columns of half w / 4)
+// and then form the D x D blocks F^H T of the tile's row blocks f1 >= f, one
+// block per warp.  Per tile, as soon as its accumulator is complete both
+// buffers are free and the next tile's first two boxes are loaded; their
+// MMAs go out after the epilogue, the third box is loaded while the blocks
+// are formed and issued after them, so the loads overlap the lane work.
+// Returns false if a tensor-core wait ran out (status raised, loads in
+// flight drained; the caller then uses the lane build).
+__device__ bool als_reduced_oz(AlsShared& sm, const AlsArgs& a, const CUtensorMap* mapG,
+                               long long item, int e, int side, double2* gX, float4* gXdf,
+                               const short* gexp, uint32_t tmem) {
+  const int tid = threadIdx.x, D = a.D, nA = a.nA, K = OZ_K, ng = K * K;
+  const int warp = tid >> 5, lane = tid & 31;
+  const double2* F = side == 0 ? sm.MB : sm.MA;
+  const OzSmem os = oz_smem(&sm.S);
+  float4* Ts = reinterpret_cast<float4*>(sm.y);        // 128 rows x D (y, y2, p, ap: 16 KB)
+  uint64_t* full = os.bar;
+  uint64_t* freeb = os.bar + 2;
+  uint64_t* accb = os.bar + 4;
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i) tc::mbar_init(&os.bar[i], 1);
+    tc::fence_barrier_init();
+    *os.dead = 0;
+  }
+  oz_fill_b(os, F, D);                                  // ends with a barrier
+  // ---- thread 0's steps.  Box G (tile G / 3, box G % 3) uses buffer G & 1,
+  // whose use number G >> 1 gives the barrier phases.  `issued` / `landed`
+  // count the boxes loaded and waited for, so that a failed wait can still
+  // drain the loads in flight before the shared memory is reused.
+  int issued = 0, landed = 0;
+  bool ok0 = true;
+  const uint64_t bd = tc::sdesc_k128(tc::smem_u32(os.bop));
+  auto load = [&](int G) {
+    int f, t;
+    oz_tile_ft(G / OZ_BOXES, f, t);
+    ++issued;
+    tc::mbar_expect_tx(&full[G & 1], OZ_BOX_BYTES);
+    tc::tma_load_3d(os.abuf + (G & 1) * OZ_BOX_BYTES, mapG, &full[G & 1], 0,
+                    (int)oz_row(side, f, t, G % OZ_BOXES), (int)item);
+  };
+  auto mma_box = [&](int G) {
+    if (!ok0) return;
+    if (!tc::mbar_wait_sleep(&full[G & 1], (uint32_t)((G >> 1) & 1), OZ_POLLS)) { ok0 = false; return; }
+    ++landed;
+    tc::fence_after_sync();
+    const uint64_t ad = tc::sdesc_k128(tc::smem_u32(os.abuf + (G & 1) * OZ_BOX_BYTES));
+    const int box = G % OZ_BOXES;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * box + h;
+      const uint32_t idesc = tc::idesc_bf16_f32(128, (OZ_SLICES - i) * OZ_LEVEL_COLS);
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+        tc::mma_bf16(tmem + (uint32_t)(i * OZ_LEVEL_COLS), ad + 4 * h + 2 * kk, bd + 2 * kk,
+                     idesc, (i | kk) != 0);
+    }
+    tc::mma_commit(&freeb[G & 1]);
+    if (box == OZ_BOXES - 1) tc::mma_commit(accb);
+  };
+  auto wait_free = [&](int G) {       // the MMAs of box G have retired
+    if (ok0 && !tc::mbar_wait_sleep(&freeb[G & 1], (uint32_t)((G >> 1) & 1), OZ_POLLS)) ok0 = false;
+  };
+  if (tid == 0) {                                     // tile 0 in full
+    load(0);
+    load(1);
+    mma_box(0);
+    mma_box(1);
+    wait_free(0);
+    if (ok0) load(2);
+    mma_box(2);
+    if (!ok0) *os.dead = 1;
+  }
+  __syncthreads();
+  for (int tau = 0; tau < OZ_TILES && !*os.dead; ++tau) {
+    int f, t;
+    oz_tile_ft(tau, f, t);
+    const int Gn = (tau + 1) * OZ_BOXES;               // first box of the next tile
+    const bool more = tau + 1 < OZ_TILES;
+    // ---- epilogue: warp w combines the six levels of TMEM lane row =
+    // 32 (w % 4) + lane for the output columns of q = 4 (w / 4) .. + 3
+    {
+      const bool ready =
+          __all_sync(0xffffffffu, tc::mbar_wait_sleep(accb, (uint32_t)(tau & 1), OZ_POLLS));
+      tc::fence_after_sync();
+      if (tid == 0 && ready && more && ok0) {
+        // every MMA of this tile has retired: both buffers take the next
+        // tile's first two boxes now
+        load(Gn);
+        load(Gn + 1);
+      }
+      const int row = (warp & 3) * 32 + lane, qh = warp >> 2;
+      float hi[8], lo[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) { hi[m] = 0.f; lo[m] = 0.f; }
+      if (ready) {
+        const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(qh * 8);
+#pragma unroll
+        for (int l0 = 0; l0 < OZ_SLICES; l0 += 3) {
+          float v[24];
+          tc::tmem_ld8x3(ta + l0 * OZ_LEVEL_COLS, ta + (l0 + 1) * OZ_LEVEL_COLS,
+                         ta + (l0 + 2) * OZ_LEVEL_COLS, v);
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            const float sc = __int_as_float((127 - 8 * (l0 + u + 2)) << 23);   // 2^-8(l+2)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) df_add1(hi[m], lo[m], v[u * 8 + m] * sc, 0.f);
+          }
+        }
+      } else {
+        *os.dead = 1;
+      }
+      // exponents are relative to the unscaled g: T in the frame g 2^-ge
+      const int er = gexp[(side * K + f) * ng + t * 128 + row] - e;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = qh * 4 + j;
+        if (q < D) {
+          const int ex = er + os.eq[q];
+          if (ex > -126 && ex < 128) {                  // 2^ex as a normal FP32: exact products
+            const float sc = __int_as_float((ex + 127) << 23);
+            Ts[row * D + q] = make_float4(hi[2 * j] * sc, hi[2 * j + 1] * sc, lo[2 * j] * sc,
+                                          lo[2 * j + 1] * sc);
+          } else {
+            Ts[row * D + q] = make_float4(ldexpf(hi[2 * j], ex), ldexpf(hi[2 * j + 1], ex),
+                                          ldexpf(lo[2 * j], ex), ldexpf(lo[2 * j + 1], ex));
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (*os.dead) break;
+    // ---- the next tile's first two boxes go out; its third loads meanwhile
+    if (tid == 0 && more) {
+      tc::fence_after_sync();
+      mma_box(Gn);
+      mma_box(Gn + 1);
+      wait_free(Gn);
+      if (ok0) load(Gn + 2);
+    }
+    // ---- second stage: the entries (q1, q) of the blocks (f1, f) of this
+    // tile with f1 >= f, spread over the threads (block f1 from rows
+    // 16 (f1 - 8 t) .. of the tile)
+    const int fa = f > t * 8 ? f : t * 8;              // first row block with f1 >= f
+    const int nent = (t * 8 + 8 - fa) * D * D;
+    const float4* Fd = os.fdf;
+    // warp 0 issues the loads and MMAs meanwhile: warps 1-7 take the entries
+    for (int it = tid - 32; it < nent; it += NTU_CTA - 32) {
+      if (it < 0) break;
+      const int f1 = fa + it / (D * D), q1 = (it % (D * D)) / D, q = it % D;
+      if (f1 == f && q1 < q) continue;
+      {
+        const float4* Tw = Ts + (f1 - t * 8) * K * D;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int c1 = 0; c1 < K; ++c1) df_cmac<true>(acc, Fd[c1 * D + q1], Tw[c1 * D + q]);
+        const int row = f1 * D + q1, col = f * D + q;
+        double2 v = df_join(acc);
+        if (e != 0) v = make_double2(scalbn(v.x, e), scalbn(v.y, e));
+        gX[(size_t)col * nA + row] = v;
+        gXdf[(size_t)col * nA + row] = acc;
+        if (row != col) {
+          gX[(size_t)row * nA + col] = cconj(v);
+          gXdf[(size_t)row * nA + col] = make_float4(acc.x, -acc.y, acc.z, -acc.w);
+        }
+      }
+    }
+    if (tid == 0 && more) {
+      mma_box(Gn + 2);                                 // completes the next accumulator
+      if (!ok0) *os.dead = 1;
+    }
+    __syncthreads();
+  }
+  const bool ok = !*os.dead;
+  __syncthreads();
+  if (tid == 0 && !ok) {
+    for (int G = landed; G < issued; ++G)               // drain the loads in flight
+      tc::mbar_wait(&full[G & 1], (uint32_t)((G >> 1) & 1), OZ_WAIT);
+    raise_status(a.status, ST_TIMEOUT, WHY_TC_WAIT);
+  }
+  __syncthreads();
+  return ok;
 }
 
 // Reduced metric and source for the free side (Fig. 5(b,c)).  side 0: the
@@ -884,7 +1088,9 @@ __device__ void als_solve(AlsShared& sm, const AlsArgs& a, int side, double2* gX
 
 // MINB: CTAs per SM the register budget is sized for (2: 128 registers, no
 // spills; 3: 80 registers, for batches of more than two items per SM).
-template <int MINB, bool SPLIT>
+// OZ: the instantiation with the tensor-core build (its code is kept out of
+// the other instantiations, whose register allocation it would perturb).
+template <int MINB, bool SPLIT, bool OZ>
 __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   AlsShared& sm = *reinterpret_cast<AlsShared*>(smem_raw);
@@ -926,6 +1132,18 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     sm.err = 0; sm.n_cg = 0; sm.n_fast = 0; sm.n_eig = 0; sm.ge = 0;
     sm.tau_sel = __longlong_as_double(0x7ff8000000000000ll);
   }
+  // the tensor-core build (single-CTA kernels, K = 16): its accumulator
+  // columns, held until the last sweep (the address passes through red[0])
+  bool oz = OZ && !SPLIT && a.oz;
+  uint32_t oz_tmem = 0;
+  if (oz) {
+    if (wid == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(sm.red), OZ_TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    oz_tmem = *reinterpret_cast<volatile uint32_t*>(sm.red);
+    __syncthreads();
+  }
   // X0 = R_A R_B^T, x0 = vec(X0) with kA slow
   for (int idx = tid; idx < K * K; idx += NTU_CTA) {
     int i = idx / K, j = idx % K;
@@ -944,6 +1162,8 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
     if (tid == 0) sm.ge = ge;
     if (split > 1) als_exchange(a, item, phase);          // the split g is written
   }
+  // the slices of g come from k_oz_slice, launched before this kernel
+  const short* gexp = oz ? a.gexp + item * (long long)2 * K * ng : nullptr;
   // gx0 = g x0 (double-FP32 products on the mixed contexts), eps0 = x0^H g x0
   double e0 = 0.0;
   if (a.df) {
@@ -971,7 +1191,16 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   for (int s = 0; s < a.sweeps; ++s) {
     for (int side = 0; side < 2; ++side) {
       if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
-      if (a.df) {
+      if (oz && als_reduced_oz(sm, a, a.gmap, item, ge, side, gX, reinterpret_cast<float4*>(gC),
+                               gexp, oz_tmem)) {
+        // built on the tensor cores
+      } else if (a.df) {
+        if (oz) {
+          // a tensor-core wait ran out (status raised): the lane build takes
+          // over for the rest of this ALS, the accumulator is released at the end
+          oz = false;
+          if (split == 1) oz_tmem |= 0x80000000u;
+        }
         // every CTA is done with its copy of the last reduced metric before
         // any writes the next one, and all blocks are in before anyone reads
         if (split > 1) als_exchange(a, item, phase);
@@ -987,6 +1216,20 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
         als_solve(sm, a, side, gX, jv, pv, tauv, dv, ev, log);
       }
     }
+  }
+  if (OZ && !SPLIT && a.oz) {
+    // every MMA has retired before the accumulator columns are released
+    const OzSmem os = oz_smem(&sm.S);
+    __syncthreads();
+    if (tid == 0) {
+      tc::mbar_init(&os.bar[5], 1);
+      tc::fence_barrier_init();
+      tc::mma_commit(&os.bar[5]);
+      if (!tc::mbar_wait(&os.bar[5], 0, OZ_WAIT)) raise_status(a.status, ST_TIMEOUT, WHY_TC_WAIT);
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (wid == 0) tc::tmem_dealloc(oz_tmem & 0x7fffffffu, OZ_TMEM_COLS);
   }
   // balance (Fig. 5(d))
   if (a.sweeps > 0 && !als_tilt_fast(sm, a, 2)) als_tilt(sm, a, 2, nullptr);
@@ -1082,11 +1325,17 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   a.sync = W.als_sync;
   a.wait_polls = c->wait_polls;
   a.sync_extra = c->inject_timeout;
+  // the tensor-core build of the reduced metric: single-CTA items, K = 16,
+  // unless the tuning asks for the lane build
+  a.oz = (c->plan.oz_ok && split == 1 && c->tune.als_build != 1) ? 1 : 0;
+  a.gsl = reinterpret_cast<__nv_bfloat16*>(W.gsl);
+  a.gexp = W.gexp;
+  a.gmap = W.gmap;
   if (split > 1) {
     cudaError_t e = cudaMemsetAsync(W.als_sync, 0, sizeof(int) * (size_t)n, c->stream);
     if (e != cudaSuccess) return e;
-    cudaFuncSetAttribute(k_als<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_als<2, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_als<2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_als<2, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
@@ -1101,23 +1350,29 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_als<2, true>, a);
+    e = cudaLaunchKernelEx(&cfg, k_als<2, true, false>, a);
     if (e != cudaSuccess) return e;
     return after_launch(c, "k_als (cluster)");
   }
   const bool three = c->tune.als_ctas_per_sm ? c->tune.als_ctas_per_sm == 3 : n > 2 * sms;
-  if (three) {
-    cudaFuncSetAttribute(k_als<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_als<3, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    k_als<3, false><<<n, NTU_CTA, sm, c->stream>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_als<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_als<2, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    k_als<2, false><<<n, NTU_CTA, sm, c->stream>>>(a);
+  if (a.oz) {
+    // slices of every item's g for the tensor-core build
+    const long long tasks = (long long)n * 2 * OZ_K * OZ_K * OZ_K * 4;
+    long long blocks = (tasks + NTU_CTA - 1) / NTU_CTA;
+    if (blocks > 16LL * sms) blocks = 16LL * sms;
+    k_oz_slice<<<(int)blocks, NTU_CTA, 0, c->stream>>>(n, g,
+                                                       reinterpret_cast<__nv_bfloat16*>(W.gsl),
+                                                       W.gexp);
+    cudaError_t e = after_launch(c, "k_oz_slice");
+    if (e != cudaSuccess) return e;
   }
-  return after_launch(c, "k_als");
+  void (*kern)(AlsArgs) = three ? (a.oz ? k_als<3, false, true> : k_als<3, false, false>)
+                                : (a.oz ? k_als<2, false, true> : k_als<2, false, false>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  kern<<<n, NTU_CTA, sm, c->stream>>>(a);
+  return after_launch(c, a.oz ? "k_als (tensor-core build)" : "k_als");
 }
 
 }  // namespace ntu

@@ -36,10 +36,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NTU_NOALLOC_SCR
 
 // Host copies of the array's device address, one per device.  In host code
 // the symbol g_noalloc_scratch is only a host-side stand-in, never a device
-// address, so the address is looked up with cudaGetSymbolAddress.
+// address, so the address is looked up with cudaGetSymbolAddress.  The set-up
+// also sets k_gate_split's shared-memory limit on that device, once.  The
+// cache assumes the device's context lives as long as the process: after a
+// cudaDeviceReset the array may move, so no reset may come between calls.
 #define NTU_NOALLOC_MAX_DEVICES 64
 static void* g_noalloc_ptr[NTU_NOALLOC_MAX_DEVICES];
 static std::mutex g_noalloc_mu;
+static size_t gate_split_smem_bytes() { return sizeof(ntu::SvdSmem) + 16 * 16 * sizeof(double2); }
 
 static int noalloc_scratch(void** out) {
   int dev = -1;
@@ -54,6 +58,11 @@ static int noalloc_scratch(void** out) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return ntu::fail(nullptr, NTU_ECUDA, "cudaGetSymbolAddress of the scratch array: %s",
+                       cudaGetErrorString(e));
+    e = cudaFuncSetAttribute(ntu::k_gate_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gate_split_smem_bytes());
+    if (e != cudaSuccess)
+      return ntu::fail(nullptr, NTU_ECUDA, "shared-memory limit of k_gate_split: %s",
                        cudaGetErrorString(e));
     g_noalloc_ptr[dev] = p;
   }
@@ -88,13 +97,9 @@ extern "C" int ntu_gate_qr_noalloc(int D, int d_phys, int d_anc, int r, const do
   double2* Mg = GB + n_gate;              // 2 m K: gated matrices of both sides
   double2* Qcm = Mg + 2 * m * K;          // 2 m K: Q work buffers of both sides
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t sm = sizeof(SvdSmem) + 16 * 16 * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(k_gate_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e == cudaSuccess) {
-    k_gate_split<<<1, NTU_CTA, sm, s>>>(d_phys, r, 0, (const double2*)gate, GA, GB);
-    e = cudaGetLastError();
-  }
+  const size_t sm = gate_split_smem_bytes();
+  k_gate_split<<<1, NTU_CTA, sm, s>>>(d_phys, r, 0, (const double2*)gate, GA, GB);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     int zsplit = (int)((m * K + NTU_CTA * 8 - 1) / (NTU_CTA * 8));
     if (zsplit < 1) zsplit = 1;

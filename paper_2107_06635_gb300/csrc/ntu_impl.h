@@ -68,6 +68,9 @@ struct Plan {
   long long rowsE, rowsT, rowsHL, rowsHR;  // allocated rows of the split operands
   int* d_tab;                           // device index tables
   int n_tab;
+  // tensor-core build of the ALS reduced metric (K = 16, mixed contexts)
+  int oz_ok;
+  CUtensorMap mapGsl;                   // slices of g, box 128 rows x 64 BF16
 };
 
 // Device work space for max_batch items.  Every pointer is the base of a
@@ -106,6 +109,9 @@ struct Work {
   double2 *mscr1, *mscr2, *medge;   // measurement scratch
   double2 *mval;
   double* lam;                // simple update: bond tensors lambda_0..3 (4 x D)
+  void* gsl;                  // tensor-core ALS build: BF16 slices of g (n x 3 MB at K = 16)
+  short* gexp;                // and their exponents
+  CUtensorMap* gmap;          // the TMA map of gsl, copied to device memory
 };
 
 }  // namespace ntu

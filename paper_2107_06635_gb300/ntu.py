@@ -28,7 +28,7 @@ class NTUError(RuntimeError):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("t12_pair", ctypes.c_int), ("als_ctas_per_sm", ctypes.c_int),
-                ("als_split", ctypes.c_int)]
+                ("als_split", ctypes.c_int), ("als_build", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -289,8 +289,9 @@ class Context:
         self._ck(self.lib.ntu_batch_recompose_dev(self.h, n, _ptr(QA), _ptr(QB), _ptr(MA),
                                                   _ptr(MB), _ptr(Ta_out), _ptr(Tb_out)))
 
-    def set_tuning(self, t12_pair: int = -1, als_ctas_per_sm: int = 0, als_split: int = 0):
-        t = Tuning(t12_pair, als_ctas_per_sm, als_split)
+    def set_tuning(self, t12_pair: int = -1, als_ctas_per_sm: int = 0, als_split: int = 0,
+                   als_build: int = 0):
+        t = Tuning(t12_pair, als_ctas_per_sm, als_split, als_build)
         self._ck(self.lib.ntu_set_tuning(self.h, ctypes.byref(t)))
 
     def get_tuning(self):
@@ -428,8 +429,8 @@ class UnevenBatch:
         return self.lib.ntu_uneven_last_launch_count(self.h)
 
     def set_tuning(self, kind: int, t12_pair: int = -1, als_ctas_per_sm: int = 0,
-                   als_split: int = 0):
-        t = Tuning(t12_pair, als_ctas_per_sm, als_split)
+                   als_split: int = 0, als_build: int = 0):
+        t = Tuning(t12_pair, als_ctas_per_sm, als_split, als_build)
         self._ck(self.lib.ntu_uneven_set_tuning(self.h, kind, ctypes.byref(t)))
 
     def get_tuning(self, kind: int):

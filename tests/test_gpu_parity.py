@@ -361,6 +361,43 @@ def test_als_double_fp32_build_matches_oracle(D, precision):
         assert _rel(MB[i].cpu().numpy(), mb) < 1e-9
 
 
+@pytest.mark.parametrize("D,r,precision", [(8, 2, 2), (4, 4, 2), (8, 2, 1)])
+def test_als_tensor_core_build_matches_oracle(D, r, precision):
+    """K = D r = 16 on a mixed context with one CTA per item: the first stage
+    of the reduced-metric build runs on the tensor cores with exact BF16
+    slicing (six slices, levels combined in double-FP32).  On the same FP64
+    metric the ALS result stays within 1e-9 of the FP64 oracle, like the
+    double-FP32 lane build, and the two builds agree to 1e-11."""
+    n, sweeps = 3, 10
+    Ta, Tb, G = _items(660 + D, n, 2, D)
+    cfg = O.Config(D=D, r=r, sweeps=sweeps, tau_exponents=tuple(range(4, 9)))
+    gs, RAs, RBs, refs = [], [], [], []
+    for i in range(n):
+        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+        g, _ = O.hermitise_repair(O.metric_raw(Ta[i], Tb[i], qa, qb, 2, D))
+        gs.append(g); RAs.append(ra); RBs.append(rb)
+        refs.append(O.als_truncate(g, ra, rb, D, sweeps, cfg.taus))
+    ctx = _ctx(D, r, sweeps=sweeps, precision=precision, max_batch=n, kmin=4, kmax=8)
+    K = D * r
+    outs = {}
+    for build in (2, 1):
+        ctx.set_tuning(als_split=1, als_build=build)
+        MA, MB = _empty((n, K, D)), _empty((n, K, D))
+        info = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+        ctx.batch_als_dev(n, _dev(np.stack(gs)), _dev(np.stack(RAs)), _dev(np.stack(RBs)), MA,
+                          MB, info)
+        ctx.sync()
+        outs[build] = (MA.cpu().numpy(), MB.cpu().numpy(), info.cpu().numpy())
+    MA, MB, info = outs[2]
+    for i in range(n):
+        ma, mb, eps, delta, eps0, tau = refs[i]
+        assert abs(info[i, 2] - eps0) < 1e-12 * eps0
+        assert abs(info[i, 1] - delta) < 1e-10
+        assert info[i, 3] == tau
+        assert _rel(MA[i], ma) < 1e-9 and _rel(MB[i], mb) < 1e-9
+        assert _rel(MA[i], outs[1][0][i]) < 1e-11 and _rel(MB[i], outs[1][1][i]) < 1e-11
+
+
 @pytest.mark.parametrize("spread,path", [(30.0, "als_cholesky"), (1e7, "als_eigen")])
 def test_als_dense_metric_paths(spread, path):
     """A dense metric g = W diag(lam) W^H (W Haar-random, lam geometric on
@@ -868,9 +905,13 @@ def test_split_als_identical_to_single_cta(precision):
     G = np.stack([I.heisenberg_gate(0.01)] * n)
     small = _ctx(4, 4, precision=precision, max_batch=n, kmax=8)
     big = _ctx(4, 4, precision=precision, max_batch=240, kmax=8)
+    big.set_tuning(als_build=1)           # the lane build, as on the split CTAs
     a1, b1, i1 = small.batch_update_host(Ta, Tb, G)
     a2, b2, i2 = big.batch_update_host(Ta, Tb, G)
     assert np.array_equal(a1, a2) and np.array_equal(b1, b2) and np.array_equal(i1, i2)
+    big.set_tuning()                      # automatic: the tensor-core build (K = 16)
+    a3, b3, i3 = big.batch_update_host(Ta, Tb, G)
+    assert _rel(a3, a1) < 1e-10 and _rel(b3, b1) < 1e-10
     cfg = O.Config(D=4, r=4, tau_exponents=tuple(range(4, 9)))
     for i in range(n):
         A2, B2, inf = O.bond_update(Ta[i], Tb[i], G[i], cfg)

@@ -31,7 +31,9 @@ def _rel(a, b):
 
 def test_noalloc_gate_qr_matches_context_entry_point():
     lib = ntu.load()
-    cases = [(4, 2, 1, 2, 11), (3, 2, 2, 4, 12)]      # two calls in a row
+    # two calls in a row, then the largest configuration the 4 MiB array
+    # takes (D=8, r=4: 2.1 MB of scratch)
+    cases = [(4, 2, 1, 2, 11), (3, 2, 2, 4, 12), (8, 2, 1, 4, 13)]
     for D, d, d_anc, r, seed in cases:
         rng = np.random.default_rng(seed)
         d_p, K = d * d_anc, D * r
@@ -67,3 +69,7 @@ def test_noalloc_rejects_sizes_beyond_the_fixed_array():
     st = lib.ntu_gate_qr_noalloc(8, 4, 2, 4, p, p, p, p, p, p, p, None)
     assert st == 1
     assert b"scratch" in lib.ntu_last_error(None)
+    # a gated matrix with fewer rows than columns (d_p D^2 < r) is refused too
+    st = lib.ntu_gate_qr_noalloc(1, 2, 1, 4, p, p, p, p, p, p, p, None)
+    assert st == 1
+    assert b"unsupported" in lib.ntu_last_error(None)
