@@ -591,7 +591,7 @@ def run_ours(args):
         from paper_2107_06635_gb300 import autotune
         dev = torch.cuda.get_device_name()
         key = {"D": D, "r": r, "d": 2, "batch": B, "sweeps": S, "precision": int(precision),
-           "library": 2}
+           "library": 3}
         rec = None if args.retune else autotune.lookup(dev, key)
         if rec is not None:
             ctx.set_tuning(**rec["chosen"])

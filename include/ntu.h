@@ -295,14 +295,16 @@ int ntu_inject_wait_timeout(ntu_ctx* ctx, int on);
  *                   else 2); 2 or 3: the ALS kernel's register budget for
  *                   that many CTAs per SM;
  *   als_split       0: automatic (the split chosen at ntu_init, reduced
- *                   while items x split exceeds 3 x SMs); 1, 2 or 4 CTAs per
- *                   item's ALS, at most the split ntu_init allocated for
- *                   (mixed contexts only; FP64 contexts take 0 or 1);
+ *                   while items x split exceeds the SMs, 1.5 x SMs at
+ *                   D <= 4); 1, 2 or 4 CTAs per item's ALS, at most the
+ *                   split ntu_init allocated for (mixed contexts only;
+ *                   FP64 contexts take 0 or 1);
  *   als_build       how the mixed contexts build the ALS reduced metric
  *                   (Fig. 5(b)): 0 automatic (2 where possible), 1 in
  *                   double-FP32 on the FP32 lanes, 2 its first stage on the
- *                   tensor cores with exact BF16 slicing (K = D r = 16 and
- *                   one CTA per item only; else the lanes).  The two builds
+ *                   tensor cores with exact BF16 slicing (K = D r = 16 or
+ *                   32, on one CTA or on a cluster of als_split CTAs that
+ *                   divide its tiles; else the lanes).  The two builds
  *                   agree to ~2^-48 relative, not bit for bit.
  * The schedule fields change speed only: with the same als_build every
  * combination gives the same numbers bit for bit.

@@ -32,17 +32,12 @@ AUTOMATIC = {"t12_pair": -1, "als_ctas_per_sm": 0, "als_split": 0, "als_build": 
 def candidates(D: int, precision: int, split_max: int, builds=(0,)):
     """Every valid tuning of a context: t12 pairing (split-BF16 at D = 8
     only), ALS CTAs per SM, ALS split up to what the context allocated, and
-    the ALS reduced-metric builds in `builds` (1 lanes, 2 tensor cores; the
-    tensor-core build runs only with one CTA per item)."""
+    the ALS reduced-metric builds in `builds` (1 lanes, 2 tensor cores)."""
     pairs = [0, 1] if (D == 8 and precision == ntu.NTU_MIXED_BF16X3) else [-1]
     ctas = [2, 3]
     splits = [s for s in (1, 2, 4) if s <= split_max] if precision != ntu.NTU_FP64 else [1]
-    out = []
-    for p, c, s, b in itertools.product(pairs, ctas, splits, builds):
-        if b == 2 and s != 1:
-            continue
-        out.append({"t12_pair": p, "als_ctas_per_sm": c, "als_split": s, "als_build": b})
-    return out
+    return [{"t12_pair": p, "als_ctas_per_sm": c, "als_split": s, "als_build": b}
+            for p, c, s, b in itertools.product(pairs, ctas, splits, builds)]
 
 
 def builds_of(setter) -> tuple:

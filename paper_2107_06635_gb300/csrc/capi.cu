@@ -166,11 +166,13 @@ void carve(ntu_ctx* c, Carver& cv) {
   W.medge = cv.take<double2>(4 * (size_t)P.D * P.D);
   W.mval = cv.take<double2>(2);
   W.lam = cv.take<double>(4 * (size_t)P.D);
-  // slices of g for the tensor-core ALS build (mixed contexts, K = 16):
-  // 2 steps x 16 column blocks x 2 row tiles x 3 boxes x 128 rows x 128 bytes
-  const bool oz = mixed && P.K == 16;
-  W.gsl = oz ? (void*)cv.take<char>(n * (size_t)2 * 12288 * 128) : nullptr;
-  W.gexp = oz ? cv.take<short>(n * (size_t)2 * 16 * 256) : nullptr;
+  // slices of g for the tensor-core ALS build (mixed contexts, K = 16 or
+  // 32): both ALS steps' box rows of 128 bytes, 3 MB (K = 16) or 48 MB
+  // (K = 32) per item, left out beyond 24 GB in all
+  const size_t oz_item = (size_t)2 * oz_rows_side(P.K) * 128;
+  const bool oz = mixed && oz_item > 0 && n * oz_item <= ((size_t)24 << 30);
+  W.gsl = oz ? (void*)cv.take<char>(n * oz_item) : nullptr;
+  W.gexp = oz ? cv.take<short>(n * (size_t)2 * P.K * P.ng) : nullptr;
   W.gmap = oz ? cv.take<CUtensorMap>(1) : nullptr;
 }
 }  // namespace
@@ -312,7 +314,8 @@ int ntu::init_context(const ntu_config* cfg, void* stream, ntu_ctx** out, int ma
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     if (major == 10 &&
-        tc_make_map(&c->plan.mapGsl, c->w.gsl, 64, 2 * 12288, f.max_batch, 128) == NTU_OK &&
+        tc_make_map(&c->plan.mapGsl, c->w.gsl, 64, 2 * oz_rows_side(c->plan.K), f.max_batch,
+                    128) == NTU_OK &&
         cudaMemcpy(c->w.gmap, &c->plan.mapGsl, sizeof(CUtensorMap), cudaMemcpyHostToDevice) ==
             cudaSuccess)
       c->plan.oz_ok = 1;
@@ -371,8 +374,8 @@ extern "C" int ntu_set_tuning(ntu_ctx* c, const ntu_tuning* t) {
   if (t->als_build < 0 || t->als_build > 2)
     return fail(c, NTU_EINVAL, "als_build=%d outside 0..2", t->als_build);
   if (t->als_build == 2 && !c->plan.oz_ok)
-    return fail(c, NTU_EINVAL, "als_build=2 needs a mixed context with K = D r = 16 on a "
-                "compute capability 10.x GPU");
+    return fail(c, NTU_EINVAL, "als_build=2 needs a mixed context with K = D r = 16 or 32 on "
+                "a compute capability 10.x GPU");
   c->tune = *t;
   drop_step_graphs(c);
   return NTU_OK;

@@ -187,6 +187,9 @@ cudaError_t launch_su_weight(ntu_ctx* c, int skip, int inverse, int normalise,
 cudaError_t launch_su_lambda(ntu_ctx* c, int bond);
 cudaError_t launch_identity_metric(ntu_ctx* c, double2* g);
 size_t als_smem_bytes();
+// Box rows of one ALS step's slices of g for the tensor-core build at this
+// K (0 where that build does not exist) (k_solve.cu).
+long long oz_rows_side(int K);
 // Dynamic shared-memory limits of the fixed-size kernels, set on the
 // current device when a context is created there (k_gate_qr.cu, k_t12.cu,
 // k_tc.cu).

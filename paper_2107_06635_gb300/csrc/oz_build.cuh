@@ -1,5 +1,5 @@
 // Tensor-core build of the ALS reduced metric (Fig. 5(b)) with exact
-// integer slicing, for K = D r = 16 on the mixed contexts.
+// integer slicing, for K = D r = 16 or 32 on the mixed contexts.
 //
 // Per half sweep the reduced metric is g_A = (1 x F)^H g (1 x F) with F the
 // fixed K x D factor (M_B on the A step, M_A on the B step).  Its first and
@@ -42,22 +42,50 @@
 
 namespace ntu {
 
-constexpr int OZ_K = 16;                    // K of the tensor-core build
 constexpr int OZ_SLICES = 6;
-constexpr int OZ_BOXES = 3;                 // TMA boxes per tile (two slices per box)
 constexpr int OZ_LEVEL_COLS = 16;           // accumulator columns per level (2 D <= 16)
 constexpr int OZ_TMEM_COLS = 128;           // 6 levels x 16 columns, rounded up
 constexpr int OZ_BOX_BYTES = 128 * 128;     // 128 rows x 64 BF16
 constexpr int OZ_B_ROWS = OZ_SLICES * OZ_LEVEL_COLS;   // 96
-constexpr int OZ_TILES = 24;                // (f, t) tiles per half sweep with f1 >= f
-constexpr int OZ_ROWS_PER_SIDE = OZ_K * 2 * OZ_BOXES * 128;   // 12288 box rows
 constexpr long long OZ_WAIT = 1ll << 26;
 constexpr int OZ_POLLS = 1 << 16;           // polls of up to 20 us each: about a second
 
+// Geometry of the build for K = 16 or 32 (n_g = K^2 rows of g, 128-row
+// tiles): a 128-byte box row holds spb = 32 / K slices of a row segment
+// (2 K reals each), so a tile takes boxes = 6 / spb boxes and each slice
+// K / 8 MMA K-steps; a tile covers bpt = 128 / K row blocks f1, a column
+// block f has T = n_g / 128 tiles, of which those holding a block f1 >= f
+// are built (ntiles per half sweep).
+struct OzGeo {
+  int K, ng, spb, boxes, ksteps, bpt, T, ntiles;
+  long long rows_side;       // box rows of one ALS step's slices
+};
+__host__ __device__ inline OzGeo oz_geo(int K) {
+  OzGeo g;
+  g.K = K; g.ng = K * K; g.spb = 32 / K; g.boxes = OZ_SLICES / g.spb; g.ksteps = K / 8;
+  g.bpt = 128 / K; g.T = g.ng / 128;
+  g.ntiles = 0;
+  for (int f = 0; f < K; ++f) g.ntiles += g.T - f / g.bpt;
+  g.rows_side = (long long)K * g.T * g.boxes * 128;
+  return g;
+}
+__host__ __device__ inline bool oz_supported(int K) { return K == 16 || K == 32; }
+
 // Rows of the slice array of one item: [side][f][t][box][128 rows], each row
-// 64 BF16 = slices (2 box, 2 box + 1) x [Re (16) | Im (16)].
-__device__ __forceinline__ long long oz_row(int side, int f, int t, int box) {
-  return (long long)side * OZ_ROWS_PER_SIDE + ((long long)(f * 2 + t) * OZ_BOXES + box) * 128;
+// 64 BF16 = spb slices x [Re (K) | Im (K)].
+__device__ __forceinline__ long long oz_row(const OzGeo& G, int side, int f, int t, int box) {
+  return (long long)side * G.rows_side + ((long long)(f * G.T + t) * G.boxes + box) * 128;
+}
+
+// Tile tau of a half sweep -> column block f and row tile t (f major, t
+// from the first tile holding a block f1 >= f): the bpt columns blocks f of
+// group b = f / bpt each have T - b tiles.
+__device__ __forceinline__ void oz_tile_ft(const OzGeo& G, int tau, int& f, int& t) {
+  int b = 0, cum = 0;
+  while (b < G.T - 1 && tau >= cum + G.bpt * (G.T - b)) { cum += G.bpt * (G.T - b); ++b; }
+  const int w = G.T - b, rem = tau - cum;
+  f = b * G.bpt + rem / w;
+  t = b + rem % w;
 }
 
 __device__ __forceinline__ void oz_fence_proxy_global() {
@@ -111,27 +139,31 @@ __device__ __forceinline__ uint32_t oz_digit_bits(long long X, int i) {
 // segment exponents (relative to the unscaled g).  Side 1 reads g with kA
 // and kB swapped in rows and columns (the B step's view).  Thread task:
 // one 8-value group (real or imaginary part of 8 consecutive entries) of
-// one row segment; the four groups of a segment are adjacent lanes, which
+// one row segment; the K / 4 groups of a segment are adjacent lanes, which
 // agree on the exponent by shuffles.  Each task writes its 16-byte chunk of
-// all six slices.
+// all six slices.  KK = K = D r (16 or 32).
+template <int KK>
 __global__ void __launch_bounds__(NTU_CTA) k_oz_slice(int n, const double2* __restrict__ g,
                                                       __nv_bfloat16* __restrict__ gsl,
                                                       short* __restrict__ gexp) {
-  const int K = OZ_K, ng = K * K;
-  const long long tasks = (long long)n * 2 * K * ng * 4;
+  constexpr int K = KK;
+  const OzGeo G = oz_geo(K);
+  const int ng = G.ng, gps = K / 4;                    // groups per segment: 4 or 8
+  const long long tasks = (long long)n * 2 * K * ng * gps;
   for (long long task = blockIdx.x * (long long)blockDim.x + threadIdx.x;
        task - threadIdx.x < tasks; task += (long long)gridDim.x * blockDim.x) {
     const bool live = task < tasks;
     const long long tk = live ? task : 0;
-    const int grp = (int)(tk & 3);
-    const long long seg = tk >> 2;
-    const long long item = seg / (2 * K * ng);
-    const int side = (int)((seg / (K * ng)) % 2), f = (int)((seg / ng) % K), R = (int)(seg % ng);
+    const int grp = (int)(tk % gps);
+    const long long seg = tk / gps;
+    const long long item = seg / (2LL * K * ng);
+    const int side = (int)((seg / ((long long)K * ng)) % 2), f = (int)((seg / ng) % K),
+              R = (int)(seg % ng);
     const double2* gi = g + item * (long long)ng * ng;
     const double2* rowp = side == 0 ? gi + (size_t)R * ng + f * K
                                     : gi + (size_t)((R % K) * K + R / K) * ng + f;
     const int cs = side == 0 ? 1 : K;
-    const int part = grp >> 1, c0 = (grp & 1) * 8;
+    const int part = grp / (K / 8), c0 = (grp % (K / 8)) * 8;
     double x[8];
     int e = -100000;
 #pragma unroll
@@ -139,12 +171,11 @@ __global__ void __launch_bounds__(NTU_CTA) k_oz_slice(int n, const double2* __re
       const double2 v = rowp[(c0 + k) * cs];
       x[k] = part ? v.y : v.x;
     }
-    // the segment exponent covers all 32 reals: the other part's maximum
-    // comes from the partner lanes
+    // the segment exponent covers all 2 K reals: the other groups' maxima
+    // come from the partner lanes
 #pragma unroll
     for (int k = 0; k < 8; ++k) e = max(e, oz_bexp(x[k]));
-    e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
-    e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+    for (int o = 1; o < gps; o <<= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
     if (e < -1000) e = 0;                                // an all-zero segment
     if (!live) continue;
     if (grp == 0) gexp[(item * 2 + side) * (long long)K * ng + f * ng + R] = (short)e;
@@ -152,26 +183,28 @@ __global__ void __launch_bounds__(NTU_CTA) k_oz_slice(int n, const double2* __re
 #pragma unroll
     for (int k = 0; k < 8; ++k) X[k] = oz_fixed(x[k], e);
     const int t = R >> 7, r = R & 127;
-    __nv_bfloat16* base = gsl + item * (long long)2 * OZ_ROWS_PER_SIDE * 64;
+    __nv_bfloat16* base = gsl + item * 2 * G.rows_side * 64;
 #pragma unroll
     for (int i = 0; i < OZ_SLICES; ++i) {
       uint32_t w[4];
 #pragma unroll
       for (int k = 0; k < 8; k += 2)
         w[k >> 1] = oz_digit_bits(X[k], i) | (oz_digit_bits(X[k + 1], i) << 16);
-      const long long row = oz_row(side, f, t, i >> 1) + r;
-      *reinterpret_cast<uint4*>(base + row * 64 + (i & 1) * 32 + grp * 8) =
+      const long long row = oz_row(G, side, f, t, i / G.spb) + r;
+      *reinterpret_cast<uint4*>(base + row * 64 + (i % G.spb) * 2 * K + grp * 8) =
           make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
 
 // Shared-memory pieces of the build, carved from the ALS CTA's SVD work
-// arrays (free during a build): two A box buffers, the B operand, F in
-// double-FP32 and F's column exponents.  Base 1024-byte aligned.
-// The mbarriers live there too and are initialised afresh for every build
-// (all their phases complete within a build), so the ALS CTA's permanent
-// shared state does not grow.
+// arrays (free during a build) from the first 1024-byte boundary on: two A
+// box buffers, the B operand and F in double-FP32, 48 KB at K = 32 (the
+// arrays are followed by 1 KB of slack for the alignment).  The column
+// exponents, the failure flag and the
+// mbarriers take the CTA's reduction scratch (unused during a build); the
+// barriers are initialised afresh for every build (all their phases
+// complete within it), so the permanent shared state does not grow.
 struct OzSmem {
   unsigned char* abuf;     // 2 x OZ_BOX_BYTES
   unsigned char* bop;      // OZ_B_ROWS x 128 bytes
@@ -181,30 +214,28 @@ struct OzSmem {
   uint64_t* bar;           // A box full [2], A box free [2], accumulator ready, done
 };
 
-__device__ __forceinline__ OzSmem oz_smem(void* region) {
+__device__ __forceinline__ OzSmem oz_smem(void* region, double* scratch) {
   OzSmem s;
   unsigned char* p = (unsigned char*)(((uintptr_t)region + 1023) & ~(uintptr_t)1023);
   s.abuf = p;
   s.bop = p + 2 * OZ_BOX_BYTES;
   s.fdf = reinterpret_cast<float4*>(s.bop + OZ_B_ROWS * 128);
-  s.eq = reinterpret_cast<int*>(s.fdf + OZ_K * 8);
+  s.eq = reinterpret_cast<int*>(scratch);
   s.dead = s.eq + 8;
-  s.bar = reinterpret_cast<uint64_t*>(s.eq + 16);
+  s.bar = reinterpret_cast<uint64_t*>(scratch + 5);
   return s;
 }
 
-// Bytes of the build's shared pieces, including the alignment slack.
-constexpr size_t OZ_SMEM_BYTES = 1024 + 2 * OZ_BOX_BYTES + OZ_B_ROWS * 128 +
-                                 OZ_K * 8 * sizeof(float4) + 16 * sizeof(int) +
-                                 6 * sizeof(uint64_t);
+// Bytes of the build's shared pieces in the SVD arrays at the largest K.
+constexpr size_t OZ_SMEM_BYTES = 2 * OZ_BOX_BYTES + OZ_B_ROWS * 128 + 32 * 8 * sizeof(float4);
 
 // B operand of one half sweep from F (K x D, FP64 complex): row
-// l * 16 + 2 q + part holds slice l of output column (q, part) over the 32
+// l * 16 + 2 q + part holds slice l of output column (q, part) over the 2 K
 // real K positions, written with the 128-byte swizzle the MMA descriptor
 // expects (16-byte chunk c of row n at chunk c ^ (n & 7)).  Also F in
 // double-FP32 for the second stage.
-__device__ void oz_fill_b(const OzSmem& s, const double2* F, int D) {
-  const int tid = threadIdx.x, K = OZ_K;
+static __device__ void oz_fill_b(const OzSmem& s, const double2* F, int K, int D) {
+  const int tid = threadIdx.x, cpr = K / 4;            // used chunks per row
   for (int i = tid; i < K * D; i += NTU_CTA) s.fdf[i] = df_split(F[i]);
   if (tid < D) {
     int e = -100000;
@@ -212,21 +243,20 @@ __device__ void oz_fill_b(const OzSmem& s, const double2* F, int D) {
     s.eq[tid] = e < -1000 ? 0 : e;
   }
   __syncthreads();
-  // 96 rows x 4 used chunks of 8 BF16 (K positions 0..31)
-  for (int it = tid; it < OZ_B_ROWS * 4; it += NTU_CTA) {
-    const int n = it >> 2, ch = it & 3;
+  for (int it = tid; it < OZ_B_ROWS * cpr; it += NTU_CTA) {
+    const int n = it / cpr, ch = it % cpr;
     const int lvl = n >> 4, m = n & 15, q = m >> 1, part = m & 1;
     uint32_t w[4] = {0u, 0u, 0u, 0u};
     if (q < D) {
       const int e = s.eq[q];
       // K position kpos = ch * 8 + k: first half c = kpos (Re F or Im F),
-      // second half c = kpos - 16 (-Im F or Re F)
+      // second half c = kpos - K (-Im F or Re F)
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const int kpos = ch * 8 + k, c = kpos & 15;
+        const int kpos = ch * 8 + k, c = kpos < K ? kpos : kpos - K;
         const double2 fv = F[c * D + q];
         long long X;
-        if (kpos < 16) X = oz_fixed(part ? fv.y : fv.x, e);
+        if (kpos < K) X = oz_fixed(part ? fv.y : fv.x, e);
         else X = part ? oz_fixed(fv.x, e) : -oz_fixed(fv.y, e);
         w[k >> 1] |= oz_digit_bits(X, lvl) << (16 * (k & 1));
       }

@@ -14,12 +14,10 @@ torch = pytest.importorskip("torch")
 
 def test_every_tuning_gives_identical_updates():
     """D = 8, split-BF16, 6 items (the context allocates 4-way ALS splits):
-    t12 pairing on/off x 2 or 3 ALS CTAs per SM x ALS split 1, 2, 4 with the
-    lane build of the reduced metric all reproduce the automatic choice's
-    A', B' and info exactly (the automatic choice splits, which takes the
-    lane build); with the tensor-core build (one CTA per item) the schedule
-    choices agree bit for bit among themselves and with the lane build to
-    1e-10."""
+    t12 pairing on/off x 2 or 3 ALS CTAs per SM x ALS split 1, 2, 4 give,
+    within each build of the reduced metric (lanes, tensor cores), the same
+    A', B' and info bit for bit; the two builds agree to 1e-10, and the
+    automatic choice reproduces one of them exactly."""
     from paper_2107_06635_gb300 import autotune, ntu
     D, n = 8, 6
     Ta, Tb, G = I.batch_items(21, n, 2, D, I.zz_gate(0.01))
@@ -29,21 +27,17 @@ def test_every_tuning_gives_identical_updates():
     assert auto == autotune.AUTOMATIC and smax == 4
     assert autotune.builds_of(ctx.set_tuning) == (1, 2)
     cands = autotune.candidates(D, ntu.NTU_MIXED_BF16X3, smax, (1, 2))
-    assert len(cands) == 12 + 4
-    tc_ref = None
+    assert len(cands) == 12 + 12
+    per_build = {}
     for t in cands:
         ctx.set_tuning(**t)
         out = ctx.batch_update_host(Ta, Tb, G)
-        if t["als_build"] == 1:
-            for a, b in zip(out, ref):
-                assert np.array_equal(a, b), t
-        elif tc_ref is None:
-            tc_ref = out
-            for a, b in zip(out[:2], ref[:2]):
-                assert np.linalg.norm(a - b) < 1e-10 * np.linalg.norm(b), t
-        else:
-            for a, b in zip(out, tc_ref):
-                assert np.array_equal(a, b), t
+        first = per_build.setdefault(t["als_build"], out)
+        for a, b in zip(out, first):
+            assert np.array_equal(a, b), t
+    for a, b in zip(per_build[2][:2], per_build[1][:2]):
+        assert np.linalg.norm(a - b) < 1e-10 * np.linalg.norm(b)
+    assert any(all(np.array_equal(a, b) for a, b in zip(ref, per_build[k])) for k in (1, 2))
     ctx.close()
 
 
