@@ -37,32 +37,59 @@ __device__ __forceinline__ float4* als_fdf(AlsShared& sm) { return reinterpret_c
 __device__ __forceinline__ float4* als_pdf(AlsShared& sm) { return reinterpret_cast<float4*>(sm.S.W) + 256; }
 
 
+static __device__ void als_exchange(const AlsArgs& a, long long item, int& phase);
+
 // out = g v in double-FP32 products from the split copy gdf = g 2^-ge (mixed
-// contexts): v is split into the SVD array A (free outside the tilts), one
-// warp per row, two accumulators per lane, rescaled by 2^ge.
-static __device__ void als_gmat_df(AlsShared& sm, const float4* gdf, int ge, const double2* v,
-                                   double2* out, int ng) {
+// contexts): v is split into the SVD array A (free outside the tilts); a
+// warp takes two rows at a time, two accumulators per row and lane, and
+// rescales by 2^ge.  When an item's ALS runs on `split` CTAs, CTA `rank`
+// takes the rows rank, rank + split, ... and writes them into every CTA's
+// copy of out (`cstride` elements apart, the first at out); the cluster
+// then exchanges, so each copy holds all rows.
+static __device__ void als_gmat_df(AlsShared& sm, const AlsArgs& a, const float4* gdf, int ge,
+                                   const double2* v, double2* out, long long cstride, int ng,
+                                   long long item, int rank, int split, int& phase) {
   const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
   float4* vdf = reinterpret_cast<float4*>(sm.S.A);           // ng <= 1024
   for (int i = tid; i < ng; i += NTU_CTA) vdf[i] = df_split(v[i]);
   __syncthreads();
-  for (int r = wid; r < ng; r += NTU_WARPS) {
-    const float4* gr = gdf + (size_t)r * ng;
-    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+  for (int r0 = rank + 2 * split * wid; r0 < ng; r0 += 2 * split * NTU_WARPS) {
+    const int r1 = r0 + split;
+    const bool two = r1 < ng;
+    const float4* g0 = gdf + (size_t)r0 * ng;
+    const float4* g1 = gdf + (size_t)(two ? r1 : r0) * ng;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a0 = z, a1 = z, b0 = z, b1 = z;
     for (int c = lid; c < ng; c += 64) {
-      df_cmac<false>(a0, gr[c], vdf[c]);
-      if (c + 32 < ng) df_cmac<false>(a1, gr[c + 32], vdf[c + 32]);
+      const float4 v0 = vdf[c];
+      df_cmac<false>(a0, g0[c], v0);
+      df_cmac<false>(b0, g1[c], v0);
+      if (c + 32 < ng) {
+        const float4 v1 = vdf[c + 32];
+        df_cmac<false>(a1, g0[c + 32], v1);
+        df_cmac<false>(b1, g1[c + 32], v1);
+      }
     }
     df_add1(a0.x, a0.z, a1.x, a1.z);
     df_add1(a0.y, a0.w, a1.y, a1.w);
+    df_add1(b0.x, b0.z, b1.x, b1.z);
+    df_add1(b0.y, b0.w, b1.y, b1.w);
     a0 = df_warp_sum(a0);
+    b0 = df_warp_sum(b0);
     if (lid == 0) {
-      double2 y = df_join(a0);
-      if (ge != 0) y = make_double2(scalbn(y.x, ge), scalbn(y.y, ge));
-      out[r] = y;
+      double2 y = df_join(a0), w = df_join(b0);
+      if (ge != 0) {
+        y = make_double2(scalbn(y.x, ge), scalbn(y.y, ge));
+        w = make_double2(scalbn(w.x, ge), scalbn(w.y, ge));
+      }
+      for (int cp = 0; cp < split; ++cp) {
+        out[cp * cstride + r0] = y;
+        if (two) out[cp * cstride + r1] = w;
+      }
     }
   }
-  __syncthreads();
+  if (split > 1) als_exchange(a, item, phase);
+  else __syncthreads();
 }
 
 // Rendezvous of the `split` CTAs of one item (one thread-block cluster, so
@@ -195,30 +222,6 @@ static __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
   }
   __syncthreads();
   return 1;
-}
-
-// g (FP64) -> gdf = g 2^-e in FP32 pairs.  e = 0 while max |Re|, |Im| lies
-// in [2^-60, 2^60] (products and sums of the build then stay far inside the
-// FP32 range); otherwise 2^e is the power of two just above the maximum, an
-// exact scaling.  gdfT[(kB',kA'),(kB,kA)] = gdf[(kA',kB'),(kA,kB)] lets the B
-// step read its blocks along rows as the A step does.  Returns e.
-static __device__ int als_split_g(AlsShared& sm, const double2* g, float4* gdf, float4* gdfT, int ng,
-                                  int K, bool write) {
-  const int tid = threadIdx.x;
-  const size_t nn = (size_t)ng * ng;
-  double mx = 0.0;
-  for (size_t i = tid; i < nn; i += NTU_CTA) mx = fmax(mx, fmax(fabs(g[i].x), fabs(g[i].y)));
-  mx = block_max(mx, sm.red);
-  const int e = (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ilogb(mx) + 1 : 0;
-  for (size_t i = tid; i < nn && write; i += NTU_CTA) {
-    double2 v = g[i];
-    const float4 d = df_split(make_double2(scalbn(v.x, -e), scalbn(v.y, -e)));
-    gdf[i] = d;
-    const int r = (int)(i / ng), c = (int)(i % ng);
-    gdfT[(size_t)((r % K) * K + r / K) * ng + (c % K) * K + c / K] = d;
-  }
-  __syncthreads();
-  return e;
 }
 
 // als_reduced in double-FP32 arithmetic, block by block: block (f1, f),
@@ -919,7 +922,7 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   }
   // the tensor-core build (K = 16 or 32): its accumulator columns, held
   // until the last sweep (the address passes through red[0])
-  bool oz = OZK != 0 && a.oz && a.K == OZK;
+  const bool oz = OZK != 0 && a.oz && a.K == OZK;
   uint32_t oz_tmem = 0;
   if (oz) {
     if (wid == 0) tc::tmem_alloc(reinterpret_cast<uint32_t*>(sm.red), OZ_TMEM_COLS);
@@ -942,17 +945,15 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   if (a.df) {
     gdf = a.gdf + item * (long long)ng * ng;
     gdfT = a.gdfT + item * (long long)ng * ng;
-    ge = als_split_g(sm, g, a.gdf + item * (long long)ng * ng, a.gdfT + item * (long long)ng * ng,
-                     ng, K, rank == 0);
+    ge = a.gscale[item];                                   // g is split by k_gsplit
     if (tid == 0) sm.ge = ge;
-    if (split > 1) als_exchange(a, item, phase);          // the split g is written
   }
   // the slices of g come from k_oz_slice, launched before this kernel
   const short* gexp = oz ? a.gexp + item * (long long)2 * K * ng : nullptr;
   // gx0 = g x0 (double-FP32 products on the mixed contexts), eps0 = x0^H g x0
   double e0 = 0.0;
   if (a.df) {
-    als_gmat_df(sm, gdf, ge, x0, gx0, ng);
+    als_gmat_df(sm, a, gdf, ge, x0, gx0 - rank * (long long)ng, ng, ng, item, rank, split, phase);
     for (int r = tid; r < ng; r += NTU_CTA) e0 += cmulc(x0[r], gx0[r]).x;
   } else {
     for (int r = wid; r < ng; r += NTU_WARPS) {
@@ -973,31 +974,31 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   // (U sqrt(S), conj(V) sqrt(S)) whose first tilt is (U S, conj(V)): with
   // sweeps to run, the start goes straight to the tilted pair.
   als_tilt(sm, a, a.sweeps > 0 ? 0 : 2, x0);
-  for (int s = 0; s < a.sweeps; ++s) {
+  bool tc_dead = false;
+  for (int s = 0; s < a.sweeps && !tc_dead; ++s) {
     for (int side = 0; side < 2; ++side) {
       if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
       // every CTA of a cluster is done with its copy of the last reduced
       // metric before any writes the next one, and all blocks are in before
       // anyone reads
-      bool built = false;
       if constexpr (OZK != 0) {
-        if (oz) {
-          if (split > 1) als_exchange(a, item, phase);
-          built = als_reduced_oz<OZK>(sm, a, a.gmap, item, ge, side, split > 1 ? gX0 : gX,
-                                      reinterpret_cast<float4*>(split > 1 ? gC0 : gC), gexp,
-                                      oz_tmem, rank, split, nA2);
-          if (split > 1) als_exchange(a, item, phase);
-          // a tensor-core wait that ran out (status raised) hands this and the
-          // remaining builds to the lanes; the accumulator is released at the end
-          if (!built) oz = false;
+        if (split > 1) als_exchange(a, item, phase);
+        const bool built = oz && als_reduced_oz<OZK>(sm, a, a.gmap, item, ge, side,
+                                                     split > 1 ? gX0 : gX,
+                                                     reinterpret_cast<float4*>(split > 1 ? gC0 : gC),
+                                                     gexp, oz_tmem, rank, split, nA2);
+        if (split > 1) als_exchange(a, item, phase);
+        // a tensor-core wait that ran out has raised the status: this item's
+        // ALS stops there (the accumulator is released at the end)
+        if (!built) {
+          if (!oz) raise_status(a.status, ST_NUMERIC, WHY_TC_WAIT);
+          tc_dead = true;
+          break;
         }
-      }
-      if (built) {
-        // built on the tensor cores
       } else if (a.df) {
         if (split > 1) als_exchange(a, item, phase);
         als_reduced_df<SPLIT>(sm, a, gdf, gdfT, ge, side, split > 1 ? gX0 : gX,
-                       reinterpret_cast<float4*>(split > 1 ? gC0 : gC), rank, split, nA2);
+                              reinterpret_cast<float4*>(split > 1 ? gC0 : gC), rank, split, nA2);
         if (split > 1) als_exchange(a, item, phase);
       } else {
         als_reduced(sm, a, g, side, Tm, gX, jv, gx0);
@@ -1036,7 +1037,8 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   __syncthreads();
   double eps = 0.0;
   if (a.df) {
-    als_gmat_df(sm, gdf, ge, xv, gx0, ng);                 // gx0 is free by now
+    als_gmat_df(sm, a, gdf, ge, xv, gx0 - rank * (long long)ng, ng, ng, item, rank, split,
+                phase);                                    // gx0 is free by now
     for (int r = tid; r < ng; r += NTU_CTA) eps += cmulc(xv[r], gx0[r]).x;
   } else {
     for (int r = wid; r < ng; r += NTU_WARPS) {

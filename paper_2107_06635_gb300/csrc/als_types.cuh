@@ -49,8 +49,9 @@ struct AlsArgs {
   int rotcap;
   int* status;
   int df;                      // build the reduced metric in double-FP32 arithmetic
-  float4* gdf;                 // n x ng^2 scratch: g split into FP32 pairs
+  float4* gdf;                 // n x ng^2: g 2^-e split into FP32 pairs (k_gsplit)
   float4* gdfT;                // the same with kA and kB swapped in rows and columns
+                               // (written for the lane build only)
   int split;                   // CTAs per item (a cluster); the private scratch above
                                // (x0 ... rk, gA, gC) has n * split copies
   int* sync;                   // n exchange counters, zero at launch (split > 1)
@@ -59,6 +60,7 @@ struct AlsArgs {
   int oz;                      // build the first stage on the tensor cores (K = 16)
   __nv_bfloat16* gsl;          // n x 2 x rows_side x 64 slices of g (oz_build.cuh)
   short* gexp;                 // n x 2 x K x n_g exponents of the slice segments
+  const int* gscale;           // n scale exponents e of the double-FP32 g (k_gsplit)
   const CUtensorMap* gmap;     // TMA map of gsl, in global memory (a tensor map as a
                                // kernel parameter slowed this kernel down 1.85x)
 };

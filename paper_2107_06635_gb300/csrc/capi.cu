@@ -144,6 +144,8 @@ void carve(ntu_ctx* c, Carver& cv) {
   W.rs = cv.take<double>(na * W.rotcap);
   W.rk = cv.take<int>(na * W.rotcap);
   W.als_sync = cv.take<int>(n);
+  W.gmaxb = cv.take<unsigned long long>(n);
+  W.gscale = cv.take<int>(n);
   W.MA = cv.take<double2>(n * (size_t)P.K * P.D);
   W.MB = cv.take<double2>(n * (size_t)P.K * P.D);
   W.info = cv.take<double>(n * 4 + 16);

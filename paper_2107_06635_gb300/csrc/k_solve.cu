@@ -199,6 +199,79 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
   }
 }
 
+// ------------------------------------------- double-FP32 copy of g
+// The mixed contexts' ALS reads g as double-FP32 pairs gdf = g 2^-e.  e = 0
+// while max |Re|, |Im| lies in [2^-60, 2^60] (products and sums of the
+// build then stay far inside the FP32 range); otherwise 2^e is the power of
+// two just above the maximum, an exact scaling.  Two streaming passes over
+// the batch, spread over every SM: the largest |Re|, |Im| of each item, then
+// the split; for the lane build of the reduced metric also the copy
+// gdfT[(kB',kA'),(kB,kA)] = gdf[(kA',kB'),(kA,kB)], which lets the B step
+// read its blocks along rows as the A step does.  The maximum is taken on
+// the bit patterns, whose order is that of the non-negative values; NaN
+// entries are skipped.
+__global__ void __launch_bounds__(NTU_CTA) k_gmax(long long nn, const double2* __restrict__ g,
+                                                  unsigned long long* __restrict__ gmax) {
+  __shared__ unsigned long long red[NTU_WARPS];
+  const long long item = blockIdx.y;
+  const double2* gi = g + item * nn;
+  unsigned long long m = 0;
+  for (long long i = blockIdx.x * (long long)NTU_CTA + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * NTU_CTA) {
+    const double2 v = gi[i];
+    unsigned long long a = dfb_bits(v.x) & 0x7fffffffffffffffull;
+    unsigned long long b = dfb_bits(v.y) & 0x7fffffffffffffffull;
+    if (a > 0x7ff0000000000000ull) a = 0;
+    if (b > 0x7ff0000000000000ull) b = 0;
+    m = max(m, max(a, b));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < NTU_WARPS; ++w) m = max(m, red[w]);
+    atomicMax(gmax + item, m);
+  }
+}
+
+__device__ __forceinline__ int gscale_exp(unsigned long long mb) {
+  const double mx = dfb_double(mb);
+  return (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ilogb(mx) + 1 : 0;
+}
+
+// One row of g per block iteration: row r of gdf is written in place, and
+// row r' = (r mod K) K + r / K of gdfT, whose entry (c mod K) K + c / K is
+// entry c of row r, from a copy staged in shared memory, so that both
+// writes are contiguous.
+__global__ void __launch_bounds__(NTU_CTA) k_gsplit(int ng, int K, const double2* __restrict__ g,
+                                                    const unsigned long long* __restrict__ gmax,
+                                                    int* __restrict__ gscale,
+                                                    float4* __restrict__ gdf,
+                                                    float4* __restrict__ gdfT) {
+  __shared__ float4 row[1024];                          // ng <= 1024
+  const long long item = blockIdx.y, nn = (long long)ng * ng;
+  const int e = gscale_exp(gmax[item]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) gscale[item] = e;
+  const double2* gi = g + item * nn;
+  float4* di = gdf + item * nn;
+  float4* ti = gdfT ? gdfT + item * nn : nullptr;
+  for (int r = blockIdx.x; r < ng; r += gridDim.x) {
+    for (int c = threadIdx.x; c < ng; c += NTU_CTA) {
+      double2 v = gi[(size_t)r * ng + c];
+      if (e != 0) v = make_double2(scalbn(v.x, -e), scalbn(v.y, -e));
+      const float4 d = df_split_bits(v);
+      di[(size_t)r * ng + c] = d;
+      if (ti) row[(c % K) * K + c / K] = d;
+    }
+    if (ti) {
+      __syncthreads();
+      float4* tr = ti + (size_t)((r % K) * K + r / K) * ng;
+      for (int c = threadIdx.x; c < ng; c += NTU_CTA) tr[c] = row[c];
+      __syncthreads();
+    }
+  }
+}
+
 size_t als_smem_bytes() { return sizeof(AlsShared); }
 
 long long oz_rows_side(int K) { return oz_supported(K) ? oz_geo(K).rows_side : 0; }
@@ -262,6 +335,27 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
   a.gsl = reinterpret_cast<__nv_bfloat16*>(W.gsl);
   a.gexp = W.gexp;
   a.gmap = W.gmap;
+  a.gscale = W.gscale;
+  if (a.df) {
+    // the double-FP32 copies of g, on every SM: blocks per item enough for
+    // about eight per SM in all
+    const long long nn = (long long)P.ng * P.ng;
+    long long bx = (8LL * sms + n - 1) / n;
+    const long long most = (nn + 4LL * NTU_CTA - 1) / (4LL * NTU_CTA);
+    if (bx > most) bx = most;
+    if (bx < 1) bx = 1;
+    cudaError_t e = cudaMemsetAsync(W.gmaxb, 0, sizeof(unsigned long long) * (size_t)n, c->stream);
+    if (e != cudaSuccess) return e;
+    k_gmax<<<dim3((unsigned)bx, (unsigned)n), NTU_CTA, 0, c->stream>>>(nn, g, W.gmaxb);
+    e = after_launch(c, "k_gmax");
+    if (e != cudaSuccess) return e;
+    long long bs = (8LL * sms + n - 1) / n;              // row blocks per item
+    if (bs > P.ng) bs = P.ng;
+    k_gsplit<<<dim3((unsigned)bs, (unsigned)n), NTU_CTA, 0, c->stream>>>(
+        P.ng, P.K, g, W.gmaxb, W.gscale, a.gdf, a.oz ? nullptr : a.gdfT);
+    e = after_launch(c, "k_gsplit");
+    if (e != cudaSuccess) return e;
+  }
   if (a.oz) {
     // slices of every item's g for the tensor-core build
     const long long tasks = (long long)n * 2 * P.K * P.ng * (P.K / 4);

@@ -9,6 +9,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "df_bits.cuh"
+
 #define NTU_CTA 256
 #define NTU_WARPS (NTU_CTA / 32)
 
@@ -292,6 +294,16 @@ __device__ __forceinline__ float4 df_split(double2 v) {
 }
 __device__ __forceinline__ double2 df_join(float4 a) {
   return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+}
+// The same split from the bit patterns (df_bits.cuh): the same bits, issued
+// on the integer and FP32 pipes instead of the conversion and FP64 ones.
+// It pays where those limit a kernel (a streaming pass over g) and costs
+// where the FP32 pipe does (the double-FP32 products).
+__device__ __forceinline__ float4 df_split_bits(double2 v) {
+  float rh, rl, ih, il;
+  df_split_real(v.x, rh, rl);
+  df_split_real(v.y, ih, il);
+  return make_float4(rh, ih, rl, il);
 }
 // (sh, sl) += (xh + xl) (yh + yl)
 __device__ __forceinline__ void df_mac1(float& sh, float& sl, float xh, float xl, float yh,

@@ -97,6 +97,8 @@ struct Work {
   int rotcap;
   int als_split;              // most CTAs one item's ALS may use (1, 2 or 4)
   int* als_sync;              // cap exchange counters of the split ALS
+  unsigned long long* gmaxb;  // cap: largest |entry| of each item's g (bit pattern)
+  int* gscale;                // cap: scale exponent e of each item's double-FP32 g
   double2 *MA, *MB;
   double *info;               // 4 per item
   // outputs of a full update when the caller gives none
