@@ -224,6 +224,84 @@ static __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
   return 1;
 }
 
+// Tilt of a half sweep by a QR factorisation (Fig. 5(a)).  Before the step
+// that solves for one factor, the other, fixed one is brought to an
+// isometry: Y = Q R with Q (K x D) orthonormal and R upper triangular with
+// a real positive diagonal (classical Gram-Schmidt, every column
+// orthogonalised twice), Y <- Q and the free factor Z <- Z R^T, so the bond
+// matrix Z Y^T is unchanged.  Any isometry spanning the columns of Y serves:
+// the reduced metric for Q W (W unitary) is (1 x W)^H g_A (1 x W), with the
+// same spectrum, pseudo-inverse truncation and minimiser Z Y^T; only the
+// last tilt (the balance) fixes the gauge, by the SVD.  side 0 (A step):
+// Y = M_B, Z = M_A; side 1: Y = M_A, Z = M_B.  Returns 0, changing nothing,
+// when min R_qq <= 1e-12 max R_qq (the SVD tilt then handles the nearly
+// rank-deficient factor).  Gram-Schmidt takes D dependent reductions where
+// the one-sided Jacobi SVD takes some 15 rounds of FP64 rotations.
+static __device__ int als_tilt_qr(AlsShared& sm, const AlsArgs& a, int side) {
+  const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31, K = a.K, D = a.D;
+  double2* Y = side == 0 ? sm.MB : sm.MA;
+  double2* Z = side == 0 ? sm.MA : sm.MB;
+  double2* Q = sm.S.A;                                  // column q at Q[q * 32 + i]
+  double2* R = sm.S.V;                                  // R[p * 32 + q], row p, column q
+  double* rd = sm.S.s;                                  // R_qq
+  for (int idx = tid; idx < 32 * D; idx += NTU_CTA) {
+    const int i = idx & 31, q = idx >> 5;
+    Q[idx] = i < K ? Y[i * D + q] : cz();
+    R[q * 32 + i] = cz();                               // rows q < D, columns i < 32
+  }
+  __syncthreads();
+  for (int q = 0; q < D; ++q) {
+    for (int pass = 0; pass < 2 && q > 0; ++pass) {
+      // c_p = Q_p^H v for p < q (warp p), then v -= sum_p Q_p c_p
+      for (int p = wid; p < q; p += NTU_WARPS) {
+        double2 c = lid < K ? cmulc(Q[p * 32 + lid], Q[q * 32 + lid]) : cz();
+        c = warp_sum2(c);
+        if (lid == 0) {
+          sm.ph[p] = c;
+          R[p * 32 + q] = cadd(R[p * 32 + q], c);
+        }
+      }
+      __syncthreads();
+      if (tid < K) {
+        double2 v = Q[q * 32 + tid];
+        for (int p = 0; p < q; ++p) v = cfms(Q[p * 32 + tid], sm.ph[p], v);
+        Q[q * 32 + tid] = v;
+      }
+      __syncthreads();
+    }
+    if (wid == 0) {
+      double s2 = lid < K ? cabs2(Q[q * 32 + lid]) : 0.0;
+      s2 = warp_sum(s2);
+      if (lid == 0) rd[q] = sqrt(s2);
+    }
+    __syncthreads();
+    const double rq = rd[q];
+    if (tid < K) Q[q * 32 + tid] = rq > 0.0 ? cscale(Q[q * 32 + tid], 1.0 / rq) : cz();
+    if (tid == 0) R[q * 32 + q] = make_double2(rq, 0.0);
+    __syncthreads();
+  }
+  double lo = rd[0], hi = rd[0];
+  for (int q = 1; q < D; ++q) {
+    lo = rd[q] < lo ? rd[q] : lo;
+    hi = rd[q] > hi ? rd[q] : hi;
+  }
+  if (!(lo > 1e-12 * hi) || !isfinite(hi)) return 0;
+  // Z R^T into W, then both factors in place
+  for (int idx = tid; idx < K * D; idx += NTU_CTA) {
+    const int i = idx / D, q = idx % D;
+    double2 acc = cz();
+    for (int p = q; p < D; ++p) acc = cfma(Z[i * D + p], R[q * 32 + p], acc);
+    sm.S.W[idx] = acc;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < K * D; idx += NTU_CTA) {
+    Z[idx] = sm.S.W[idx];
+    Y[idx] = Q[(idx % D) * 32 + idx / D];
+  }
+  __syncthreads();
+  return 1;
+}
+
 // als_reduced in double-FP32 arithmetic, block by block: block (f1, f),
 // f1 >= f, of the reduced metric is
 //   gX[(f1,q1),(f,q)] = sum_{c',c} conj(F[c'][q1]) g[f1*sf + c'*sc][f*sf + c*sc] F[c][q],
@@ -977,7 +1055,8 @@ __global__ void __launch_bounds__(NTU_CTA, MINB) k_als(AlsArgs a) {
   bool tc_dead = false;
   for (int s = 0; s < a.sweeps && !tc_dead; ++s) {
     for (int side = 0; side < 2; ++side) {
-      if ((s > 0 || side > 0) && !als_tilt_fast(sm, a, side)) als_tilt(sm, a, side, nullptr);
+      if ((s > 0 || side > 0) && !als_tilt_qr(sm, a, side) && !als_tilt_fast(sm, a, side))
+        als_tilt(sm, a, side, nullptr);
       // every CTA of a cluster is done with its copy of the last reduced
       // metric before any writes the next one, and all blocks are in before
       // anyone reads
