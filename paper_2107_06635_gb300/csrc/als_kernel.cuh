@@ -670,8 +670,10 @@ static __device__ void als_mirror_df(float4* A, int nA) {
 // on the copy scaled by 2^-ge (v is split into als_pdf(sm) first).  Two threads
 // per row take the two halves of the sum, each with two independent
 // accumulators, so that the dependent chains are a quarter of n_A long.
+// With rsum (df only), also rsum[i] = sum_{j != i} |Re| + |Im| of the high
+// parts of row i, summed in FP32 (the Gershgorin radii of the solve).
 static __device__ void als_matvec(AlsShared& sm, const double2* A, const float4* Adf, const double2* v,
-                                  double2* out, int nA, bool df) {
+                                  double2* out, int nA, bool df, float* rsum = nullptr) {
   const int tid = threadIdx.x, h = tid & 1;
   const int half = (nA + 1) >> 1;
   const int j0 = h ? half : 0, j1 = h ? nA : half;
@@ -684,14 +686,35 @@ static __device__ void als_matvec(AlsShared& sm, const double2* A, const float4*
     const bool on = i < nA;
     if (df) {
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+      float sr = 0.f;
       if (on) {
         int j = j0;
+        if (rsum) {
 #pragma unroll 4
-        for (; j + 1 < j1; j += 2) {
-          df_cmac<false>(a0, Adf[(size_t)j * nA + i], als_pdf(sm)[j]);
-          df_cmac<false>(a1, Adf[(size_t)(j + 1) * nA + i], als_pdf(sm)[j + 1]);
+          for (; j + 1 < j1; j += 2) {
+            const float4 e0 = Adf[(size_t)j * nA + i], e1 = Adf[(size_t)(j + 1) * nA + i];
+            df_cmac<false>(a0, e0, als_pdf(sm)[j]);
+            df_cmac<false>(a1, e1, als_pdf(sm)[j + 1]);
+            sr += (j != i ? fabsf(e0.x) + fabsf(e0.y) : 0.f) +
+                  (j + 1 != i ? fabsf(e1.x) + fabsf(e1.y) : 0.f);
+          }
+          if (j < j1) {
+            const float4 e0 = Adf[(size_t)j * nA + i];
+            df_cmac<false>(a0, e0, als_pdf(sm)[j]);
+            sr += j != i ? fabsf(e0.x) + fabsf(e0.y) : 0.f;
+          }
+        } else {
+#pragma unroll 4
+          for (; j + 1 < j1; j += 2) {
+            df_cmac<false>(a0, Adf[(size_t)j * nA + i], als_pdf(sm)[j]);
+            df_cmac<false>(a1, Adf[(size_t)(j + 1) * nA + i], als_pdf(sm)[j + 1]);
+          }
+          if (j < j1) df_cmac<false>(a0, Adf[(size_t)j * nA + i], als_pdf(sm)[j]);
         }
-        if (j < j1) df_cmac<false>(a0, Adf[(size_t)j * nA + i], als_pdf(sm)[j]);
+      }
+      if (rsum) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+        if (on && h == 0) rsum[i] = sr;
       }
       df_add1(a0.x, a0.z, a1.x, a1.z);
       df_add1(a0.y, a0.w, a1.y, a1.w);
@@ -731,24 +754,28 @@ static __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, 
   // |Im|) >= sum_{j != i} |gX[i][j]|, so every eigenvalue lies in
   // [min(d - s), max(d + s)].  gX is full and Hermitian, so row i's sum is
   // column i's (contiguous).  On the mixed contexts s_i is summed in FP32
-  // from the high parts of the double-FP32 copy (scaled by 2^-ge); that
+  // from the high parts of the double-FP32 copy (scaled by 2^-ge), in the
+  // pass of the first product g_A x of the conjugate gradients below, which
+  // reads every entry anyway (the product is dropped if tier 2 runs); that
   // rounding (< 1e-5 relative for n_A <= 256) is covered by inflating s_i by
   // 1e-4.
+  const bool df = a.df != 0;
+  const float4* gXdf = reinterpret_cast<const float4*>(gC);
+  const double2* M0 = side == 0 ? sm.MA : sm.MB;
   double glo = INFINITY, ghi = -INFINITY;
-  for (int i = wid; i < nA; i += NTU_WARPS) {
-    double sgi;
-    if (a.df) {
-      const float4* col = reinterpret_cast<const float4*>(gC) + (size_t)i * nA;
-      float sf = 0.f;
-#pragma unroll 4
-      for (int j = lid; j < nA; j += 32) {
-        const float4 v = col[j];
-        sf += j != i ? fabsf(v.x) + fabsf(v.y) : 0.f;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
-      sgi = scalbn((double)sf, sm.ge) * (1.0 + 1e-4);
-    } else {
+  if (df) {
+    float* rsum = reinterpret_cast<float*>(sm.S.V);         // free during a solve
+    for (int i = tid; i < nA; i += NTU_CTA) sm.y[i] = M0[i];
+    __syncthreads();
+    als_matvec(sm, gX, gXdf, sm.y, sm.ap, nA, true, rsum);  // ap = g_A x, and the s_i
+    for (int i = tid; i < nA; i += NTU_CTA) {
+      const double sgi = scalbn((double)rsum[i], sm.ge) * (1.0 + 1e-4);
+      const double d = gX[(size_t)i * nA + i].x;
+      glo = fmin(glo, d - sgi);
+      ghi = fmax(ghi, d + sgi);
+    }
+  } else {
+    for (int i = wid; i < nA; i += NTU_WARPS) {
       const double2* col = gX + (size_t)i * nA;
       double sd = 0.0;
 #pragma unroll 4
@@ -756,11 +783,11 @@ static __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, 
         const double2 v = col[j];
         sd += j != i ? fabs(v.x) + fabs(v.y) : 0.0;
       }
-      sgi = warp_sum(sd);
+      const double sgi = warp_sum(sd);
+      const double d = gX[(size_t)i * nA + i].x;
+      glo = fmin(glo, d - sgi);
+      ghi = fmax(ghi, d + sgi);
     }
-    const double d = gX[(size_t)i * nA + i].x;
-    glo = fmin(glo, d - sgi);
-    ghi = fmax(ghi, d + sgi);
   }
   glo = block_min(glo, sm.red);
   const double bmax = block_max(ghi, sm.red);               // >= lambda_max
@@ -775,12 +802,11 @@ static __device__ int als_solve_chol(AlsShared& sm, const AlsArgs& a, int side, 
     // build left in gC, and a candidate is accepted only once its residual,
     // recomputed in FP64, is <= 1e-13 |J| (at most three restarts from that
     // residual); the FP64 context iterates in FP64 down to 1e-15 |J|.
-    const bool df = a.df != 0;
-    const float4* gXdf = reinterpret_cast<const float4*>(gC);
-    const double2* M0 = side == 0 ? sm.MA : sm.MB;
-    for (int i = tid; i < nA; i += NTU_CTA) sm.y[i] = M0[i];
-    __syncthreads();
-    als_matvec(sm, gX, gXdf, sm.y, sm.ap, nA, df);          // ap = g_A x
+    if (!df) {
+      for (int i = tid; i < nA; i += NTU_CTA) sm.y[i] = M0[i];
+      __syncthreads();
+      als_matvec(sm, gX, gXdf, sm.y, sm.ap, nA, false);     // ap = g_A x
+    }
     double js = 0.0, rs = 0.0;
     for (int i = tid; i < nA; i += NTU_CTA) {
       const double2 r = csub(jv[i], sm.ap[i]);
