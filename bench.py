@@ -98,10 +98,10 @@ def als_peak(precision, gemm_peaks):
 
 
 def als_traffic(precision, D, r, sweeps, items):
-    """DRAM bytes of one k_als launch from the ncu capture recorded in
-    profiles/traffic.json, scaled by items (every item's data is private);
-    None when the kernel sources changed since the capture or the workload
-    differs."""
+    """DRAM bytes of the ALS stage's launches (k_gmax, k_gsplit, k_oz_slice,
+    k_als) from the ncu capture recorded in profiles/traffic.json, scaled by
+    items (every item's data is private); None when the kernel sources
+    changed since the capture or the workload differs."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_als"]
         h = hashlib.sha256()
@@ -765,7 +765,8 @@ def run_ours(args):
         "config": workload_config(args, {
             "bf16x3": PRECISION_BF16X3, "fp32": PRECISION_FP32,
             "fp64": "FP64 throughout"}[args.precision]),
-        "roofline": {"kernel": "k_als (ALS truncation, Fig. 5)", "bound": "alu",
+        "roofline": {"kernel": ("ALS stage (Fig. 5): k_als with its streaming inputs k_gmax, "
+                                "k_gsplit, k_oz_slice"), "bound": "alu",
                      "achieved": achieved / 1e12, "peak": als_pk / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / als_pk,
                      "traffic": als_traffic(args.precision, D, r, S, B),

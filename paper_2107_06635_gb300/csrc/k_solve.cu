@@ -239,10 +239,14 @@ __device__ __forceinline__ int gscale_exp(unsigned long long mb) {
   return (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ilogb(mx) + 1 : 0;
 }
 
-// One row of g per block iteration: row r of gdf is written in place, and
-// row r' = (r mod K) K + r / K of gdfT, whose entry (c mod K) K + c / K is
-// entry c of row r, from a copy staged in shared memory, so that both
-// writes are contiguous.
+// Without the swapped copy a thread loads four entries of the item before
+// it splits and stores them (one load at a time left the kernel latency-
+// bound at a sixth of the HBM rate, measured); with it, one row of g per
+// block iteration: row r of gdf is written in place, and row
+// r' = (r mod K) K + r / K of gdfT, whose entry (c mod K) K + c / K is entry
+// c of row r, from a copy staged in shared memory, so that both writes are
+// contiguous, while the next row's entries are already being loaded.
+constexpr int GSPLIT_BATCH = 4;
 __global__ void __launch_bounds__(NTU_CTA) k_gsplit(int ng, int K, const double2* __restrict__ g,
                                                     const unsigned long long* __restrict__ gmax,
                                                     int* __restrict__ gscale,
@@ -254,21 +258,57 @@ __global__ void __launch_bounds__(NTU_CTA) k_gsplit(int ng, int K, const double2
   if (blockIdx.x == 0 && threadIdx.x == 0) gscale[item] = e;
   const double2* gi = g + item * nn;
   float4* di = gdf + item * nn;
-  float4* ti = gdfT ? gdfT + item * nn : nullptr;
+  if (!gdfT) {
+    const long long step = (long long)gridDim.x * NTU_CTA;
+    for (long long i0 = blockIdx.x * (long long)NTU_CTA + threadIdx.x; i0 < nn;
+         i0 += GSPLIT_BATCH * step) {
+      double2 v[GSPLIT_BATCH];
+#pragma unroll
+      for (int u = 0; u < GSPLIT_BATCH; ++u) {
+        const long long i = i0 + u * step;
+        v[u] = i < nn ? gi[i] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < GSPLIT_BATCH; ++u) {
+        const long long i = i0 + u * step;
+        if (i < nn) {
+          if (e != 0) v[u] = make_double2(scalbn(v[u].x, -e), scalbn(v[u].y, -e));
+          di[i] = df_split_bits(v[u]);
+        }
+      }
+    }
+    return;
+  }
+  float4* ti = gdfT + item * nn;
+  constexpr int PER = 1024 / NTU_CTA;                   // entries of a row per thread, at most
+  double2 cur[PER], nxt[PER];
+  auto load_row = [&](int r, double2* dst) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int c = threadIdx.x + u * NTU_CTA;
+      dst[u] = (r < ng && c < ng) ? gi[(size_t)r * ng + c] : make_double2(0.0, 0.0);
+    }
+  };
+  load_row(blockIdx.x, cur);
   for (int r = blockIdx.x; r < ng; r += gridDim.x) {
-    for (int c = threadIdx.x; c < ng; c += NTU_CTA) {
-      double2 v = gi[(size_t)r * ng + c];
-      if (e != 0) v = make_double2(scalbn(v.x, -e), scalbn(v.y, -e));
-      const float4 d = df_split_bits(v);
-      di[(size_t)r * ng + c] = d;
-      if (ti) row[(c % K) * K + c / K] = d;
+    load_row(r + gridDim.x, nxt);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int c = threadIdx.x + u * NTU_CTA;
+      if (c < ng) {
+        double2 v = cur[u];
+        if (e != 0) v = make_double2(scalbn(v.x, -e), scalbn(v.y, -e));
+        const float4 d = df_split_bits(v);
+        di[(size_t)r * ng + c] = d;
+        row[(c % K) * K + c / K] = d;
+      }
     }
-    if (ti) {
-      __syncthreads();
-      float4* tr = ti + (size_t)((r % K) * K + r / K) * ng;
-      for (int c = threadIdx.x; c < ng; c += NTU_CTA) tr[c] = row[c];
-      __syncthreads();
-    }
+    __syncthreads();
+    float4* tr = ti + (size_t)((r % K) * K + r / K) * ng;
+    for (int c = threadIdx.x; c < ng; c += NTU_CTA) tr[c] = row[c];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) cur[u] = nxt[u];
   }
 }
 
@@ -349,7 +389,7 @@ cudaError_t launch_als(ntu_ctx* c, int n, const double2* g, const double2* RA,
     k_gmax<<<dim3((unsigned)bx, (unsigned)n), NTU_CTA, 0, c->stream>>>(nn, g, W.gmaxb);
     e = after_launch(c, "k_gmax");
     if (e != cudaSuccess) return e;
-    long long bs = (8LL * sms + n - 1) / n;              // row blocks per item
+    long long bs = (8LL * sms + n - 1) / n;              // blocks per item
     if (bs > P.ng) bs = P.ng;
     k_gsplit<<<dim3((unsigned)bs, (unsigned)n), NTU_CTA, 0, c->stream>>>(
         P.ng, P.K, g, W.gmaxb, W.gscale, a.gdf, a.oz ? nullptr : a.gdfT);
