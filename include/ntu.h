@@ -385,7 +385,9 @@ int ntu_solver_paths(ntu_ctx* ctx, int* counts);
  * call reuses the same array: calls that overlap on the GPU (different
  * streams, or several host threads) race on it and must be serialised by
  * the caller.  Errors are reported through ntu_last_error(NULL), whose
- * message belongs to the calling host thread. */
+ * message belongs to the calling host thread.  No device status is kept:
+ * a non-finite input gives non-finite outputs and still returns NTU_OK, so
+ * check the outputs where that matters. */
 int ntu_gate_qr_noalloc(int D, int d_phys, int d_anc, int r, const double* Ta,
                         const double* Tb, const double* gate, double* QA, double* RA,
                         double* QB, double* RB, void* stream);
