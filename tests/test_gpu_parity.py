@@ -1000,3 +1000,38 @@ def test_full_size_bench_batch_sampled_against_oracle(D):
         pair = np.einsum("plurn,qrvwx->plunqvwx", A_o[i], B_o[i])
         pref = np.einsum("plurn,qrvwx->plunqvwx", A2, B2)
         assert _rel(pair, pref) < 1e-4
+
+
+@pytest.mark.parametrize("D,r", [(4, 4), (3, 2)])
+def test_mixed_als_scaled_metric(D, r):
+    """A metric far outside [2^-60, 2^60] is split for the mixed ALS as
+    g 2^-e with e from its largest entry (the per-item maximum and split
+    kernels): every product of the build, the solves and the error is then
+    scaled by exact powers of two, so g 2^70 and g 2^-70 give the same
+    factors and delta as g, and eps scaled by 2^(+-70).  (4,4): the
+    tensor-core build (K = 16); (3,2): the lane build with the swapped copy."""
+    n, sweeps = 2, 6
+    Ta, Tb, G = _items(700 + D, n, 2, D)
+    cfg = O.Config(D=D, r=r, sweeps=sweeps, tau_exponents=tuple(range(4, 9)))
+    gs, RAs, RBs = [], [], []
+    for i in range(n):
+        qa, ra, qb, rb = _oracle_stage(Ta[i], Tb[i], G[i], cfg)
+        g, _ = O.hermitise_repair(O.metric_raw(Ta[i], Tb[i], qa, qb, 2, D))
+        gs.append(g); RAs.append(ra); RBs.append(rb)
+    ctx = _ctx(D, r, sweeps=sweeps, precision=2, max_batch=n, kmin=4, kmax=8)
+    K = D * r
+    outs = {}
+    for p in (0, 70, -70):
+        gsc = np.stack(gs) * 2.0 ** p
+        MA, MB = _empty((n, K, D)), _empty((n, K, D))
+        info = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+        ctx.batch_als_dev(n, _dev(gsc), _dev(np.stack(RAs)), _dev(np.stack(RBs)), MA, MB, info)
+        ctx.sync()
+        outs[p] = (MA.cpu().numpy(), MB.cpu().numpy(), info.cpu().numpy())
+    MA0, MB0, i0 = outs[0]
+    for p in (70, -70):
+        MA, MB, inf = outs[p]
+        assert _rel(MA, MA0) < 1e-12 and _rel(MB, MB0) < 1e-12, p
+        assert np.allclose(inf[:, 1], i0[:, 1], rtol=1e-12, atol=0), p
+        assert np.allclose(inf[:, 0], i0[:, 0] * 2.0 ** p, rtol=1e-12, atol=0), p
+    ctx.close()
