@@ -151,6 +151,42 @@ __device__ void qrdf_factor_inverse(const double2* L, int K, double2* Ru, double
   __syncthreads();
 }
 
+// Row i of X R for the column-major m x K double-FP32 X and an upper
+// triangular R (double-FP32, row-major K x K): out_j = sum_{l <= j} x_l
+// R[l][j], the terms in ascending l.  The outputs are formed in chunks of
+// four columns, highest first, each from one pass over the x_l it needs
+// (a chunk of columns j reads x_l for l <= j only, so writing it in place
+// leaves every x_l a lower chunk reads untouched); the row's entries come
+// from L2 once per chunk instead of once per output.  JOIN: write the
+// FP64 values to the row-major Q row instead of in place.
+template <bool JOIN>
+__device__ __forceinline__ void qrdf_row_times_upper(float4* X, int m, int K, int i,
+                                                     const float4* Rd, double2* Qrow) {
+  constexpr int CH = 4;                                 // columns per chunk (registers)
+  for (int jc = (K - 1) / CH * CH; jc >= 0; jc -= CH) {
+    float4 acc[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int jend = jc + CH < K ? jc + CH : K;
+    for (int l = 0; l < jend; ++l) {
+      const float4 x = X[(size_t)l * m + i];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int j = jc + u;
+        if (j < jend && l <= j) df_cmac<false>(acc[u], x, Rd[l * K + j]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = jc + u;
+      if (j < jend) {
+        if (JOIN) Qrow[j] = df_join(acc[u]);
+        else X[(size_t)j * m + i] = acc[u];
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(NTU_CTA) k_qr_df(int m, int K, const double2* __restrict__ Mg,
                                                    float4* __restrict__ Xg,
                                                    double2* __restrict__ QA, double2* __restrict__ RA,
@@ -162,7 +198,21 @@ __global__ void __launch_bounds__(NTU_CTA) k_qr_df(int m, int K, const double2* 
   const size_t mk = (size_t)m * K;
   const double2* M = Mg + ((size_t)item * 2 + side) * mk;
   float4* X = Xg + ((size_t)item * 2 + side) * mk;
-  for (size_t idx = tid; idx < mk; idx += NTU_CTA) X[idx] = df_split(M[idx]);
+  // four independent loads per thread before the splits and stores (one
+  // at a time left this loop latency-bound)
+  for (size_t i0 = tid; i0 < mk; i0 += 4 * NTU_CTA) {
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t idx = i0 + (size_t)u * NTU_CTA;
+      v[u] = idx < mk ? M[idx] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t idx = i0 + (size_t)u * NTU_CTA;
+      if (idx < mk) X[idx] = df_split(v[u]);
+    }
+  }
   __syncthreads();
   // pass 1: G1 = M^H M = L1 L1^H, R1 = L1^H, Q1 = M R1^{-1} (in place)
   qrdf_gram(X, m, K, S.G);
@@ -177,15 +227,8 @@ __global__ void __launch_bounds__(NTU_CTA) k_qr_df(int m, int K, const double2* 
   }
   if (ok) {
     qrdf_factor_inverse(S.G, K, S.R1, S.Ri, S.Rid);
-    // row i: q_j = sum_{l <= j} x_l Ri[l][j], descending j so that the
-    // update can overwrite x in place
-    for (int i = tid; i < m; i += NTU_CTA) {
-      for (int j = K - 1; j >= 0; --j) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int l = 0; l <= j; ++l) df_cmac<false>(acc, X[(size_t)l * m + i], S.Rid[l * K + j]);
-        X[(size_t)j * m + i] = acc;
-      }
-    }
+    // row i: q_j = sum_{l <= j} x_l Ri[l][j], in place
+    for (int i = tid; i < m; i += NTU_CTA) qrdf_row_times_upper<false>(X, m, K, i, S.Rid, nullptr);
     __syncthreads();
     // pass 2: G2 = Q1^H Q1 = L2 L2^H, R2 = L2^H, Q = Q1 R2^{-1}, R = R2 R1
     qrdf_gram(X, m, K, S.G);
@@ -207,13 +250,8 @@ __global__ void __launch_bounds__(NTU_CTA) k_qr_df(int m, int K, const double2* 
     __syncthreads();
     qrdf_factor_inverse(S.G, K, S.R1, S.Ri, S.Rid);    // R1 <- L2^H, Ri / Rid <- its inverse
     double2* Qo = (side ? QB : QA) + (size_t)item * mk;
-    for (int i = tid; i < m; i += NTU_CTA) {
-      for (int j = 0; j < K; ++j) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int l = 0; l <= j; ++l) df_cmac<false>(acc, X[(size_t)l * m + i], S.Rid[l * K + j]);
-        Qo[(size_t)i * K + j] = df_join(acc);
-      }
-    }
+    for (int i = tid; i < m; i += NTU_CTA)
+      qrdf_row_times_upper<true>(X, m, K, i, S.Rid, Qo + (size_t)i * K);
   }
   if (tid == 0) {
     fallback[item * 2 + side] = ok ? 0 : 1;
