@@ -345,6 +345,12 @@ extern "C" int ntu_destroy(ntu_ctx* c) {
   if (c->d_status) cudaFree(c->d_status);
   for (int i = 0; i < 6; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (int i = 0; i < 3; ++i)
+    if (c->cev[i]) cudaEventDestroy(c->cev[i]);
   plan_free(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -745,6 +751,66 @@ extern "C" int ntu_stage_times(ntu_ctx* c, double* ms_out) {
   return NTU_OK;
 }
 
+// A host-buffer batch of at least two full ALS waves (2 x 3 x SMs items)
+// runs as two halves: the second half's inputs are copied in on a second
+// stream while the first half computes, and the first half's outputs are
+// copied out while the second computes, so that only half of the copies
+// stay outside the compute.  Each half keeps full ALS waves and the same
+// kernels and schedule, so the results are those of one launch.
+static int batch_update_host_halves(ntu_ctx* c, int n, const double* Ta, const double* Tb,
+                                    const double* gates, double* Ta_out, double* Tb_out,
+                                    double* info) {
+  const Plan& P = c->plan;
+  Work& W = c->w;
+  if (!c->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 3; ++i)
+      CK(cudaEventCreateWithFlags(&c->cev[i], cudaEventDisableTiming), "copy event");
+  }
+  cudaStream_t S = c->stream, C = c->copy_stream;
+  const int n1 = n / 2, n2 = n - n1;
+  const size_t t_item = (size_t)P.szT, g_item = (size_t)P.d * P.d * P.d * P.d;
+  const size_t tb1 = n1 * t_item * sizeof(double2), tb2 = n2 * t_item * sizeof(double2);
+  const size_t gb1 = n1 * g_item * sizeof(double2), gb2 = n2 * g_item * sizeof(double2);
+  const size_t ot = n1 * t_item, og = n1 * g_item;      // element offsets of the second half
+  // the second half's inputs go in on C only after S is past any earlier use
+  // of the staging buffers
+  CK(cudaEventRecord(c->cev[0], S), "event");
+  CK(cudaStreamWaitEvent(C, c->cev[0], 0), "wait");
+  CK(cudaMemcpyAsync(W.Ta_in, Ta, tb1, cudaMemcpyHostToDevice, S), "copy Ta");
+  CK(cudaMemcpyAsync(W.Tb_in, Tb, tb1, cudaMemcpyHostToDevice, S), "copy Tb");
+  CK(cudaMemcpyAsync(W.G_in, gates, gb1, cudaMemcpyHostToDevice, S), "copy gates");
+  CK(cudaMemcpyAsync(W.Ta_in + ot, Ta + 2 * ot, tb2, cudaMemcpyHostToDevice, C), "copy Ta");
+  CK(cudaMemcpyAsync(W.Tb_in + ot, Tb + 2 * ot, tb2, cudaMemcpyHostToDevice, C), "copy Tb");
+  CK(cudaMemcpyAsync(W.G_in + og, gates + 2 * og, gb2, cudaMemcpyHostToDevice, C), "copy gates");
+  CK(cudaEventRecord(c->cev[1], C), "event");
+  int st = ntu_batch_update_dev(c, n1, (const double*)W.Ta_in, (const double*)W.Tb_in,
+                                (const double*)W.G_in, (double*)W.Ta_out, (double*)W.Tb_out,
+                                W.info);
+  if (st) return st;
+  CK(cudaEventRecord(c->cev[2], S), "event");
+  CK(cudaStreamWaitEvent(C, c->cev[2], 0), "wait");
+  CK(cudaMemcpyAsync(Ta_out, W.Ta_out, tb1, cudaMemcpyDeviceToHost, C), "copy Ta_out");
+  CK(cudaMemcpyAsync(Tb_out, W.Tb_out, tb1, cudaMemcpyDeviceToHost, C), "copy Tb_out");
+  CK(cudaMemcpyAsync(info, W.info, (size_t)n1 * 4 * sizeof(double), cudaMemcpyDeviceToHost, C),
+     "copy info");
+  CK(cudaStreamWaitEvent(S, c->cev[1], 0), "wait");
+  st = ntu_batch_update_dev(c, n2, (const double*)(W.Ta_in + ot), (const double*)(W.Tb_in + ot),
+                            (const double*)(W.G_in + og), (double*)(W.Ta_out + ot),
+                            (double*)(W.Tb_out + ot), W.info + 4 * (size_t)n1);
+  if (st) return st;
+  CK(cudaMemcpyAsync(Ta_out + 2 * ot, W.Ta_out + ot, tb2, cudaMemcpyDeviceToHost, S),
+     "copy Ta_out");
+  CK(cudaMemcpyAsync(Tb_out + 2 * ot, W.Tb_out + ot, tb2, cudaMemcpyDeviceToHost, S),
+     "copy Tb_out");
+  CK(cudaMemcpyAsync(info + 4 * (size_t)n1, W.info + 4 * (size_t)n1,
+                     (size_t)n2 * 4 * sizeof(double), cudaMemcpyDeviceToHost, S), "copy info");
+  // the call returns when both streams are done
+  CK(cudaEventRecord(c->cev[0], C), "event");
+  CK(cudaStreamWaitEvent(S, c->cev[0], 0), "wait");
+  return check_status(c);
+}
+
 extern "C" int ntu_batch_update_host(ntu_ctx* c, int n, const double* Ta, const double* Tb,
                                      const double* gates, double* Ta_out, double* Tb_out,
                                      double* info) {
@@ -753,6 +819,8 @@ extern "C" int ntu_batch_update_host(ntu_ctx* c, int n, const double* Ta, const 
   if (n == 0) return NTU_OK;
   if (!Ta || !Tb || !gates || !Ta_out || !Tb_out || !info)
     return fail(c, NTU_EINVAL, "ntu_batch_update_host: NULL argument");
+  if (n >= 6 * c->sms)
+    return batch_update_host_halves(c, n, Ta, Tb, gates, Ta_out, Tb_out, info);
   const Plan& P = c->plan;
   Work& W = c->w;
   size_t tb = (size_t)n * P.szT * sizeof(double2);

@@ -132,6 +132,8 @@ struct ntu_ctx {
   size_t env_es;      // element size of the environment buffers
   int profiling;
   cudaEvent_t ev[6];
+  cudaStream_t copy_stream;   // host-buffer batches: the overlapped copies (created on use)
+  cudaEvent_t cev[3];
   int* d_paths;       // [ALS Gershgorin+CG, ALS shifted Cholesky, ALS eigen,
                       //  repair Gershgorin, repair Cholesky, repair eigen,
                       //  QR CholeskyQR2, QR Householder]
