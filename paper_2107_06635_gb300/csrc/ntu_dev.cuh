@@ -370,6 +370,35 @@ struct SvdSmem {
   int bad;        // set when a singular value came out non-finite
 };
 
+// Phase convention of an SVD held as S.A = U (m x n columns), S.V = V:
+// the first entry of each column of U within 1e-10 of the column's largest
+// modulus becomes real positive, V's column taking the same phase (so U S
+// V^H is unchanged); one 16-lane group per column.
+__device__ inline void cta_svd_phase(SvdSmem& S, int m, int n) {
+  const int tid = threadIdx.x, grp = tid >> 4, lane = tid & 15;
+  const unsigned mask = 0xffffu << (tid & 16);
+  for (int k = grp; k < n; k += 16) {
+    double mx = 0.0;
+    for (int r = lane; r < m; r += 16) mx = fmax(mx, cabs2(S.A[k * 32 + r]));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(mask, mx, o));
+    mx = sqrt(mx);
+    int piv = 1 << 30;
+    for (int r = lane; r < m; r += 16)
+      if (mx > 0.0 && sqrt(cabs2(S.A[k * 32 + r])) >= (1.0 - 1e-10) * mx) piv = min(piv, r);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(mask, piv, o));
+    if (mx > 0.0 && isfinite(mx) && piv < m) {
+      double2 up = S.A[k * 32 + piv];
+      double a = sqrt(cabs2(up));
+      double2 ph = make_double2(up.x / a, -up.y / a);
+      for (int r = lane; r < m; r += 16) S.A[k * 32 + r] = cmul(S.A[k * 32 + r], ph);
+      for (int r = lane; r < n; r += 16) S.V[k * 32 + r] = cmul(S.V[k * 32 + r], ph);
+    }
+  }
+  __syncthreads();
+}
+
 __device__ inline void cta_svd_cols(SvdSmem& S, int m, int n, int phase) {
   const int tid = threadIdx.x;
   const int np = (n + 1) & ~1;          // even number of columns (virtual zero col)
@@ -499,28 +528,7 @@ __device__ inline void cta_svd_cols(SvdSmem& S, int m, int n, int phase) {
   __syncthreads();
   for (int i = tid; i < 32 * 32; i += NTU_CTA) { S.A[i] = S.W[i]; }
   __syncthreads();
-  if (!phase) return;
-  // phase convention, one group per column
-  for (int k = grp; k < n; k += 16) {
-    double mx = 0.0;
-    for (int r = lane; r < m; r += 16) mx = fmax(mx, cabs2(S.A[k * 32 + r]));
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(mask, mx, o));
-    mx = sqrt(mx);
-    int piv = 1 << 30;
-    for (int r = lane; r < m; r += 16)
-      if (mx > 0.0 && sqrt(cabs2(S.A[k * 32 + r])) >= (1.0 - 1e-10) * mx) piv = min(piv, r);
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(mask, piv, o));
-    if (mx > 0.0 && isfinite(mx) && piv < m) {
-      double2 up = S.A[k * 32 + piv];
-      double a = sqrt(cabs2(up));
-      double2 ph = make_double2(up.x / a, -up.y / a);
-      for (int r = lane; r < m; r += 16) S.A[k * 32 + r] = cmul(S.A[k * 32 + r], ph);
-      for (int r = lane; r < n; r += 16) S.V[k * 32 + r] = cmul(S.V[k * 32 + r], ph);
-    }
-  }
-  __syncthreads();
+  if (phase) cta_svd_phase(S, m, n);
 }
 
 // Square n x n case with the phase convention.
