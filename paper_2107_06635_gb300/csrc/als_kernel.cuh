@@ -346,8 +346,9 @@ static __device__ int als_tilt_fast(AlsShared& sm, const AlsArgs& a, int mode) {
 // Tilt of a half sweep by a QR factorisation (Fig. 5(a)).  Before the step
 // that solves for one factor, the other, fixed one is brought to an
 // isometry: Y = Q R with Q (K x D) orthonormal and R upper triangular with
-// a real positive diagonal (classical Gram-Schmidt, every column
-// orthogonalised twice), Y <- Q and the free factor Z <- Z R^T, so the bond
+// a real positive diagonal (classical Gram-Schmidt, a column orthogonalised
+// a second time only when the first pass removed more than half of its
+// squared norm), Y <- Q and the free factor Z <- Z R^T, so the bond
 // matrix Z Y^T is unchanged.  Any isometry spanning the columns of Y serves:
 // the reduced metric for Q W (W unitary) is (1 x W)^H g_A (1 x W), with the
 // same spectrum, pseudo-inverse truncation and minimiser Z Y^T; only the
@@ -369,7 +370,19 @@ static __device__ int als_tilt_qr(AlsShared& sm, const AlsArgs& a, int side) {
     R[q * 32 + i] = cz();                               // rows q < D, columns i < 32
   }
   __syncthreads();
+  // squared column norms before any projection (warp per column)
+  double* n2 = sm.S.s + 8;
+  for (int q = wid; q < D; q += NTU_WARPS) {
+    double s2 = lid < K ? cabs2(Q[q * 32 + lid]) : 0.0;
+    s2 = warp_sum(s2);
+    if (lid == 0) n2[q] = s2;
+  }
+  __syncthreads();
   for (int q = 0; q < D; ++q) {
+    // project out the previous columns; a second pass only when the first
+    // left less than 1/sqrt(2) of the norm (the DGKS criterion: then the
+    // column is orthogonal to working precision)
+    double before = n2[q];
     for (int pass = 0; pass < 2 && q > 0; ++pass) {
       // c_p = Q_p^H v for p < q (warp p), then v -= sum_p Q_p c_p
       for (int p = wid; p < q; p += NTU_WARPS) {
@@ -387,16 +400,22 @@ static __device__ int als_tilt_qr(AlsShared& sm, const AlsArgs& a, int side) {
         Q[q * 32 + tid] = v;
       }
       __syncthreads();
+      if (wid == 0) {
+        double s2 = lid < K ? cabs2(Q[q * 32 + lid]) : 0.0;
+        s2 = warp_sum(s2);
+        if (lid == 0) n2[q] = s2;
+      }
+      __syncthreads();
+      const double after = n2[q];
+      if (after >= 0.5 * before) break;
+      before = after;
     }
-    if (wid == 0) {
-      double s2 = lid < K ? cabs2(Q[q * 32 + lid]) : 0.0;
-      s2 = warp_sum(s2);
-      if (lid == 0) rd[q] = sqrt(s2);
-    }
-    __syncthreads();
-    const double rq = rd[q];
+    const double rq = sqrt(n2[q]);
     if (tid < K) Q[q * 32 + tid] = rq > 0.0 ? cscale(Q[q * 32 + tid], 1.0 / rq) : cz();
-    if (tid == 0) R[q * 32 + q] = make_double2(rq, 0.0);
+    if (tid == 0) {
+      R[q * 32 + q] = make_double2(rq, 0.0);
+      rd[q] = rq;
+    }
     __syncthreads();
   }
   double lo = rd[0], hi = rd[0];
