@@ -282,13 +282,14 @@ def test_repair_clips_negative_eigenvalues():
 # ------------------------------------------------------------------ ALS
 @pytest.mark.parametrize("D,r,sweeps,kmin", [(2, 2, 3, 4), (3, 2, 10, 4), (4, 2, 5, 4),
                                              (3, 4, 4, 4), (3, 2, 4, 0), (5, 2, 2, 0),
-                                             (4, 2, 0, 4)])
+                                             (4, 2, 0, 4), (6, 4, 0, 4), (7, 4, 0, 4)])
 def test_als_matches_oracle(D, r, sweeps, kmin):
     """kmin=4: g_A is well conditioned, the Cholesky certificate decides the
     tolerance selection.  kmin=0: the grid starts at tau=1, which drops every
     eigenpair, so the certificate cannot hold and every solve goes through
     the eigendecomposition and the full selection.  sweeps=0: the balanced
-    SVDU truncation with no solve, reported tau NaN."""
+    SVDU truncation with no solve, reported tau NaN; at K = D r = 24 and 28
+    its K x K SVD is the preconditioned one (QR, then Jacobi on R^H)."""
     n = 2
     Ta, Tb, G = _items(600 + D, n, 2, D)
     cfg = O.Config(D=D, r=r, sweeps=sweeps, tau_exponents=tuple(range(kmin, 16)))
@@ -718,11 +719,12 @@ def test_measure_matches_oracle():
 
 
 # ------------------------------------------------------------- uneven batches
-@pytest.mark.parametrize("D,precision", [(7, 0), (8, 0), (8, 2)])
+@pytest.mark.parametrize("D,precision", [(6, 0), (7, 0), (8, 0), (8, 2)])
 def test_batch_update_r4_large_bond(D, precision):
-    """r=4 gates at D=7, 8: K = D r = 28, 32 (the largest bond the library
-    takes), g of size K^2 = 784, 1024 and reduced metrics of n_A = 196, 256;
-    the Heisenberg gate exp(-i 0.01 (XX+YY+ZZ)) has rank 4."""
+    """r=4 gates at D=6, 7, 8: K = D r = 24, 28, 32 (32 is the largest bond
+    the library takes), g of size K^2 = 576, 784, 1024 and reduced metrics of
+    n_A = 144, 196, 256; the Heisenberg gate exp(-i 0.01 (XX+YY+ZZ)) has rank
+    4.  From K = 24 on the SVDU start takes the preconditioned SVD."""
     n = 2
     rng = np.random.default_rng(900 + D)
     Ta = np.stack([I.random_site_tensor(rng, 2, D) for _ in range(n)])
