@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
                                                     double2* __restrict__ pv,
                                                     double* __restrict__ diag, int* status,
                                                     int* paths) {
-  extern __shared__ double chain[];      // 2 * ng
+  extern __shared__ __align__(16) double chain[];   // 2 * ng (also n_g float4 for the Cholesky)
   __shared__ double sred[2 * NTU_WARPS];
   __shared__ int sh[4];
   __shared__ int okflag;
@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(NTU_CTA) k_repair(int ng, const C2in* __restri
   }
   // 2. Cholesky of the lower triangle certifies positive definiteness
   __syncthreads();
-  int ok = kDf ? cta_cholesky_df(reinterpret_cast<float4*>(sc), ng, &okflag)
+  int ok = kDf ? cta_cholesky_df(reinterpret_cast<float4*>(sc), ng, &okflag,
+                                 reinterpret_cast<float4*>(chain))
                : cta_cholesky(sc, ng, 0.0, &okflag);
   if (tid == 0 && paths) atomicAdd(paths + (ok ? 4 : 5), 1);
   double ratio = __longlong_as_double(0x7ff8000000000000ULL);   // NaN

@@ -764,8 +764,10 @@ __device__ inline int cta_cholesky(double2* __restrict__ A, int n, double shift,
 // right-looking steps, with each pivot's square root and reciprocal taken
 // in FP64 from its exact double value.  Returns 1 if every pivot was positive
 // and finite.  Used as the positive-definiteness certificate where the
-// metric itself carries FP32 rounding.
-__device__ inline int cta_cholesky_df(float4* __restrict__ A, int n, int* flag) {
+// metric itself carries FP32 rounding.  col: n float4 of shared memory (the
+// current column, staged for the trailing update).
+__device__ inline int cta_cholesky_df(float4* __restrict__ A, int n, int* flag,
+                                      float4* __restrict__ col) {
   const int tid = threadIdx.x, wid = tid >> 5, lid = tid & 31;
   if (tid == 0) *flag = 1;
   __syncthreads();
@@ -782,20 +784,34 @@ __device__ inline int cta_cholesky_df(float4* __restrict__ A, int n, int* flag) 
       const float sh = (float)sp;
       cj[j] = make_float4(sh, 0.f, (float)(sp - (double)sh), 0.f);
     }
+    // the scaled column j, also staged in shared memory for the update
     for (int i = j + 1 + tid; i < n; i += NTU_CTA) {
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
       df_cmac<false>(acc, cj[i], rdf);
       cj[i] = acc;
+      col[i] = acc;
     }
     __syncthreads();
+    // trailing update, a warp per column k, four independent rows per lane
+    // and iteration (one load-modify-store at a time left this latency-bound)
     for (int k = j + 1 + wid; k < n; k += NTU_WARPS) {
-      const float4 lk = cj[k];
+      const float4 lk = col[k];
       float4* ck = A + (size_t)k * n;
-      for (int i = k + lid; i < n; i += 32) {
-        const float4 ci = cj[i];
-        float4 acc = ck[i];
-        df_cmac<true>(acc, lk, make_float4(-ci.x, -ci.y, -ci.z, -ci.w));   // -= c_i conj(l_k)
-        ck[i] = acc;
+      for (int i0 = k + lid; i0 < n; i0 += 128) {
+        float4 acc[4], ci[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          if (i < n) { acc[u] = ck[i]; ci[u] = col[i]; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u;
+          if (i < n) {
+            df_cmac<true>(acc[u], lk, make_float4(-ci[u].x, -ci[u].y, -ci[u].z, -ci[u].w));   // -= c_i conj(l_k)
+            ck[i] = acc[u];
+          }
+        }
       }
     }
     __syncthreads();
