@@ -205,7 +205,9 @@ int run_graph(ntu_uneven* u, CachedGraph& G, const std::vector<int>& cnt, int pa
     }
     if (e != cudaSuccess) return ufail(u, NTU_ECUDA, "end capture: %s", cudaGetErrorString(e));
     G.graph = g;
-    e = cudaGraphInstantiate(&G.exec, G.graph, 0);
+    // the kernel nodes keep the priorities of the streams they were captured
+    // from (heaviest kinds first), which the replay honours only with this flag
+    e = cudaGraphInstantiate(&G.exec, G.graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
       G.drop();
       return ufail(u, NTU_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
