@@ -192,7 +192,12 @@ int ntu_batch_update_dev(ntu_ctx* ctx, int n, const double* Ta, const double* Tb
                          double* info);
 
 /* Same with host pointers: host-to-device copies, the update and the
- * device-to-host copies, synchronised before return. */
+ * device-to-host copies, synchronised before return.  A batch of at least
+ * 6 x SMs items runs as two halves whose copies overlap the other half's
+ * compute (a second stream of the context, created on first use); the
+ * outputs equal those of one ntu_batch_update_dev call bit for bit, and
+ * ntu_stage_times then reports the second half.  Pinned host buffers let
+ * the copies run asynchronously. */
 int ntu_batch_update_host(ntu_ctx* ctx, int n, const double* Ta, const double* Tb,
                           const double* gates, double* Ta_out, double* Tb_out,
                           double* info);
